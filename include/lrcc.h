@@ -1,0 +1,151 @@
+/*
+ * liblrcc: k-point-blocked LR-CCSD Jacobian products and dipole polarizability
+ * for 1D periodic systems, GB300 (sm_103a).
+ *
+ * The method is the periodic linear-response CCSD of arXiv 2508.01266 (Caricato,
+ * Parsons, Frisch, Abdoullaeva): ground-state amplitudes T and multipliers Lambda
+ * plus crystal-orbital integrals in, alpha_XY(w) for chosen dipole components and
+ * frequencies out (Sec. II, Eqs. 4, 12-15).
+ *
+ * Conventions shared by every entry point
+ *   - Complex numbers are interleaved (re, im) IEEE double pairs ("c128").
+ *   - Momentum: k indices 0..nk-1 on any of the meshes of Sec. II.A; conservation is
+ *     k_a + k_b = k_i + k_j (mod nk) in index space (Eq. 5).
+ *   - Orbitals per cell: nocc occupied then nvir virtual (n = nocc + nvir), closed
+ *     shell, spatial orbitals.  Amplitudes are the alpha / alpha-beta blocks of the
+ *     paper's spin-orbital amplitudes (Sec. II.A keeps all spin blocks).
+ *   - Density-fitting factors L[k1][k2][Q][p][q] (paper units):
+ *         <pq|rs> = (pr|qs) = sum_Q L[kp][kr][Q][p][r] * L[kq][ks][Q][q][s].
+ *     Hermiticity L[k2][k1][Q] = L[k1][k2][Q]^H is assumed, which makes the paper's
+ *     assumption <PQ|RS>* = <RS|PQ> (Sec. II.C) exact.
+ *   - Singles x1[k][i][a]; doubles x2[ki][kj][ka][i][j][a][b] with kb implied,
+ *     in the paper's normalization (t2 and lambda2 carry the factor Nk relative to
+ *     the supercell amplitudes, so Eqs. 6-15 hold with their printed 1/Nk factors).
+ *     Doubles must be pair-symmetric: x2[ki,kj,ka,i,j,a,b] = x2[kj,ki,kb,j,i,b,a].
+ *   - The caller owns every buffer.  set_* calls copy their inputs; no pointer is
+ *     retained after a call returns.  No C++ exception crosses this interface.
+ *   - One problem per host thread at a time.  Device work is issued on the CUDA
+ *     stream given (NULL = legacy default stream).
+ */
+#ifndef LRCC_H_
+#define LRCC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LRCC_OK = 0,
+  LRCC_EINVAL = 1,       /* bad argument, shape or state */
+  LRCC_ENOMEM = 2,       /* host or device allocation failed */
+  LRCC_ECUDA = 3,        /* a CUDA runtime call failed (see lrcc_last_error) */
+  LRCC_ENOCONV = 4,      /* iterative solver did not reach the tolerance */
+  LRCC_ETIMEOUT = 5,     /* a bounded device wait gave up */
+  LRCC_EUNSUPPORTED = 6  /* option or size not supported by this build */
+} lrcc_status;
+
+typedef struct lrcc_problem lrcc_problem;
+typedef struct lrcc_plan lrcc_plan;
+
+typedef struct {
+  int32_t nk, nocc, nvir, naux;
+  int32_t kmesh; /* 0 Gamma-centred, 1 NRecip odd (Gamma + edge), 2 NRecip even (shifted); labels only */
+} lrcc_dims;
+
+typedef struct {
+  double conv_tol;     /* relative residual of the response equations (default 1e-10) */
+  double refine_tol;   /* mixed precision: FP64 residual target of iterative refinement */
+  int32_t max_iter;    /* default 200 */
+  int32_t diis_depth;  /* default 8 */
+  int32_t diis_period; /* extrapolate every n iterations (default 1) */
+  int32_t precision;   /* 0 FP64, 1 TF32, 2 BF16x3 (split bf16, FP32 accumulate) */
+  int32_t autotune;
+  int32_t use_graphs;
+  uint64_t spin_timeout_cycles;
+} lrcc_options;
+
+/* ---------------------------------------------------------------------------
+ * Problem lifecycle
+ * ------------------------------------------------------------------------- */
+
+/* Create a problem for the given sizes (Sec. II.A).  *out receives a handle that
+ * must be released with lrcc_destroy.  Errors: EINVAL for non-positive sizes. */
+lrcc_status lrcc_create(const lrcc_dims* dims, lrcc_problem** out);
+
+/* Integrals of Sec. II.A/II.C: DF factors (c128 [nk][nk][naux][n][n], paper units),
+ * orbital energies eps ([nk][n], canonical Fock diagonal, Eq. 9) and dipole
+ * integrals (c128 [3][nk][n][n], k-diagonal, <p|mu_c|q>).  Pointers are host
+ * memory when on_device == 0, device memory otherwise.  Copies the data. */
+lrcc_status lrcc_set_integrals(lrcc_problem* p, const void* L, const double* eps, const void* dip,
+                               int32_t on_device);
+
+/* Ground-state amplitudes T (Eqs. 7-8) and multipliers Lambda (Eqs. 10-11),
+ * paper normalization, layouts above.  l1/l2 may be NULL when only Jacobian
+ * products are wanted.  Builds the T-dependent intermediates on the device. */
+lrcc_status lrcc_set_ground_state(lrcc_problem* p, const void* t1, const void* t2, const void* l1,
+                                  const void* l2, int32_t on_device);
+
+/* Jacobian product on nrhs vectors (device pointers, RHS-major, each vector laid
+ * out as above).  transpose == 0:  y = A x, the derivative of the CCSD residual
+ * along x (the left-hand side of Eqs. 13-14, i.e. -D t plus all J terms);
+ * transpose == 1:  y = P_sym A^T x under the plain array pairing
+ * sum x1 y1 + sum x2 y2 (the Lambda-type product of Eqs. 10-11), P_sym = pair
+ * symmetrization.  x and y must not overlap.  Asynchronous on `stream`. */
+lrcc_status lrcc_jacobian_apply(lrcc_problem* p, int32_t transpose, int32_t nrhs, const void* x1,
+                                const void* x2, void* y1, void* y2, const lrcc_options* opt,
+                                void* stream);
+
+/* Polarizability alpha_XY(w) per cell (Eq. 15, symmetric form), a.u., for the
+ * dipole components comps[0..ncomp) (0 = x, 1 = y, 2 = z) and frequencies
+ * omegas[0..nomega).  alpha receives c128 [nomega][ncomp][ncomp] in host memory.
+ * info (may be NULL) receives int32 [2 + ncomp]: total iterations, status of the
+ * last solve, and per component 1 if it was skipped because its integrals vanish
+ * (max |mu| < 1e-14, Sec. II.C).  Requires set_integrals and set_ground_state
+ * with Lambda.  Synchronous. */
+lrcc_status lrcc_polarizability(lrcc_problem* p, const int32_t* comps, int32_t ncomp, const double* omegas,
+                                int32_t nomega, const lrcc_options* opt, void* alpha, int32_t* info);
+
+/* Last error message of a problem (static storage owned by the handle). */
+const char* lrcc_last_error(const lrcc_problem* p);
+
+/* Release every host and device resource of a problem.  NULL is ignored. */
+void lrcc_destroy(lrcc_problem* p);
+
+/* Default options. */
+void lrcc_default_options(lrcc_options* opt);
+
+/* ---------------------------------------------------------------------------
+ * Plan introspection (host only; never touches the GPU)
+ *
+ * The Jacobian is executed as a fixed list of ops: segmented batched complex
+ * GEMMs, momentum-aware layout permutations and batched 2-D transposes over five
+ * arenas (0 fixed data, 1 input vector, 2 output vector, 3 per-vector scratch,
+ * 4 W-block workspace).  These calls expose that list so its index arithmetic can
+ * be checked on a CPU.  which: 0 ground-state program, 1 Jacobian, 2 transposed
+ * Jacobian.
+ * ------------------------------------------------------------------------- */
+lrcc_status lrcc_plan_create(const lrcc_dims* dims, int64_t ws_budget, lrcc_plan** out);
+void lrcc_plan_destroy(lrcc_plan* h);
+/* arena_sizes int64[5] (complex elements); offsets int64[10]: Loo, Lov, Lvo, Lvv,
+ * f0, t1, t2, identity, x1, x2; flops double[3]: Jacobian, ladder, W build. */
+lrcc_status lrcc_plan_info(const lrcc_plan* h, int64_t* arena_sizes, int64_t* offsets, double* flops);
+int32_t lrcc_plan_num_ops(const lrcc_plan* h, int32_t which);
+/* kind_idx_fixed int32[3]: kind (0 GEMM, 1 permute, 2 2-D transpose), table index,
+ * fixed-only flag. */
+lrcc_status lrcc_plan_op(const lrcc_plan* h, int32_t which, int32_t i, int32_t* kind_idx_fixed);
+/* ints int32[15]: M N K ta tb arA arB arC epi ep0..ep3 nbatch nseg; lds int64[3];
+ * alpha double[2]; coff int64[nbatch], sbeg int32[nbatch+1], aoff/boff int64[nseg]. */
+lrcc_status lrcc_plan_gemm(const lrcc_plan* h, int32_t idx, int32_t* ints, int64_t* lds, double* alpha,
+                           int64_t* coff, int32_t* sbeg, int64_t* aoff, int64_t* boff);
+/* ints int32[18]: src(kind nk n0..n3) dst(kind nk n0..n3) pi0..pi3 arS arD; offs int64[2]. */
+lrcc_status lrcc_plan_perm(const lrcc_plan* h, int32_t idx, int32_t* ints, int64_t* offs, double* alpha);
+/* ints int32[5]: nb R C arS arD; offs int64[2]. */
+lrcc_status lrcc_plan_btrans(const lrcc_plan* h, int32_t idx, int32_t* ints, int64_t* offs, double* alpha);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LRCC_H_ */

@@ -267,14 +267,14 @@ class RCC:
         r1, r2 = self.residual(a1, a2, h)
         f = (y1 * r1).sum() + (y2 * r2).sum()
         g1, g2 = torch.autograd.grad(f, (a1, a2), grad_outputs=torch.ones((), dtype=DT))
-        return g1.conj().detach(), self.sym(g2.conj().detach())
+        return g1.conj().resolve_conj().detach(), self.sym(g2.conj().resolve_conj().detach())
 
     def energy_grad(self, t1, t2, h=None):
         a1 = t1.detach().clone().requires_grad_(True)
         a2 = t2.detach().clone().requires_grad_(True)
         e = self.energy(a1, a2, h)
         g1, g2 = torch.autograd.grad(e, (a1, a2), grad_outputs=torch.ones((), dtype=DT))
-        return g1.conj().detach(), self.sym(g2.conj().detach())
+        return g1.conj().resolve_conj().detach(), self.sym(g2.conj().resolve_conj().detach())
 
     # -- denominators and solvers ------------------------------------------------
     def denominators(self):
@@ -373,7 +373,7 @@ def lagrangian_grad(R: RCC, t1, t2, l1, l2, h=None):
     r1, r2 = R.residual(a1, a2, h)
     f = R.energy(a1, a2, h) + (l1 * r1).sum() + (l2 * r2).sum()
     g1, g2 = torch.autograd.grad(f, (a1, a2), grad_outputs=torch.ones((), dtype=DT))
-    return g1.conj().detach(), R.sym(g2.conj().detach())
+    return g1.conj().resolve_conj().detach(), R.sym(g2.conj().resolve_conj().detach())
 
 
 def solve_lambda(R: RCC, t1, t2, tol=1e-10, maxit=200, verbose=False):

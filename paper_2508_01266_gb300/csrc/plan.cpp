@@ -1,0 +1,1058 @@
+// Plan builder: the ground-state intermediates and the Jacobian product of
+// closed-shell, k-point LR-CCSD as lists of GEMM / layout-permute ops.
+//
+// Method (Eqs. 7-8 and 13-14 of the paper, read through the supercell picture):
+//   Omega(t1, t2) = R(H~(t1), t2), where H~ = exp(-T1) H exp(T1) has DF factors
+//   L~ = (1 - tau) L (1 + tau) (tau[a,i] = t1[i,a]) and R is the closed-shell CCD-form
+//   residual of a general Hamiltonian:
+//     R2 = (ai|bj) + sum_cd t_ij^cd (ac|bd)                                  [A]
+//        + sum_kl t_kl^ab [(ki|lj) + sum_cd t_ij^cd (kc|ld)]                  [B]
+//        + P_ij^ab { -1/2 sum_kc t_kj^bc [(ki|ac) - 1/2 sum_ld t_li^ad (kd|lc)]
+//                    - sum_kc t_ki^bc [(kj|ac) - 1/2 sum_ld t_lj^ad (kd|lc)]  [C]
+//                    + 1/2 sum_kc u_jk^bc [L_aikc + 1/2 sum_ld u_il^ad L_ldkc] [D]
+//                    + sum_c t_ij^ac [f_bc - sum_kld u_kl^bd (ld|kc)]
+//                    - sum_k t_ik^ab [f_kj + sum_lcd u_lj^cd (kd|lc)] }      [E]
+//     R1 = f_ai + sum_me u_im^ae f_me + sum_mef u_im^ef (ae|mf) - sum_mne u_mn^ae (ne|mi)
+//   with u = 2t - t(a<->b), L_pqrs = 2(pq|rs) - (ps|rq), P_ij^ab Y = Y + Y(i<->j, a<->b).
+//   The Jacobian A.X = dOmega(t + hX)/dh is R linearized in t2 (X2 part) plus R
+//   evaluated with the dressed-Hamiltonian derivative dH~ = [H~, X1] (X1 part):
+//     dL~ = [L~, xi], xi[a,i] = x1[i,a]:  dL~_ai = L~_ae x_i^e - x_m^a L~_mi,
+//     dL~_mi = L~_me x_i^e, dL~_ae = -x_m^a L~_me, dL~_me = 0;
+//     df~ = [f~, xi] + sum_me x_m^e [2(pq|me) - (pe|mq)].
+// Units: the supercell picture uses L / sqrt(Nk) and s2 = t2_paper / Nk; the
+// program takes and returns vectors in the paper's normalization (Sec. II.B).
+#include "plan.h"
+
+#include <algorithm>
+#include <array>
+#include <cassert>
+#include <map>
+#include <stdexcept>
+
+namespace lrcc {
+
+static inline int md(int a, int n) { return ((a % n) + n) % n; }
+
+int64_t layout_offset(const Layout& L, int k1, int k2, int k3, int i1, int i2, int i3, int i4) {
+  const int nk = L.nk;
+  const int64_t n0 = L.n[0], n1 = L.n[1], n2 = L.n[2], n3 = L.n[3];
+  switch (L.kind) {
+    case LK_K3:
+      return (((int64_t)k1 * nk + k2) * nk + k3) * (n0 * n1 * n2 * n3) +
+             ((i1 * n1 + i2) * n2 + i3) * n3 + i4;
+    case LK_PP: {
+      int P = md(k1 + k2, nk);
+      int64_t rows = nk * n0 * n1, cols = nk * n2 * n3;
+      int64_t r = ((int64_t)k1 * n0 + i1) * n1 + i2;
+      int64_t c = ((int64_t)k3 * n2 + i3) * n3 + i4;
+      return (int64_t)P * rows * cols + r * cols + c;
+    }
+    case LK_PH: {
+      int q = md(k3 - k1, nk);
+      int k4 = md(k1 + k2 - k3, nk);
+      int64_t rows = nk * n0 * n2, cols = nk * n3 * n1;
+      int64_t r = ((int64_t)k1 * n0 + i1) * n2 + i3;
+      int64_t c = ((int64_t)k4 * n3 + i4) * n1 + i2;
+      return (int64_t)q * rows * cols + r * cols + c;
+    }
+    case LK_CH:
+      return (((int64_t)k1 * nk + k3) * nk + k2) * (n0 * n1 * n2 * n3) +
+             ((i1 * n2 + i3) * n1 + i2) * n3 + i4;
+  }
+  throw std::runtime_error("bad layout");
+}
+
+int64_t Gemm::flops() const {
+  return 8LL * M * N * K * (int64_t)aoff.size();
+}
+
+namespace {
+
+struct T4 {
+  int ar;
+  int64_t off;
+  Layout L;
+};
+
+struct B {
+  Plan& P;
+  int nk, o, v, Q;
+  explicit B(Plan& p) : P(p), nk(p.d.nk), o(p.d.o), v(p.d.v), Q(p.d.Q) {}
+
+  int64_t alloc(int ar, int64_t n) {
+    int64_t off = P.arena_size[ar];
+    n = (n + 31) / 32 * 32;  // 512-byte alignment of every buffer
+    P.arena_size[ar] += n;
+    return off;
+  }
+  T4 t4(int ar, int kind, int a, int b, int c, int d) {
+    T4 t;
+    t.ar = ar;
+    t.L.kind = kind;
+    t.L.nk = nk;
+    t.L.n[0] = a; t.L.n[1] = b; t.L.n[2] = c; t.L.n[3] = d;
+    t.off = alloc(ar, t.L.size());
+    return t;
+  }
+  T4 relayout(const T4& x, int ar, int kind) {  // same logical tensor, new buffer
+    return t4(ar, kind, x.L.n[0], x.L.n[1], x.L.n[2], x.L.n[3]);
+  }
+  static bool is_var(int ar) { return ar == AR_IN || ar == AR_OUT || ar == AR_SCR; }
+
+  void push(Program& pr, int kind, int idx, int fixed_only = 0) {
+    Op op;
+    op.kind = kind;
+    op.idx = idx;
+    op.fixed_only = fixed_only;
+    pr.ops.push_back(op);
+  }
+
+  // dst += alpha * src o pi (logical permutation)
+  void perm(Program& pr, const T4& dst, const T4& src, std::array<int, 4> pi, double ar,
+            double ai = 0.0, const char* tag = "") {
+    for (int s = 0; s < 4; ++s)
+      if (src.L.n[s] != dst.L.n[pi[s]]) throw std::runtime_error(std::string("perm dims ") + tag);
+    bool ok = ((pi[0] < 2 && pi[1] < 2 && pi[2] >= 2 && pi[3] >= 2) ||
+               (pi[0] >= 2 && pi[1] >= 2 && pi[2] < 2 && pi[3] < 2));
+    if (!ok) throw std::runtime_error(std::string("perm breaks momentum rule ") + tag);
+    Perm p;
+    p.src = src.L;
+    p.dst = dst.L;
+    for (int s = 0; s < 4; ++s) p.pi[s] = pi[s];
+    p.ar = ar;
+    p.ai = ai;
+    p.arS = src.ar;
+    p.arD = dst.ar;
+    p.offS = src.off;
+    p.offD = dst.off;
+    p.tag = tag;
+    P.perms.push_back(p);
+    push(pr, OP_PERM, (int)P.perms.size() - 1, (!is_var(src.ar) && !is_var(dst.ar)) ? 1 : 0);
+  }
+
+  void btr(Program& pr, int nb, int R, int C, int arD, int64_t offD, int arS, int64_t offS,
+           double ar, const char* tag = "") {
+    BTrans t;
+    t.nb = nb; t.R = R; t.C = C;
+    t.ar = ar; t.ai = 0.0;
+    t.arS = arS; t.arD = arD; t.offS = offS; t.offD = offD;
+    t.tag = tag;
+    P.btrans.push_back(t);
+    push(pr, OP_BTRANS, (int)P.btrans.size() - 1, (!is_var(arS) && !is_var(arD)) ? 1 : 0);
+  }
+
+  Gemm& g_new(int M, int N, int K, int ta, int tb, int64_t lda, int64_t ldb, int64_t ldc,
+              int arA, int arB, int arC, double ar, double ai, const char* tag) {
+    Gemm g;
+    g.M = M; g.N = N; g.K = K;
+    g.ta = ta; g.tb = tb;
+    g.lda = lda; g.ldb = ldb; g.ldc = ldc;
+    g.arA = arA; g.arB = arB; g.arC = arC;
+    g.ar = ar; g.ai = ai;
+    g.tag = tag;
+    g.sbeg.push_back(0);
+    P.gemms.push_back(g);
+    return P.gemms.back();
+  }
+  static void batch(Gemm& g, int64_t coff) {
+    g.coff.push_back(coff);
+    g.sbeg.push_back(g.sbeg.back());
+  }
+  static void seg(Gemm& g, int64_t aoff, int64_t boff) {
+    g.aoff.push_back(aoff);
+    g.boff.push_back(boff);
+    g.sbeg.back() += 1;
+  }
+  void g_push(Program& pr) {
+    Gemm& g = P.gemms.back();
+    // drop empty batches
+    Gemm h = g;
+    h.coff.clear();
+    h.sbeg.assign(1, 0);
+    h.aoff.clear();
+    h.boff.clear();
+    for (int b = 0; b < g.nbatch(); ++b) {
+      if (g.sbeg[b + 1] == g.sbeg[b]) continue;
+      batch(h, g.coff[b]);
+      for (int s = g.sbeg[b]; s < g.sbeg[b + 1]; ++s) seg(h, g.aoff[s], g.boff[s]);
+    }
+    g = h;
+    if (g.nbatch() == 0) {
+      P.gemms.pop_back();
+      return;
+    }
+    int nvar = (is_var(g.arA) ? 1 : 0) + (is_var(g.arB) ? 1 : 0);
+    if (nvar > 1) throw std::runtime_error("gemm with two variable operands: " + g.tag);
+    bool fixed = !is_var(g.arA) && !is_var(g.arB) && !is_var(g.arC);
+    if (!fixed && !is_var(g.arC)) throw std::runtime_error("variable gemm into fixed arena: " + g.tag);
+    push(pr, OP_GEMM, (int)P.gemms.size() - 1, fixed ? 1 : 0);
+  }
+
+  // pair-matrix geometry
+  static void pair_dims(const Layout& L, int64_t& rows, int64_t& cols) {
+    if (L.kind == LK_PP) {
+      rows = (int64_t)L.nk * L.n[0] * L.n[1];
+      cols = (int64_t)L.nk * L.n[2] * L.n[3];
+    } else if (L.kind == LK_PH) {
+      rows = (int64_t)L.nk * L.n[0] * L.n[2];
+      cols = (int64_t)L.nk * L.n[3] * L.n[1];
+    } else {
+      throw std::runtime_error("pair_dims on non-pair layout");
+    }
+  }
+  // C_g += alpha op(A_g) op(B_g) for every momentum group g
+  void pair_gemm(Program& pr, const T4& C, const T4& A, int ta, const T4& Bm, int tb, double ar,
+                 double ai, const char* tag) {
+    int64_t rA, cA, rB, cB, rC, cC;
+    pair_dims(A.L, rA, cA);
+    pair_dims(Bm.L, rB, cB);
+    pair_dims(C.L, rC, cC);
+    int64_t M = ta ? cA : rA, K = ta ? rA : cA;
+    int64_t K2 = tb ? cB : rB, N = tb ? rB : cB;
+    if (K != K2 || M != rC || N != cC || A.L.kind != C.L.kind || Bm.L.kind != C.L.kind)
+      throw std::runtime_error(std::string("pair_gemm shapes ") + tag);
+    Gemm& g = g_new((int)M, (int)N, (int)K, ta, tb, cA, cB, cC, A.ar, Bm.ar, C.ar, ar, ai, tag);
+    for (int q = 0; q < nk; ++q) {
+      batch(g, C.off + q * rC * cC);
+      seg(g, A.off + q * rA * cA, Bm.off + q * rB * cB);
+    }
+    g_push(pr);
+  }
+};
+
+}  // namespace
+
+Plan build_plan(const Dims& d, int64_t ws_budget) {
+  Plan P;
+  P.d = d;
+  B b(P);
+  const int nk = d.nk, o = d.o, v = d.v, Q = d.Q, n = o + v;
+  (void)n;
+  const int64_t o2 = (int64_t)o * o, v2 = (int64_t)v * v, ov = (int64_t)o * v;
+  auto kb3 = [&](int k1, int k2, int k3) { return md(k1 + k2 - k3, nk); };
+  const double sNk = (double)nk;
+
+  // ---------------- FIX inputs ----------------
+  // DF factor blocks [k1][k2][Q][n1][n2] in supercell units (L / sqrt(Nk))
+  auto dfsz = [&](int a, int c) { return (int64_t)nk * nk * Q * a * c; };
+  P.off_Loo = b.alloc(AR_FIX, dfsz(o, o));
+  P.off_Lov = b.alloc(AR_FIX, dfsz(o, v));
+  P.off_Lvo = b.alloc(AR_FIX, dfsz(v, o));
+  P.off_Lvv = b.alloc(AR_FIX, dfsz(v, v));
+  P.off_f0 = b.alloc(AR_FIX, (int64_t)nk * (o + v) * (o + v));  // diag(eps) per k, n x n
+  P.off_t1 = b.alloc(AR_FIX, (int64_t)nk * ov);
+  P.off_t2 = b.alloc(AR_FIX, (int64_t)nk * nk * nk * o2 * v2);  // paper units
+  P.off_idv = b.alloc(AR_FIX, o2);                               // identity o x o
+  auto DF = [&](int64_t base, int a, int c, int k1, int k2) {
+    return base + ((int64_t)k1 * nk + k2) * Q * a * c;
+  };
+  const int nn = o + v;
+  auto F0 = [&](int k, int p, int q) { return P.off_f0 + ((int64_t)k * nn + p) * nn + q; };
+  auto T1 = [&](int k) { return P.off_t1 + (int64_t)k * ov; };
+
+  Program& G = P.ground;
+  // dressed factors (ov block unchanged)
+  int64_t tLoo = b.alloc(AR_FIX, dfsz(o, o)), tLvo = b.alloc(AR_FIX, dfsz(v, o)),
+          tLvv = b.alloc(AR_FIX, dfsz(v, v));
+  int64_t Lov = P.off_Lov;
+  // Loo~ = Loo + Lov t1[k2]^T  (rows (Q,i), cols j)
+  b.perm(G, T4{AR_FIX, tLoo, Layout{LK_K3, 1, {1, 1, 1, (int)dfsz(o, o)}}},
+         T4{AR_FIX, P.off_Loo, Layout{LK_K3, 1, {1, 1, 1, (int)dfsz(o, o)}}}, {0, 1, 2, 3}, 1.0, 0.0,
+         "copy Loo");
+  {
+    Gemm& g = b.g_new(Q * o, o, v, 0, 1, v, v, o, AR_FIX, AR_FIX, AR_FIX, 1.0, 0.0, "dress oo");
+    for (int k1 = 0; k1 < nk; ++k1)
+      for (int k2 = 0; k2 < nk; ++k2) {
+        B::batch(g, DF(tLoo, o, o, k1, k2));
+        B::seg(g, DF(Lov, o, v, k1, k2), T1(k2));
+      }
+    b.g_push(G);
+  }
+  // Lvv~ = Lvv - t1[k1]^T Lov   (per Q)
+  b.perm(G, T4{AR_FIX, tLvv, Layout{LK_K3, 1, {1, 1, 1, (int)dfsz(v, v)}}},
+         T4{AR_FIX, P.off_Lvv, Layout{LK_K3, 1, {1, 1, 1, (int)dfsz(v, v)}}}, {0, 1, 2, 3}, 1.0, 0.0,
+         "copy Lvv");
+  {
+    Gemm& g = b.g_new(v, v, o, 1, 0, v, v, v, AR_FIX, AR_FIX, AR_FIX, -1.0, 0.0, "dress vv");
+    for (int k1 = 0; k1 < nk; ++k1)
+      for (int k2 = 0; k2 < nk; ++k2)
+        for (int q = 0; q < Q; ++q) {
+          B::batch(g, DF(tLvv, v, v, k1, k2) + (int64_t)q * v2);
+          B::seg(g, T1(k1), DF(Lov, o, v, k1, k2) + (int64_t)q * ov);
+        }
+    b.g_push(G);
+  }
+  // Lvo~ = Lvo + Lvv~ t1[k2]^T - t1[k1]^T Loo
+  b.perm(G, T4{AR_FIX, tLvo, Layout{LK_K3, 1, {1, 1, 1, (int)dfsz(v, o)}}},
+         T4{AR_FIX, P.off_Lvo, Layout{LK_K3, 1, {1, 1, 1, (int)dfsz(v, o)}}}, {0, 1, 2, 3}, 1.0, 0.0,
+         "copy Lvo");
+  {
+    Gemm& g = b.g_new(Q * v, o, v, 0, 1, v, v, o, AR_FIX, AR_FIX, AR_FIX, 1.0, 0.0, "dress vo a");
+    for (int k1 = 0; k1 < nk; ++k1)
+      for (int k2 = 0; k2 < nk; ++k2) {
+        B::batch(g, DF(tLvo, v, o, k1, k2));
+        B::seg(g, DF(tLvv, v, v, k1, k2), T1(k2));
+      }
+    b.g_push(G);
+    Gemm& h = b.g_new(v, o, o, 1, 0, v, o, o, AR_FIX, AR_FIX, AR_FIX, -1.0, 0.0, "dress vo b");
+    for (int k1 = 0; k1 < nk; ++k1)
+      for (int k2 = 0; k2 < nk; ++k2)
+        for (int q = 0; q < Q; ++q) {
+          B::batch(h, DF(tLvo, v, o, k1, k2) + (int64_t)q * ov);
+          B::seg(h, T1(k1), DF(P.off_Loo, o, o, k1, k2) + (int64_t)q * o2);
+        }
+    b.g_push(G);
+  }
+
+  // ---------------- Fock matrices ----------------
+  // G(L)_pq(k) = 2 sum_Q L[k,k]_pq J^Q - sum_k' sum_Qi L[k,k']_pi L[k',k]_iq,  J^Q = sum L[k',k']_ii
+  // h = f0 - G(L);  f~ = (1 - tau) h (1 + tau) + G(L~).  Blocks oo, ov, vv are needed.
+  int64_t hoo = b.alloc(AR_FIX, nk * o2), hov = b.alloc(AR_FIX, nk * ov), hvv = b.alloc(AR_FIX, nk * v2);
+  int64_t foo = b.alloc(AR_FIX, nk * o2), fov = b.alloc(AR_FIX, nk * ov), fvv = b.alloc(AR_FIX, nk * v2);
+  int64_t Jq = b.alloc(AR_FIX, Q), Jt = b.alloc(AR_FIX, Q);
+  auto fblk = [&](int64_t base, int a, int c, int k) { return base + (int64_t)k * a * c; };
+  // f0 blocks into h (h starts as f0)
+  for (int k = 0; k < nk; ++k) {
+    // oo: rows p<o, cols q<o of the n x n f0 block, copied row by row with a 1-column GEMM-free perm
+    for (int p = 0; p < o; ++p) {
+      b.perm(G, T4{AR_FIX, fblk(hoo, o, o, k) + (int64_t)p * o, Layout{LK_K3, 1, {1, 1, 1, o}}},
+             T4{AR_FIX, F0(k, p, 0), Layout{LK_K3, 1, {1, 1, 1, o}}}, {0, 1, 2, 3}, 1.0, 0.0, "f0 oo");
+      b.perm(G, T4{AR_FIX, fblk(hov, o, v, k) + (int64_t)p * v, Layout{LK_K3, 1, {1, 1, 1, v}}},
+             T4{AR_FIX, F0(k, p, o), Layout{LK_K3, 1, {1, 1, 1, v}}}, {0, 1, 2, 3}, 1.0, 0.0, "f0 ov");
+    }
+    for (int p = 0; p < v; ++p)
+      b.perm(G, T4{AR_FIX, fblk(hvv, v, v, k) + (int64_t)p * v, Layout{LK_K3, 1, {1, 1, 1, v}}},
+             T4{AR_FIX, F0(k, o + p, o), Layout{LK_K3, 1, {1, 1, 1, v}}}, {0, 1, 2, 3}, 1.0, 0.0, "f0 vv");
+  }
+  // J^Q = sum_k' sum_i L[k',k'][Q]_ii (undressed), Jt with dressed Loo~
+  auto coulomb_vec = [&](int64_t J, int64_t Loo_base, const char* tag) {
+    Gemm& g = b.g_new(Q, 1, (int)o2, 0, 0, o2, 1, 1, AR_FIX, AR_FIX, AR_FIX, 1.0, 0.0, tag);
+    B::batch(g, J);
+    for (int k = 0; k < nk; ++k) B::seg(g, DF(Loo_base, o, o, k, k), P.off_idv);
+    b.g_push(G);
+  };
+  coulomb_vec(Jq, P.off_Loo, "J");
+  coulomb_vec(Jt, tLoo, "J~");
+  // add c * G(L) block (p-range X, q-range Y) into dst
+  struct Fac { int64_t base; int a, c; };
+  auto addG = [&](int64_t dst, int a, int c, Fac Lpq, Fac Lpi, Fac Liq, int64_t J, double coef,
+                  const char* tag) {
+    // Coulomb: dst[k](p,q) += 2 coef sum_Q J[Q] L[k,k][Q](p,q)
+    Gemm& g = b.g_new(1, a * c, Q, 0, 0, Q, (int64_t)a * c, (int64_t)a * c, AR_FIX, AR_FIX, AR_FIX,
+                      2.0 * coef, 0.0, tag);
+    for (int k = 0; k < nk; ++k) {
+      B::batch(g, dst + (int64_t)k * a * c);
+      B::seg(g, J, DF(Lpq.base, Lpq.a, Lpq.c, k, k));
+    }
+    b.g_push(G);
+    // exchange: dst[k](p,q) -= coef sum_{k',Q,i} L[k,k'][Q](p,i) L[k',k][Q](i,q)
+    Gemm& h = b.g_new(a, c, o, 0, 0, o, c, c, AR_FIX, AR_FIX, AR_FIX, -coef, 0.0, tag);
+    for (int k = 0; k < nk; ++k) {
+      B::batch(h, dst + (int64_t)k * a * c);
+      for (int kp = 0; kp < nk; ++kp)
+        for (int q = 0; q < Q; ++q)
+          B::seg(h, DF(Lpi.base, Lpi.a, Lpi.c, k, kp) + (int64_t)q * a * o,
+                 DF(Liq.base, Liq.a, Liq.c, kp, k) + (int64_t)q * o * c);
+    }
+    b.g_push(G);
+  };
+  // h = f0 - G(L)
+  addG(hoo, o, o, {P.off_Loo, o, o}, {P.off_Loo, o, o}, {P.off_Loo, o, o}, Jq, -1.0, "h oo");
+  addG(hov, o, v, {P.off_Lov, o, v}, {P.off_Loo, o, o}, {P.off_Lov, o, v}, Jq, -1.0, "h ov");
+  addG(hvv, v, v, {P.off_Lvv, v, v}, {P.off_Lvo, v, o}, {P.off_Lov, o, v}, Jq, -1.0, "h vv");
+  // f~ = h~ + G(L~):  h~_ij = h_ij + h_ie t_j^e ; h~_ia = h_ia ; h~_ab = h_ab - t_m^a h_mb
+  b.perm(G, T4{AR_FIX, foo, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * o2)}}},
+         T4{AR_FIX, hoo, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * o2)}}}, {0, 1, 2, 3}, 1.0, 0.0, "h~oo");
+  b.perm(G, T4{AR_FIX, fov, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * ov)}}},
+         T4{AR_FIX, hov, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * ov)}}}, {0, 1, 2, 3}, 1.0, 0.0, "h~ov");
+  b.perm(G, T4{AR_FIX, fvv, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * v2)}}},
+         T4{AR_FIX, hvv, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * v2)}}}, {0, 1, 2, 3}, 1.0, 0.0, "h~vv");
+  {
+    Gemm& g = b.g_new(o, o, v, 0, 1, v, v, o, AR_FIX, AR_FIX, AR_FIX, 1.0, 0.0, "h~oo t");
+    for (int k = 0; k < nk; ++k) {
+      B::batch(g, fblk(foo, o, o, k));
+      B::seg(g, fblk(hov, o, v, k), T1(k));
+    }
+    b.g_push(G);
+    Gemm& h = b.g_new(v, v, o, 1, 0, v, v, v, AR_FIX, AR_FIX, AR_FIX, -1.0, 0.0, "h~vv t");
+    for (int k = 0; k < nk; ++k) {
+      B::batch(h, fblk(fvv, v, v, k));
+      B::seg(h, T1(k), fblk(hov, o, v, k));
+    }
+    b.g_push(G);
+  }
+  addG(foo, o, o, {tLoo, o, o}, {tLoo, o, o}, {tLoo, o, o}, Jt, 1.0, "G~ oo");
+  addG(fov, o, v, {Lov, o, v}, {tLoo, o, o}, {Lov, o, v}, Jt, 1.0, "G~ ov");
+  addG(fvv, v, v, {tLvv, v, v}, {tLvo, v, o}, {Lov, o, v}, Jt, 1.0, "G~ vv");
+  int64_t fovT = b.alloc(AR_FIX, nk * ov);
+  b.btr(G, nk, o, v, AR_FIX, fovT, AR_FIX, fov, 1.0, "fovT");
+
+  // ---------------- amplitude layouts (supercell units) ----------------
+  T4 t2in{AR_FIX, P.off_t2, Layout{LK_K3, nk, {o, o, v, v}}};
+  T4 Tk3 = b.t4(AR_FIX, LK_K3, o, o, v, v);
+  b.perm(G, Tk3, t2in, {0, 1, 2, 3}, 1.0 / sNk, 0.0, "T sc");
+  T4 Tpp = b.relayout(Tk3, AR_FIX, LK_PP);
+  b.perm(G, Tpp, Tk3, {0, 1, 2, 3}, 1.0, 0.0, "Tpp");
+  T4 Tc = b.relayout(Tk3, AR_FIX, LK_PH);
+  b.perm(G, Tc, Tk3, {0, 1, 3, 2}, 1.0, 0.0, "Tc");
+  T4 ud = b.relayout(Tk3, AR_FIX, LK_PH);
+  b.perm(G, ud, Tk3, {0, 1, 2, 3}, 2.0, 0.0, "ud a");
+  b.perm(G, ud, Tk3, {0, 1, 3, 2}, -1.0, 0.0, "ud b");
+  T4 uk3 = b.relayout(Tk3, AR_FIX, LK_K3);
+  b.perm(G, uk3, Tk3, {0, 1, 2, 3}, 2.0, 0.0, "uk3 a");
+  b.perm(G, uk3, Tk3, {0, 1, 3, 2}, -1.0, 0.0, "uk3 b");
+
+  // ---------------- dressed integrals from DF factors ----------------
+  // chemist GEMM: CH block (k1,k3,k2) of logical (p, r, q, s): [(p,q)][(r,s)] = sum_Q A[kp,kq](p,q) B[kr,ks](r,s)
+  auto chem = [&](Program& pr, const T4& C, int64_t Abase, int na, int nq, int64_t Bbase, int nr, int ns,
+                  int arA, int arB, double ar, const char* tag) {
+    // logical C(p, r, q, s): n = (na, nr, nq, ns); block index (kp, kq, kr), ks = kp + kr - kq
+    Gemm& g = b.g_new(na * nq, nr * ns, Q, 1, 0, (int64_t)na * nq, (int64_t)nr * ns, (int64_t)nr * ns,
+                      arA, arB, C.ar, ar, 0.0, tag);
+    for (int kp = 0; kp < nk; ++kp)
+      for (int kq = 0; kq < nk; ++kq)
+        for (int kr = 0; kr < nk; ++kr) {
+          int ks = md(kp + kr - kq, nk);
+          B::batch(g, C.off + layout_offset(C.L, kp, kr, kq, 0, 0, 0, 0));
+          B::seg(g, DF(Abase, na, nq, kp, kq), DF(Bbase, nr, ns, kr, ks));
+        }
+    b.g_push(pr);
+  };
+  // V(k,l,c,d) = (kc|ld)
+  T4 Vch = b.t4(AR_FIX, LK_CH, o, o, v, v);
+  chem(G, Vch, Lov, o, v, Lov, o, v, AR_FIX, AR_FIX, 1.0, "V ovov");
+  T4 Vpp = b.relayout(Vch, AR_FIX, LK_PP);
+  b.perm(G, Vpp, Vch, {0, 1, 2, 3}, 1.0, 0.0, "Vpp");
+  T4 Vk3 = b.relayout(Vch, AR_FIX, LK_K3);
+  b.perm(G, Vk3, Vch, {0, 1, 2, 3}, 1.0, 0.0, "Vk3");
+  // W(l,k,c,d) = (kd|lc) = V(k,l,d,c)
+  T4 Wk3 = b.relayout(Vch, AR_FIX, LK_K3);
+  b.perm(G, Wk3, Vch, {1, 0, 3, 2}, 1.0, 0.0, "Wk3");
+  // M(d,c,l,k) = (kd|lc) ; ML(d,c,l,k) = 2(ld|kc) - (lc|kd)   (PH)
+  T4 Mph = b.t4(AR_FIX, LK_PH, v, v, o, o);
+  b.perm(G, Mph, Vch, {3, 2, 0, 1}, 1.0, 0.0, "M");
+  T4 MLph = b.t4(AR_FIX, LK_PH, v, v, o, o);
+  b.perm(G, MLph, Vch, {2, 3, 0, 1}, 2.0, 0.0, "ML a");
+  b.perm(G, MLph, Vch, {2, 3, 1, 0}, -1.0, 0.0, "ML b");
+
+  // hole-hole: Whh(k,l,i,j) = (ki|lj)~ + sum_cd t_ij^cd (kc|ld)   (PP)
+  T4 Ioo = b.t4(AR_FIX, LK_CH, o, o, o, o);
+  chem(G, Ioo, tLoo, o, o, tLoo, o, o, AR_FIX, AR_FIX, 1.0, "(ki|lj)~");
+  T4 Whh = b.relayout(Ioo, AR_FIX, LK_PP);
+  b.perm(G, Whh, Ioo, {0, 1, 2, 3}, 1.0, 0.0, "Whh");
+  b.pair_gemm(G, Whh, Vpp, 0, Tpp, 1, 1.0, 0.0, "Whh += V T^T");
+
+  // ring C: WC(i,c,a,k) = (ki|ac)~ - 1/2 sum_ld t_li^ad (kd|lc)
+  T4 Ikiac = b.t4(AR_FIX, LK_CH, o, v, o, v);  // logical (k,a,i,c)
+  chem(G, Ikiac, tLoo, o, o, tLvv, v, v, AR_FIX, AR_FIX, 1.0, "(ki|ac)~");
+  T4 WC = b.t4(AR_FIX, LK_PH, o, v, v, o);
+  b.perm(G, WC, Ikiac, {3, 2, 0, 1}, 1.0, 0.0, "WC");
+  b.pair_gemm(G, WC, Tc, 0, Mph, 0, -0.5, 0.0, "WC -= 1/2 Tc M");
+  // ring D: WD(i,c,a,k) = 2(ai|kc)~ - (ac|ki)~ + 1/2 sum_ld u_il^ad L_ldkc
+  T4 Iaikc = b.t4(AR_FIX, LK_CH, v, o, o, v);  // logical (a,k,i,c)
+  chem(G, Iaikc, tLvo, v, o, Lov, o, v, AR_FIX, AR_FIX, 1.0, "(ai|kc)~");
+  T4 Iacki = b.t4(AR_FIX, LK_CH, v, o, v, o);  // logical (a,k,c,i)
+  chem(G, Iacki, tLvv, v, v, tLoo, o, o, AR_FIX, AR_FIX, 1.0, "(ac|ki)~");
+  T4 WD = b.t4(AR_FIX, LK_PH, o, v, v, o);
+  b.perm(G, WD, Iaikc, {2, 3, 0, 1}, 2.0, 0.0, "WD a");
+  b.perm(G, WD, Iacki, {2, 3, 1, 0}, -1.0, 0.0, "WD b");
+  b.pair_gemm(G, WD, ud, 0, MLph, 0, 0.5, 0.0, "WD += 1/2 ud ML");
+
+  // E intermediates: Fv[kb](b,c) = f~_bc - sum_kld u_kl^bd (ld|kc) ; Fo[kj](k,j) = f~_kj + sum_lcd u_lj^cd (kd|lc)
+  int64_t Fv = b.alloc(AR_FIX, nk * v2), Fo = b.alloc(AR_FIX, nk * o2);
+  b.perm(G, T4{AR_FIX, Fv, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * v2)}}},
+         T4{AR_FIX, fvv, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * v2)}}}, {0, 1, 2, 3}, 1.0, 0.0, "Fv=f");
+  b.perm(G, T4{AR_FIX, Fo, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * o2)}}},
+         T4{AR_FIX, foo, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * o2)}}}, {0, 1, 2, 3}, 1.0, 0.0, "Fo=f");
+  // YEv-type contraction: C[kb](b,c) += alpha sum_{kk,kl,k,l} U[kk,kl,kb](k,l)[b][d] Vk3[kl,kk,kd](l,k)[d][c]
+  auto yev = [&](Program& pr, int64_t Cb, int arC, const T4& U, double alpha, const char* tag) {
+    Gemm& g = b.g_new(v, v, v, 0, 0, v, v, v, U.ar, AR_FIX, arC, alpha, 0.0, tag);
+    for (int kbb = 0; kbb < nk; ++kbb) {
+      B::batch(g, Cb + (int64_t)kbb * v2);
+      for (int kk = 0; kk < nk; ++kk)
+        for (int kl = 0; kl < nk; ++kl) {
+          int kd = md(kk + kl - kbb, nk);
+          for (int k = 0; k < o; ++k)
+            for (int l = 0; l < o; ++l)
+              B::seg(g, U.off + layout_offset(U.L, kk, kl, kbb, k, l, 0, 0),
+                     Vk3.off + layout_offset(Vk3.L, kl, kk, kd, l, k, 0, 0));
+        }
+    }
+    b.g_push(pr);
+  };
+  // YEo-type: C[kj](k,j) += alpha sum_{kl,kc,l} Wk3[kl,kj,kc](l)[k][(c,d)] U[kl,kj,kc](l)[j][(c,d)]^T
+  auto yeo = [&](Program& pr, int64_t Cb, int arC, const T4& U, double alpha, const char* tag) {
+    Gemm& g = b.g_new(o, o, (int)v2, 0, 1, v2, v2, o, AR_FIX, U.ar, arC, alpha, 0.0, tag);
+    for (int kj = 0; kj < nk; ++kj) {
+      B::batch(g, Cb + (int64_t)kj * o2);
+      for (int kl = 0; kl < nk; ++kl)
+        for (int kc = 0; kc < nk; ++kc)
+          for (int l = 0; l < o; ++l)
+            B::seg(g, Wk3.off + layout_offset(Wk3.L, kl, kj, kc, l, 0, 0, 0),
+                   U.off + layout_offset(U.L, kl, kj, kc, l, 0, 0, 0));
+    }
+    b.g_push(pr);
+  };
+  yev(G, Fv, AR_FIX, uk3, -1.0, "Fv -= u V");
+  yeo(G, Fo, AR_FIX, uk3, 1.0, "Fo += W u");
+  // G_in = Fo(n,i) - f~(n,i) ; H_af = f~(a,f) - Fv(a,f)
+  int64_t Gm = b.alloc(AR_FIX, nk * o2), Hm = b.alloc(AR_FIX, nk * v2);
+  b.perm(G, T4{AR_FIX, Gm, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * o2)}}},
+         T4{AR_FIX, Fo, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * o2)}}}, {0, 1, 2, 3}, 1.0, 0.0, "G a");
+  b.perm(G, T4{AR_FIX, Gm, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * o2)}}},
+         T4{AR_FIX, foo, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * o2)}}}, {0, 1, 2, 3}, -1.0, 0.0, "G b");
+  b.perm(G, T4{AR_FIX, Hm, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * v2)}}},
+         T4{AR_FIX, fvv, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * v2)}}}, {0, 1, 2, 3}, 1.0, 0.0, "H a");
+  b.perm(G, T4{AR_FIX, Hm, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * v2)}}},
+         T4{AR_FIX, Fv, Layout{LK_K3, 1, {1, 1, 1, (int)(nk * v2)}}}, {0, 1, 2, 3}, -1.0, 0.0, "H b");
+  // Lvv~ with the inner matrix transposed: LvvT[k1][k2][Q][e][a]
+  int64_t LvvT = b.alloc(AR_FIX, dfsz(v, v));
+  b.btr(G, nk * nk * Q, v, v, AR_FIX, LvvT, AR_FIX, tLvv, 1.0, "LvvT");
+
+  // ---------------- W-block workspace and ladder chunks ----------------
+  // W(P,ka,kc)[(a,b)][(c,d)] = sum_Q A[ka,kc][Q](a,c) B[kb,kd][Q](b,d)  (kb = P-ka, kd = P-kc)
+  struct Tri { int P, ka, kc; };
+  std::vector<Tri> tris;
+  for (int Pm = 0; Pm < nk; ++Pm)
+    for (int ka = 0; ka < nk; ++ka)
+      for (int kc = 0; kc < nk; ++kc) tris.push_back({Pm, ka, kc});
+  const int64_t wblk_max = std::max<int64_t>(v2 * v2, ov * v2);
+  int64_t per_chunk = std::max<int64_t>(1, ws_budget / wblk_max);
+  per_chunk = std::min<int64_t>(per_chunk, (int64_t)tris.size());
+  P.ws_limit = per_chunk;
+  P.arena_size[AR_WS] = per_chunk * wblk_max;
+  // ladder over chunks: build (fixed-only) then contract.  Rows: all (ki,i,j) of the PP matrix.
+  auto ladder = [&](Program& pr, const T4& Cpp, int64_t Afac, int na, const T4& Xpp, double alpha,
+                    const char* tag, double* flop_acc, double* build_acc) {
+    // Cpp: logical (i,j,a,b) with a in [0,na); Xpp: logical (i,j,c,d)
+    const int64_t rowsX = (int64_t)nk * o2, colsX = (int64_t)nk * v2;
+    const int64_t colsC = (int64_t)nk * na * v;
+    const int64_t wsz = (int64_t)na * v * v2;
+    for (size_t c0 = 0; c0 < tris.size(); c0 += per_chunk) {
+      size_t c1 = std::min(tris.size(), c0 + (size_t)per_chunk);
+      Gemm& g = b.g_new(na * v, (int)v2, Q, 1, 0, (int64_t)na * v, v2, 0, AR_FIX, AR_FIX, AR_WS, 1.0, 0.0,
+                        "W build");
+      g.epi = 1;
+      g.ep[0] = na; g.ep[1] = v; g.ep[2] = v; g.ep[3] = v;
+      for (size_t t = c0; t < c1; ++t) {
+        const Tri& tr = tris[t];
+        int kbb = md(tr.P - tr.ka, nk), kd = md(tr.P - tr.kc, nk);
+        B::batch(g, (int64_t)(t - c0) * wsz);
+        B::seg(g, DF(Afac, na, v, tr.ka, tr.kc), DF(tLvv, v, v, kbb, kd));
+      }
+      if (build_acc) *build_acc += (double)g.flops();
+      b.g_push(pr);
+      // contraction: C_P[:, ka] += alpha X_P[:, kc] W^T, grouped by (P, ka)
+      Gemm& h = b.g_new((int)rowsX, na * v, (int)v2, 0, 1, colsX, v2, colsC, Xpp.ar, AR_WS, Cpp.ar, alpha,
+                        0.0, tag);
+      std::map<std::pair<int, int>, std::vector<size_t>> grp;
+      for (size_t t = c0; t < c1; ++t) grp[{tris[t].P, tris[t].ka}].push_back(t);
+      for (auto& kv : grp) {
+        int Pm = kv.first.first, ka = kv.first.second;
+        B::batch(h, Cpp.off + (int64_t)Pm * rowsX * colsC + (int64_t)ka * na * v);
+        for (size_t t : kv.second)
+          B::seg(h, Xpp.off + (int64_t)Pm * rowsX * colsX + (int64_t)tris[t].kc * v2, (int64_t)(t - c0) * wsz);
+      }
+      if (flop_acc) *flop_acc += (double)h.flops();
+      b.g_push(pr);
+    }
+  };
+  // Z(i,j,m,b) = sum_cd t_ij^cd (mc|bd)~   (PP), then K3
+  T4 Zpp = b.t4(AR_FIX, LK_PP, o, o, o, v);
+  ladder(G, Zpp, Lov, o, Tpp, 1.0, "Z ladder", nullptr, nullptr);
+  T4 Zk3 = b.relayout(Zpp, AR_FIX, LK_K3);
+  b.perm(G, Zk3, Zpp, {0, 1, 2, 3}, 1.0, 0.0, "Zk3");
+
+  // =====================================================================
+  // Jacobian program: IN (x1 paper, x2 paper) -> OUT (y1, y2 paper)
+  // =====================================================================
+  Program& J = P.jac;
+  P.off_x1 = b.alloc(AR_IN, nk * ov);
+  P.off_x2 = b.alloc(AR_IN, nk * (int64_t)nk * nk * o2 * v2);
+  if (b.alloc(AR_OUT, nk * ov) != P.off_x1 || b.alloc(AR_OUT, nk * (int64_t)nk * nk * o2 * v2) != P.off_x2)
+    throw std::runtime_error("IN/OUT layouts differ");
+  auto X1 = [&](int k) { return P.off_x1 + (int64_t)k * ov; };  // IN
+  auto Y1 = [&](int k) { return P.off_x1 + (int64_t)k * ov; };  // OUT
+  T4 xin{AR_IN, P.off_x2, Layout{LK_K3, nk, {o, o, v, v}}};
+  T4 yout{AR_OUT, P.off_x2, Layout{LK_K3, nk, {o, o, v, v}}};
+
+  // symmetrized input in supercell units: xs = (x + S x) / (2 Nk)
+  T4 xs = b.t4(AR_SCR, LK_K3, o, o, v, v);
+  b.perm(J, xs, xin, {0, 1, 2, 3}, 0.5 / sNk, 0.0, "xs a");
+  b.perm(J, xs, xin, {1, 0, 3, 2}, 0.5 / sNk, 0.0, "xs b");
+  T4 xpp = b.relayout(xs, AR_SCR, LK_PP);
+  b.perm(J, xpp, xs, {0, 1, 2, 3}, 1.0, 0.0, "xpp");
+  T4 xc = b.relayout(xs, AR_SCR, LK_PH);
+  b.perm(J, xc, xs, {0, 1, 3, 2}, 1.0, 0.0, "xc");
+  T4 Ud = b.relayout(xs, AR_SCR, LK_PH);
+  b.perm(J, Ud, xs, {0, 1, 2, 3}, 2.0, 0.0, "Ud a");
+  b.perm(J, Ud, xs, {0, 1, 3, 2}, -1.0, 0.0, "Ud b");
+  T4 Uk3 = b.relayout(xs, AR_SCR, LK_K3);
+  b.perm(J, Uk3, xs, {0, 1, 2, 3}, 2.0, 0.0, "Uk3 a");
+  b.perm(J, Uk3, xs, {0, 1, 3, 2}, -1.0, 0.0, "Uk3 b");
+
+  T4 r = b.t4(AR_SCR, LK_K3, o, o, v, v);     // doubles accumulator before (1 + S)
+  T4 rpp = b.t4(AR_SCR, LK_PP, o, o, v, v);   // symmetric terms (weight 1/2)
+  T4 Zc = b.t4(AR_SCR, LK_PH, o, o, v, v);    // ring C product
+  T4 Zd = b.t4(AR_SCR, LK_PH, o, o, v, v);    // ring D product
+
+  // [A] ladder
+  ladder(J, rpp, tLvv, v, xpp, 0.5, "ladder", &P.ladder_flops, &P.wbuild_flops);
+  // [B] hole-hole: rpp += 1/2 Whh^T xpp ; Yhh = V xpp^T ; rpp += 1/2 Yhh^T Tpp
+  b.pair_gemm(J, rpp, Whh, 1, xpp, 0, 0.5, 0.0, "hh");
+  T4 Yhh = b.t4(AR_SCR, LK_PP, o, o, o, o);
+  b.pair_gemm(J, Yhh, Vpp, 0, xpp, 1, 1.0, 0.0, "Yhh");
+  b.pair_gemm(J, rpp, Yhh, 1, Tpp, 0, 0.5, 0.0, "hh quad");
+  // [C] ring: Zc = WC xc - 1/2 (xc M) Tc
+  T4 YC = b.t4(AR_SCR, LK_PH, o, v, v, o);
+  b.pair_gemm(J, YC, xc, 0, Mph, 0, 1.0, 0.0, "YC");
+  b.pair_gemm(J, Zc, WC, 0, xc, 0, 1.0, 0.0, "ring C");
+  b.pair_gemm(J, Zc, YC, 0, Tc, 0, -0.5, 0.0, "ring C quad");
+  // [D] ring: Zd = 1/2 WD Ud + 1/4 (Ud ML) ud
+  T4 YD = b.t4(AR_SCR, LK_PH, o, v, v, o);
+  b.pair_gemm(J, YD, Ud, 0, MLph, 0, 1.0, 0.0, "YD");
+  b.pair_gemm(J, Zd, WD, 0, Ud, 0, 0.5, 0.0, "ring D");
+  b.pair_gemm(J, Zd, YD, 0, ud, 0, 0.25, 0.0, "ring D quad");
+  // [E] Fock-like terms in K3 blocks
+  auto e_vv = [&](Program& pr, const T4& A, int64_t Bvv, int arB, double alpha, const char* tag) {
+    // r[ki,kj,ka](ij a, b) += alpha sum_c A[ki,kj,ka](ij a, c) Bvv[kb](b, c)
+    Gemm& g = b.g_new((int)(o2 * v), v, v, 0, 1, v, v, v, A.ar, arB, AR_SCR, alpha, 0.0, tag);
+    for (int ki = 0; ki < nk; ++ki)
+      for (int kj = 0; kj < nk; ++kj)
+        for (int ka = 0; ka < nk; ++ka) {
+          int kbb = kb3(ki, kj, ka);
+          B::batch(g, r.off + layout_offset(r.L, ki, kj, ka, 0, 0, 0, 0));
+          B::seg(g, A.off + layout_offset(A.L, ki, kj, ka, 0, 0, 0, 0), Bvv + (int64_t)kbb * v2);
+        }
+    b.g_push(pr);
+  };
+  auto e_oo = [&](Program& pr, const T4& Bx, int64_t Aoo, int arA, double alpha, const char* tag) {
+    // r[ki,kj,ka](i, j, ab) += alpha sum_k Aoo[kj](k, j) Bx[ki,kj,ka](i, k, ab)
+    Gemm& g = b.g_new(o, (int)v2, o, 1, 0, o, v2, v2, arA, Bx.ar, AR_SCR, alpha, 0.0, tag);
+    for (int ki = 0; ki < nk; ++ki)
+      for (int kj = 0; kj < nk; ++kj)
+        for (int ka = 0; ka < nk; ++ka)
+          for (int i = 0; i < o; ++i) {
+            B::batch(g, r.off + layout_offset(r.L, ki, kj, ka, i, 0, 0, 0));
+            B::seg(g, Aoo + (int64_t)kj * o2, Bx.off + layout_offset(Bx.L, ki, kj, ka, i, 0, 0, 0));
+          }
+    b.g_push(pr);
+  };
+  e_vv(J, xs, Fv, AR_FIX, 1.0, "E vv");
+  e_oo(J, xs, Fo, AR_FIX, -1.0, "E oo");
+  int64_t YEv = b.alloc(AR_SCR, nk * v2), YEo = b.alloc(AR_SCR, nk * o2);
+  yev(J, YEv, AR_SCR, Uk3, 1.0, "YEv");
+  yeo(J, YEo, AR_SCR, Uk3, 1.0, "YEo");
+  e_vv(J, Tk3, YEv, AR_SCR, -1.0, "E vv quad");
+  e_oo(J, Tk3, YEo, AR_SCR, -1.0, "E oo quad");
+
+  // singles from X2: y1 += Ud_0 fovT + sum_mef U (ae|mf) - sum_mne U (ne|mi)
+  {
+    Gemm& g = b.g_new((int)(nk * ov), 1, (int)(nk * ov), 0, 0, nk * ov, 1, 1, AR_SCR, AR_FIX, AR_OUT, 1.0,
+                      0.0, "S1");
+    B::batch(g, Y1(0));
+    B::seg(g, Ud.off, fovT);  // q = 0 block of Ud
+    b.g_push(J);
+  }
+  // VQ[k1][k2][i][e][Q] = sum_{k,n} U[k1,k,k2](i,n)[e][f] Lov[k,kf][Q](n,f)^T
+  int64_t VQ = b.alloc(AR_SCR, (int64_t)nk * nk * ov * Q);
+  {
+    Gemm& g = b.g_new(v, Q, v, 0, 1, v, ov, Q, AR_SCR, AR_FIX, AR_SCR, 1.0, 0.0, "VQ");
+    for (int k1 = 0; k1 < nk; ++k1)
+      for (int k2 = 0; k2 < nk; ++k2)
+        for (int i = 0; i < o; ++i) {
+          B::batch(g, VQ + (((int64_t)k1 * nk + k2) * o + i) * v * Q);
+          for (int k = 0; k < nk; ++k) {
+            int kf = md(k1 + k - k2, nk);
+            for (int nn2 = 0; nn2 < o; ++nn2)
+              B::seg(g, Uk3.off + layout_offset(Uk3.L, k1, k, k2, i, nn2, 0, 0),
+                     DF(Lov, o, v, k, kf) + (int64_t)nn2 * v);
+          }
+        }
+    b.g_push(J);
+  }
+  {
+    // y1[ki](i,a) += sum_{ke,e,Q} VQ[ki][ke][i][e][Q] LvvT[ki,ke][Q][e][a]
+    Gemm& g = b.g_new(o, v, Q, 0, 0, (int64_t)v * Q, v2, v, AR_SCR, AR_FIX, AR_OUT, 1.0, 0.0, "S2");
+    for (int ki = 0; ki < nk; ++ki) {
+      B::batch(g, Y1(ki));
+      for (int ke = 0; ke < nk; ++ke)
+        for (int e = 0; e < v; ++e)
+          B::seg(g, VQ + ((int64_t)ki * nk + ke) * o * v * Q + (int64_t)e * Q,
+                 DF(LvvT, v, v, ki, ke) + (int64_t)e * v);
+    }
+    b.g_push(J);
+    // y1[ki](i,a) -= sum_{km,m,Q} Loo~[km,ki][Q](m,i) VQ[km][ki][m][a][Q]
+    Gemm& h = b.g_new(o, v, Q, 1, 1, o2, Q, v, AR_FIX, AR_SCR, AR_OUT, -1.0, 0.0, "S3");
+    for (int ki = 0; ki < nk; ++ki) {
+      B::batch(h, Y1(ki));
+      for (int km = 0; km < nk; ++km)
+        for (int m = 0; m < o; ++m)
+          B::seg(h, DF(tLoo, o, o, km, ki) + (int64_t)m * o, VQ + (((int64_t)km * nk + ki) * o + m) * v * Q);
+    }
+    b.g_push(J);
+  }
+
+  // ---------------- X1 part ----------------
+  int64_t dLvo = b.alloc(AR_SCR, dfsz(v, o)), dLoo = b.alloc(AR_SCR, dfsz(o, o)),
+          dLvv = b.alloc(AR_SCR, dfsz(v, v)), Ey = b.alloc(AR_SCR, dfsz(v, o));
+  {
+    // dLvo = Lvv~ x[k2]^T - x[k1]^T Loo~
+    Gemm& g = b.g_new(Q * v, o, v, 0, 1, v, v, o, AR_FIX, AR_IN, AR_SCR, 1.0, 0.0, "dLvo a");
+    for (int k1 = 0; k1 < nk; ++k1)
+      for (int k2 = 0; k2 < nk; ++k2) {
+        B::batch(g, DF(dLvo, v, o, k1, k2));
+        B::seg(g, DF(tLvv, v, v, k1, k2), X1(k2));
+      }
+    b.g_push(J);
+    Gemm& h = b.g_new(v, o, o, 1, 0, v, o, o, AR_IN, AR_FIX, AR_SCR, -1.0, 0.0, "dLvo b");
+    for (int k1 = 0; k1 < nk; ++k1)
+      for (int k2 = 0; k2 < nk; ++k2)
+        for (int q = 0; q < Q; ++q) {
+          B::batch(h, DF(dLvo, v, o, k1, k2) + (int64_t)q * ov);
+          B::seg(h, X1(k1), DF(tLoo, o, o, k1, k2) + (int64_t)q * o2);
+        }
+    b.g_push(J);
+    // dLoo = Lov x[k2]^T
+    Gemm& g2 = b.g_new(Q * o, o, v, 0, 1, v, v, o, AR_FIX, AR_IN, AR_SCR, 1.0, 0.0, "dLoo");
+    for (int k1 = 0; k1 < nk; ++k1)
+      for (int k2 = 0; k2 < nk; ++k2) {
+        B::batch(g2, DF(dLoo, o, o, k1, k2));
+        B::seg(g2, DF(Lov, o, v, k1, k2), X1(k2));
+      }
+    b.g_push(J);
+    // dLvv = -x[k1]^T Lov
+    Gemm& g3 = b.g_new(v, v, o, 1, 0, v, v, v, AR_IN, AR_FIX, AR_SCR, -1.0, 0.0, "dLvv");
+    for (int k1 = 0; k1 < nk; ++k1)
+      for (int k2 = 0; k2 < nk; ++k2)
+        for (int q = 0; q < Q; ++q) {
+          B::batch(g3, DF(dLvv, v, v, k1, k2) + (int64_t)q * v2);
+          B::seg(g3, X1(k1), DF(Lov, o, v, k1, k2) + (int64_t)q * ov);
+        }
+    b.g_push(J);
+    // Ey[k1,k2][Q](e,j) = sum_m x[k1](m,e) Loo~[k1,k2][Q](m,j)
+    Gemm& g4 = b.g_new(v, o, o, 1, 0, v, o, o, AR_IN, AR_FIX, AR_SCR, 1.0, 0.0, "Ey");
+    for (int k1 = 0; k1 < nk; ++k1)
+      for (int k2 = 0; k2 < nk; ++k2)
+        for (int q = 0; q < Q; ++q) {
+          B::batch(g4, DF(Ey, v, o, k1, k2) + (int64_t)q * ov);
+          B::seg(g4, X1(k1), DF(tLoo, o, o, k1, k2) + (int64_t)q * o2);
+        }
+    b.g_push(J);
+  }
+  // (11) (ai|bj)' : logical (a,b,i,j) in CH, into r with weight 1/2
+  {
+    T4 Iai = b.t4(AR_SCR, LK_CH, v, v, o, o);
+    chem(J, Iai, dLvo, v, o, tLvo, v, o, AR_SCR, AR_FIX, 1.0, "(ai|bj)' a");
+    chem(J, Iai, tLvo, v, o, dLvo, v, o, AR_FIX, AR_SCR, 1.0, "(ai|bj)' b");
+    b.perm(J, r, Iai, {2, 3, 0, 1}, 0.5, 0.0, "(ai|bj)' -> r");
+  }
+  // (12) A' : r[ki,kj,ka](ij)[a][b] -= sum_m x[ka](m,a) Z[ki,kj,ka](ij)[m][b]
+  {
+    Gemm& g = b.g_new(v, v, o, 1, 0, v, v, v, AR_IN, AR_FIX, AR_SCR, -1.0, 0.0, "A'");
+    for (int ki = 0; ki < nk; ++ki)
+      for (int kj = 0; kj < nk; ++kj)
+        for (int ka = 0; ka < nk; ++ka)
+          for (int ij = 0; ij < o2; ++ij) {
+            B::batch(g, r.off + layout_offset(r.L, ki, kj, ka, 0, 0, 0, 0) + (int64_t)ij * v2);
+            B::seg(g, X1(ka), Zk3.off + layout_offset(Zk3.L, ki, kj, ka, 0, 0, 0, 0) + (int64_t)ij * ov);
+          }
+    b.g_push(J);
+  }
+  // (13) B' : (ki|lj)' logical (k,l,i,j) -> PP ; rpp += 1/2 I^T Tpp
+  {
+    T4 Ioox = b.t4(AR_SCR, LK_CH, o, o, o, o);
+    chem(J, Ioox, dLoo, o, o, tLoo, o, o, AR_SCR, AR_FIX, 1.0, "(ki|lj)' a");
+    chem(J, Ioox, tLoo, o, o, dLoo, o, o, AR_FIX, AR_SCR, 1.0, "(ki|lj)' b");
+    T4 Ipp = b.relayout(Ioox, AR_SCR, LK_PP);
+    b.perm(J, Ipp, Ioox, {0, 1, 2, 3}, 1.0, 0.0, "(ki|lj)' pp");
+    b.pair_gemm(J, rpp, Ipp, 1, Tpp, 0, 0.5, 0.0, "B'");
+  }
+  // (14) C' : (ki|ac)' logical (k,a,i,c) -> WCx (PH (i,c,a,k)) ; Zc += WCx Tc
+  {
+    T4 Ix = b.t4(AR_SCR, LK_CH, o, v, o, v);
+    chem(J, Ix, dLoo, o, o, tLvv, v, v, AR_SCR, AR_FIX, 1.0, "(ki|ac)' a");
+    chem(J, Ix, tLoo, o, o, dLvv, v, v, AR_FIX, AR_SCR, 1.0, "(ki|ac)' b");
+    T4 WCx = b.t4(AR_SCR, LK_PH, o, v, v, o);
+    b.perm(J, WCx, Ix, {3, 2, 0, 1}, 1.0, 0.0, "WCx");
+    b.pair_gemm(J, Zc, WCx, 0, Tc, 0, 1.0, 0.0, "C'");
+  }
+  // (15) D' : 2(ai|kc)' - (ac|ki)' -> WDx ; Zd += 1/2 WDx ud
+  {
+    T4 Ia = b.t4(AR_SCR, LK_CH, v, o, o, v);  // (a,k,i,c)
+    chem(J, Ia, dLvo, v, o, Lov, o, v, AR_SCR, AR_FIX, 1.0, "(ai|kc)'");
+    T4 Ib = b.t4(AR_SCR, LK_CH, v, o, v, o);  // (a,k,c,i)
+    chem(J, Ib, dLvv, v, v, tLoo, o, o, AR_SCR, AR_FIX, 1.0, "(ac|ki)' a");
+    chem(J, Ib, tLvv, v, v, dLoo, o, o, AR_FIX, AR_SCR, 1.0, "(ac|ki)' b");
+    T4 WDx = b.t4(AR_SCR, LK_PH, o, v, v, o);
+    b.perm(J, WDx, Ia, {2, 3, 0, 1}, 2.0, 0.0, "WDx a");
+    b.perm(J, WDx, Ib, {2, 3, 1, 0}, -1.0, 0.0, "WDx b");
+    b.pair_gemm(J, Zd, WDx, 0, ud, 0, 0.5, 0.0, "D'");
+  }
+  // Coulomb vector of x1: Jx[Q] = sum_k sum_(m,e) Lov[k,k][Q](m,e) x1[k](m,e)
+  int64_t Jx = b.alloc(AR_SCR, Q);
+  {
+    Gemm& g = b.g_new(Q, 1, (int)ov, 0, 0, ov, 1, 1, AR_FIX, AR_IN, AR_SCR, 1.0, 0.0, "Jx");
+    B::batch(g, Jx);
+    for (int k = 0; k < nk; ++k) B::seg(g, DF(Lov, o, v, k, k), X1(k));
+    b.g_push(J);
+  }
+  // derivative Fock blocks f'vv[k](b,c), f'oo[k](k,j), f'vo[k](a,i), f'ov[k](m,e)
+  int64_t dfvv = b.alloc(AR_SCR, nk * v2), dfoo = b.alloc(AR_SCR, nk * o2), dfvo = b.alloc(AR_SCR, nk * ov),
+          dfov = b.alloc(AR_SCR, nk * ov), dfovT = b.alloc(AR_SCR, nk * ov);
+  auto coul = [&](int64_t dst, int a, int c, int64_t Lbase, int la, int lc, double alpha, const char* tag) {
+    Gemm& g = b.g_new(1, a * c, Q, 0, 0, Q, (int64_t)a * c, (int64_t)a * c, AR_SCR, AR_FIX, AR_SCR, alpha, 0.0,
+                      tag);
+    for (int k = 0; k < nk; ++k) {
+      B::batch(g, dst + (int64_t)k * a * c);
+      B::seg(g, Jx, DF(Lbase, la, lc, k, k));
+    }
+    b.g_push(J);
+  };
+  coul(dfvv, v, v, tLvv, v, v, 2.0, "f'vv J");
+  coul(dfoo, o, o, tLoo, o, o, 2.0, "f'oo J");
+  coul(dfvo, v, o, tLvo, v, o, 2.0, "f'vo J");
+  coul(dfov, o, v, Lov, o, v, 2.0, "f'ov J");
+  // exchange parts: C[k](p,q) += alpha sum_{k',Q} A[k,k'][Q](p,e) Bx[k',k][Q](e,q)
+  auto exch = [&](int64_t dst, int a, int c, int e, int64_t Abase, int arA, int64_t Bbase, int arB, double alpha,
+                  const char* tag) {
+    Gemm& g = b.g_new(a, c, e, 0, 0, e, c, c, arA, arB, AR_SCR, alpha, 0.0, tag);
+    for (int k = 0; k < nk; ++k) {
+      B::batch(g, dst + (int64_t)k * a * c);
+      for (int kp = 0; kp < nk; ++kp)
+        for (int q = 0; q < Q; ++q)
+          B::seg(g, Abase + (((int64_t)k * nk + kp) * Q + q) * a * e, Bbase + (((int64_t)kp * nk + k) * Q + q) * e * c);
+    }
+    b.g_push(J);
+  };
+  // f'vv: - sum_me x_m^e (be|mc) = + sum Lvv~[kb,km](b,e) dLvv[km,kb](e,c)
+  exch(dfvv, v, v, v, tLvv, AR_FIX, dLvv, AR_SCR, 1.0, "f'vv K");
+  // f'oo: - sum_me x_m^e (ke|mj) = - sum Lov[kj,km](k,e) Ey[km,kj](e,j)
+  exch(dfoo, o, o, v, Lov, AR_FIX, Ey, AR_SCR, -1.0, "f'oo K");
+  // f'vo: - sum_me x_m^e (ae|mi) = - sum Lvv~[k,km](a,e) Ey[km,k](e,i)
+  exch(dfvo, v, o, v, tLvv, AR_FIX, Ey, AR_SCR, -1.0, "f'vo K");
+  // f'ov: - sum_nf x_n^f (mf|ne) = + sum Lov[km,kn](m,f) dLvv[kn,km](f,e)
+  exch(dfov, o, v, v, Lov, AR_FIX, dLvv, AR_SCR, 1.0, "f'ov K");
+  // commutator parts: f'vv -= x[kb]^T f~ov ; f'oo += f~ov x^T
+  {
+    Gemm& g = b.g_new(v, v, o, 1, 0, v, v, v, AR_IN, AR_FIX, AR_SCR, -1.0, 0.0, "f'vv [f,xi]");
+    for (int k = 0; k < nk; ++k) {
+      B::batch(g, dfvv + (int64_t)k * v2);
+      B::seg(g, X1(k), fblk(fov, o, v, k));
+    }
+    b.g_push(J);
+    Gemm& h = b.g_new(o, o, v, 0, 1, v, v, o, AR_FIX, AR_IN, AR_SCR, 1.0, 0.0, "f'oo [f,xi]");
+    for (int k = 0; k < nk; ++k) {
+      B::batch(h, dfoo + (int64_t)k * o2);
+      B::seg(h, fblk(fov, o, v, k), X1(k));
+    }
+    b.g_push(J);
+  }
+  // (16) E' : r += sum_c T_ij^ac f'_bc - sum_k T_ik^ab f'_kj
+  e_vv(J, Tk3, dfvv, AR_SCR, 1.0, "E' vv");
+  e_oo(J, Tk3, dfoo, AR_SCR, -1.0, "E' oo");
+  // (17) singles from X1
+  {
+    // sum_e f~vv[k](a,e) x(i,e) -> y1[k](i,a)
+    Gemm& g = b.g_new(o, v, v, 0, 1, v, v, v, AR_IN, AR_FIX, AR_OUT, 1.0, 0.0, "y1 f x");
+    for (int k = 0; k < nk; ++k) {
+      B::batch(g, Y1(k));
+      B::seg(g, X1(k), fblk(fvv, v, v, k));
+    }
+    b.g_push(J);
+    // - sum_m f~oo[k](m,i) x(m,a)
+    Gemm& h = b.g_new(o, v, o, 1, 0, o, v, v, AR_FIX, AR_IN, AR_OUT, -1.0, 0.0, "y1 x f");
+    for (int k = 0; k < nk; ++k) {
+      B::batch(h, Y1(k));
+      B::seg(h, fblk(foo, o, o, k), X1(k));
+    }
+    b.g_push(J);
+    // - sum_n G[k](n,i) x(n,a)
+    Gemm& h2 = b.g_new(o, v, o, 1, 0, o, v, v, AR_FIX, AR_IN, AR_OUT, -1.0, 0.0, "y1 G x");
+    for (int k = 0; k < nk; ++k) {
+      B::batch(h2, Y1(k));
+      B::seg(h2, Gm + (int64_t)k * o2, X1(k));
+    }
+    b.g_push(J);
+    // - sum_f x(i,f) H[k](a,f)
+    Gemm& h3 = b.g_new(o, v, v, 0, 1, v, v, v, AR_IN, AR_FIX, AR_OUT, -1.0, 0.0, "y1 x H");
+    for (int k = 0; k < nk; ++k) {
+      B::batch(h3, Y1(k));
+      B::seg(h3, X1(k), Hm + (int64_t)k * v2);
+    }
+    b.g_push(J);
+  }
+  b.btr(J, nk, v, o, AR_OUT, Y1(0), AR_SCR, dfvo, 1.0, "f'vo -> y1");
+  b.btr(J, nk, o, v, AR_SCR, dfovT, AR_SCR, dfov, 1.0, "f'ov^T");
+  {
+    // y1 += ud_0 f'ovT   (sum_me u_im^ae f'_me)
+    Gemm& g = b.g_new((int)(nk * ov), 1, (int)(nk * ov), 0, 0, nk * ov, 1, 1, AR_FIX, AR_SCR, AR_OUT, 1.0, 0.0,
+                      "y1 u f'");
+    B::batch(g, Y1(0));
+    B::seg(g, ud.off, dfovT);
+    b.g_push(J);
+  }
+
+  // ---------------- assemble the doubles output ----------------
+  b.perm(J, r, rpp, {0, 1, 2, 3}, 1.0, 0.0, "rpp -> r");
+  b.perm(J, r, Zc, {0, 1, 2, 3}, -0.5, 0.0, "Zc -> r");
+  b.perm(J, r, Zc, {0, 1, 3, 2}, -1.0, 0.0, "Zc sw -> r");
+  b.perm(J, r, Zd, {0, 1, 2, 3}, 1.0, 0.0, "Zd -> r");
+  b.perm(J, yout, r, {0, 1, 2, 3}, sNk, 0.0, "y2 a");
+  b.perm(J, yout, r, {1, 0, 3, 2}, sNk, 0.0, "y2 b");
+
+  double tot = 0;
+  for (const Op& op : J.ops)
+    if (op.kind == OP_GEMM) tot += (double)P.gemms[op.idx].flops();
+  P.jac_flops = tot;
+  return P;
+}
+
+// ---------------------------------------------------------------------------
+// transposition
+// ---------------------------------------------------------------------------
+static bool var_arena(int ar) { return ar == AR_IN || ar == AR_OUT || ar == AR_SCR; }
+
+Program transpose_program(Plan& P, const Program& fwd) {
+  Program out;
+  std::vector<Op> rev;
+  // fixed-only ops (W builds) must stay ahead of the contraction that uses them:
+  // walk backwards, and when a variable GEMM reads the WS arena, emit the fixed
+  // build op(s) that precede it in the forward program first.
+  std::vector<int> pending;  // index in fwd of fixed-only ops not yet emitted
+  for (int i = (int)fwd.ops.size() - 1; i >= 0; --i) {
+    const Op& op = fwd.ops[i];
+    if (op.fixed_only) continue;
+    if (op.kind == OP_GEMM) {
+      const Gemm& g = P.gemms[op.idx];
+      if (g.arA == AR_WS || g.arB == AR_WS) {
+        // find the nearest preceding fixed-only op (its W build)
+        for (int j = i - 1; j >= 0; --j)
+          if (fwd.ops[j].fixed_only) {
+            out.ops.push_back(fwd.ops[j]);
+            break;
+          }
+      }
+      Gemm g2 = g;  // copy before push_back invalidates
+      Gemm t;
+      t.ar = g2.ar;
+      t.ai = g2.ai;
+      t.epi = 0;
+      t.tag = g2.tag + "^T";
+      bool bvar = var_arena(g2.arB);
+      // group segments by the target (variable operand) offset
+      std::map<int64_t, std::vector<std::pair<int64_t, int64_t>>> tgt;  // target -> (fixed operand, Cbar)
+      for (int b = 0; b < g2.nbatch(); ++b)
+        for (int s = g2.sbeg[b]; s < g2.sbeg[b + 1]; ++s) {
+          int64_t to = bvar ? g2.boff[s] : g2.aoff[s];
+          int64_t fo = bvar ? g2.aoff[s] : g2.boff[s];
+          tgt[to].push_back({fo, g2.coff[b]});
+        }
+      if (bvar) {
+        if (g2.tb == 0) {
+          // Bbar[k][n] += alpha sum_m opA(m,k) Cbar[m][n]
+          t.M = g2.K; t.N = g2.N; t.K = g2.M;
+          t.ta = !g2.ta; t.lda = g2.lda; t.arA = g2.arA;
+          t.tb = 0; t.ldb = g2.ldc; t.arB = g2.arC;
+          t.ldc = g2.ldb; t.arC = g2.arB;
+          t.sbeg.push_back(0);
+          for (auto& kv : tgt) {
+            t.coff.push_back(kv.first);
+            t.sbeg.push_back(t.sbeg.back());
+            for (auto& fc : kv.second) {
+              t.aoff.push_back(fc.first);
+              t.boff.push_back(fc.second);
+              t.sbeg.back()++;
+            }
+          }
+        } else {
+          // B stored [N][K]: Bbar[n][k] += alpha sum_m Cbar[m][n] opA(m,k)
+          t.M = g2.N; t.N = g2.K; t.K = g2.M;
+          t.ta = 1; t.lda = g2.ldc; t.arA = g2.arC;
+          t.tb = g2.ta; t.ldb = g2.lda; t.arB = g2.arA;
+          t.ldc = g2.ldb; t.arC = g2.arB;
+          t.sbeg.push_back(0);
+          for (auto& kv : tgt) {
+            t.coff.push_back(kv.first);
+            t.sbeg.push_back(t.sbeg.back());
+            for (auto& fc : kv.second) {
+              t.aoff.push_back(fc.second);
+              t.boff.push_back(fc.first);
+              t.sbeg.back()++;
+            }
+          }
+        }
+      } else {
+        if (g2.ta == 0) {
+          // Abar[m][k] += alpha sum_n Cbar[m][n] opB(k,n)
+          t.M = g2.M; t.N = g2.K; t.K = g2.N;
+          t.ta = 0; t.lda = g2.ldc; t.arA = g2.arC;
+          t.tb = !g2.tb; t.ldb = g2.ldb; t.arB = g2.arB;
+          t.ldc = g2.lda; t.arC = g2.arA;
+          t.sbeg.push_back(0);
+          for (auto& kv : tgt) {
+            t.coff.push_back(kv.first);
+            t.sbeg.push_back(t.sbeg.back());
+            for (auto& fc : kv.second) {
+              t.aoff.push_back(fc.second);
+              t.boff.push_back(fc.first);
+              t.sbeg.back()++;
+            }
+          }
+        } else {
+          // A stored [K][M]: Abar[k][m] += alpha sum_n opB(k,n) Cbar[m][n]
+          t.M = g2.K; t.N = g2.M; t.K = g2.N;
+          t.ta = g2.tb; t.lda = g2.ldb; t.arA = g2.arB;
+          t.tb = 1; t.ldb = g2.ldc; t.arB = g2.arC;
+          t.ldc = g2.lda; t.arC = g2.arA;
+          t.sbeg.push_back(0);
+          for (auto& kv : tgt) {
+            t.coff.push_back(kv.first);
+            t.sbeg.push_back(t.sbeg.back());
+            for (auto& fc : kv.second) {
+              t.aoff.push_back(fc.first);
+              t.boff.push_back(fc.second);
+              t.sbeg.back()++;
+            }
+          }
+        }
+      }
+      P.gemms.push_back(t);
+      Op o2;
+      o2.kind = OP_GEMM;
+      o2.idx = (int)P.gemms.size() - 1;
+      out.ops.push_back(o2);
+    } else if (op.kind == OP_PERM) {
+      Perm p = P.perms[op.idx];
+      Perm t;
+      t.src = p.dst; t.dst = p.src;
+      for (int s = 0; s < 4; ++s) t.pi[p.pi[s]] = s;
+      t.ar = p.ar; t.ai = p.ai;
+      t.arS = p.arD; t.arD = p.arS;
+      t.offS = p.offD; t.offD = p.offS;
+      t.tag = p.tag + "^T";
+      P.perms.push_back(t);
+      Op o2;
+      o2.kind = OP_PERM;
+      o2.idx = (int)P.perms.size() - 1;
+      out.ops.push_back(o2);
+    } else if (op.kind == OP_BTRANS) {
+      BTrans p = P.btrans[op.idx];
+      BTrans t;
+      t.nb = p.nb; t.R = p.C; t.C = p.R;
+      t.ar = p.ar; t.ai = p.ai;
+      t.arS = p.arD; t.arD = p.arS;
+      t.offS = p.offD; t.offD = p.offS;
+      t.tag = p.tag + "^T";
+      P.btrans.push_back(t);
+      Op o2;
+      o2.kind = OP_BTRANS;
+      o2.idx = (int)P.btrans.size() - 1;
+      out.ops.push_back(o2);
+    }
+  }
+  (void)pending;
+  return out;
+}
+
+}  // namespace lrcc
