@@ -116,6 +116,10 @@ void lrcc_destroy(lrcc_problem* p);
 /* Default options. */
 void lrcc_default_options(lrcc_options* opt);
 
+/* Number of device kernels this problem has launched so far (a counter kept by
+ * the executor; -1 for a NULL handle). */
+int64_t lrcc_kernel_launches(const lrcc_problem* p);
+
 /* ---------------------------------------------------------------------------
  * Plan introspection (host only; never touches the GPU)
  *
@@ -132,6 +136,9 @@ void lrcc_plan_destroy(lrcc_plan* h);
  * f0, t1, t2, identity, x1, x2; flops double[3]: Jacobian, ladder, W build. */
 lrcc_status lrcc_plan_info(const lrcc_plan* h, int64_t* arena_sizes, int64_t* offsets, double* flops);
 int32_t lrcc_plan_num_ops(const lrcc_plan* h, int32_t which);
+/* Bounds check of every op of every program against the arena sizes; writes a
+ * NUL-terminated message (empty when every access is in bounds) into msg[len]. */
+lrcc_status lrcc_plan_validate(const lrcc_plan* h, char* msg, int32_t len);
 /* kind_idx_fixed int32[3]: kind (0 GEMM, 1 permute, 2 2-D transpose), table index,
  * fixed-only flag. */
 lrcc_status lrcc_plan_op(const lrcc_plan* h, int32_t which, int32_t i, int32_t* kind_idx_fixed);

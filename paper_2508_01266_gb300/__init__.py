@@ -1,0 +1,152 @@
+"""GB300-native periodic LR-CCSD: k-point Jacobian products and polarizability.
+
+Thin Python layer over liblrcc.so (include/lrcc.h).  The functions below carry the
+C entry points' names without the `lrcc_` prefix and only marshal arguments:
+torch tensors supply device memory and streams, the library runs every step.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from ._lib import lib, lrcc_dims, lrcc_options, STATUS, LIB_PATH
+
+__all__ = ["LrccError", "Problem", "default_options", "create", "set_integrals", "set_ground_state",
+           "jacobian_apply", "polarizability", "last_error", "destroy", "kernel_launches", "LIB_PATH"]
+
+
+class LrccError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st, h):
+    if st != 0:
+        msg = lib.lrcc_last_error(h) if h else b""
+        raise LrccError(st, (msg or b"").decode())
+
+
+def default_options(**kw) -> lrcc_options:
+    o = lrcc_options()
+    lib.lrcc_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t: torch.Tensor):
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _c128(x, device):
+    t = torch.as_tensor(x) if not isinstance(x, torch.Tensor) else x
+    return t.to(device=device, dtype=torch.complex128).contiguous()
+
+
+def create(nk, nocc, nvir, naux, kmesh=0):
+    d = lrcc_dims(nk, nocc, nvir, naux, kmesh)
+    h = C.c_void_p()
+    st = lib.lrcc_create(C.byref(d), C.byref(h))
+    if st != 0:
+        msg = lib.lrcc_last_error(h) if h else b""
+        if h:
+            lib.lrcc_destroy(h)
+        raise LrccError(st, (msg or b"").decode())
+    return h
+
+
+def destroy(h):
+    lib.lrcc_destroy(h)
+
+
+def last_error(h) -> str:
+    return (lib.lrcc_last_error(h) or b"").decode()
+
+
+def kernel_launches(h) -> int:
+    return int(lib.lrcc_kernel_launches(h))
+
+
+def set_integrals(h, L, eps, dip):
+    dev = torch.device("cuda")
+    Lt, dt = _c128(L, dev), _c128(dip, dev)
+    et = torch.as_tensor(eps).to(device=dev, dtype=torch.float64).contiguous()
+    _check(lib.lrcc_set_integrals(h, _ptr(Lt), _ptr(et), _ptr(dt), 1), h)
+
+
+def set_ground_state(h, t1, t2, l1=None, l2=None):
+    dev = torch.device("cuda")
+    a, b = _c128(t1, dev), _c128(t2, dev)
+    c = _c128(l1, dev) if l1 is not None else None
+    d = _c128(l2, dev) if l2 is not None else None
+    _check(lib.lrcc_set_ground_state(h, _ptr(a), _ptr(b), _ptr(c) if c is not None else None,
+                                     _ptr(d) if d is not None else None, 1), h)
+
+
+def jacobian_apply(h, x1: torch.Tensor, x2: torch.Tensor, transpose=False, y1=None, y2=None, options=None,
+                   stream=None):
+    """y = A x (or P_sym A^T x) for a batch of vectors x1[nrhs,...], x2[nrhs,...] (CUDA complex128)."""
+    if x1.device.type != "cuda" or x2.device.type != "cuda":
+        raise ValueError("jacobian_apply takes CUDA tensors")
+    x1 = x1.contiguous()
+    x2 = x2.contiguous()
+    nrhs = x1.shape[0]
+    y1 = torch.empty_like(x1) if y1 is None else y1
+    y2 = torch.empty_like(x2) if y2 is None else y2
+    opt = options if options is not None else default_options()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib.lrcc_jacobian_apply(h, int(bool(transpose)), nrhs, _ptr(x1), _ptr(x2), _ptr(y1), _ptr(y2),
+                                   C.byref(opt), C.c_void_p(st.cuda_stream)), h)
+    return y1, y2
+
+
+def polarizability(h, comps, omegas, options=None):
+    comps = np.ascontiguousarray(comps, dtype=np.int32)
+    om = np.ascontiguousarray(omegas, dtype=np.float64)
+    out = np.zeros((len(om), len(comps), len(comps)), dtype=np.complex128)
+    info = np.zeros(2 + len(comps), dtype=np.int32)
+    opt = options if options is not None else default_options()
+    _check(lib.lrcc_polarizability(h, comps.ctypes.data_as(C.POINTER(C.c_int32)), len(comps),
+                                   om.ctypes.data_as(C.POINTER(C.c_double)), len(om), C.byref(opt),
+                                   C.c_void_p(out.ctypes.data), info.ctypes.data_as(C.POINTER(C.c_int32))), h)
+    return out, info
+
+
+class Problem:
+    """Owning wrapper around an lrcc_problem handle."""
+
+    def __init__(self, nk, nocc, nvir, naux, kmesh=0):
+        self.nk, self.nocc, self.nvir, self.naux = nk, nocc, nvir, naux
+        self.h = create(nk, nocc, nvir, naux, kmesh)
+
+    def set_integrals(self, L, eps, dip):
+        set_integrals(self.h, L, eps, dip)
+
+    def set_ground_state(self, t1, t2, l1=None, l2=None):
+        set_ground_state(self.h, t1, t2, l1, l2)
+
+    def jacobian_apply(self, x1, x2, transpose=False, **kw):
+        return jacobian_apply(self.h, x1, x2, transpose, **kw)
+
+    def polarizability(self, comps, omegas, options=None):
+        return polarizability(self.h, comps, omegas, options)
+
+    @property
+    def kernel_launches(self):
+        return kernel_launches(self.h)
+
+    def close(self):
+        if self.h:
+            destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

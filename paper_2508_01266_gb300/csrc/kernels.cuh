@@ -1,0 +1,59 @@
+// Device-side argument blocks and launchers for the op kinds of a plan.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace lrcc {
+
+// Segmented batched complex GEMM (see plan.h for the exact semantics).
+struct GemmArgs {
+  int M, N, K, ta, tb, epi, ep1, ep2, ep3;
+  long long lda, ldb, ldc;
+  double ar, ai;
+  const long long* coff;
+  const int* sbeg;
+  const long long* aoff;
+  const long long* boff;
+  int tiles_m, tiles_n, nbatch;
+  const double2* A;
+  const double2* B;
+  double2* C;
+  long long sA, sB, sC;  // per-vector strides of variable arenas (0 for shared ones)
+};
+
+struct PermArgs {
+  int skind, snk, sn[4];
+  int dkind, dnk, dn[4];
+  int pi[4];
+  long long total;
+  const double2* S;
+  double2* D;
+  long long sS, sD;
+  double ar, ai;
+};
+
+struct BTransArgs {
+  int nb, R, C;
+  const double2* S;
+  double2* D;
+  long long sS, sD;
+  double ar, ai;
+};
+
+// Tile configurations of the FP64 GEMM kernel.
+enum GemmTile : int {
+  GT_64x64 = 0, GT_32x64, GT_64x32, GT_32x32, GT_16x64, GT_64x16, GT_16x16, GT_8x32, GT_1x256, GT_256x1,
+  GT_COUNT
+};
+void gemm_tile_dims(int tile, int* bm, int* bn);
+int gemm_pick_tile(int M, int N);
+
+cudaError_t launch_gemm_f64(const GemmArgs& g, int tile, int nrhs, cudaStream_t st);
+cudaError_t launch_perm_f64(const PermArgs& p, int nrhs, cudaStream_t st);
+cudaError_t launch_btrans_f64(const BTransArgs& t, int nrhs, cudaStream_t st);
+
+// DF factor split: L[k1][k2][Q][n][n] (paper units) -> oo/ov/vo/vv blocks * scale.
+cudaError_t launch_split_df(const double2* L, int nk, int Q, int o, int v, double scale, double2* Loo,
+                            double2* Lov, double2* Lvo, double2* Lvv, cudaStream_t st);
+
+}  // namespace lrcc

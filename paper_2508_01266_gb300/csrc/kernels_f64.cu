@@ -1,0 +1,302 @@
+// FP64 (complex128) kernels of the plan executor: segmented batched GEMM,
+// momentum-aware layout permutation, batched 2-D transpose and DF-factor split.
+//
+// On GB300 the FP64 pipe (measured ~1.2 TFLOP/s for DFMA) is the bound of every
+// FP64 contraction in this path, so the GEMM is a shared-memory tiled DFMA kernel:
+// each thread owns a TM x TN register tile of complex accumulators (4 DFMA per
+// complex MAC); tiles are picked per op to minimise padded work.
+#include <cstdio>
+
+#include "kernels.cuh"
+
+namespace lrcc {
+
+__device__ __forceinline__ int kmod(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+template <int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    zgemm_seg_kernel(GemmArgs g) {
+  constexpr int NTX = BN / TN, NTY = BM / TM, NT = NTX * NTY;
+  __shared__ double2 As[BK][BM];
+  __shared__ double2 Bs[BK][BN];
+  const int tpb = g.tiles_m * g.tiles_n;
+  const int bid = blockIdx.x;
+  const int batch = bid / tpb;
+  const int t = bid - batch * tpb;
+  const int m0 = (t / g.tiles_n) * BM;
+  const int n0 = (t % g.tiles_n) * BN;
+  const long long rhs = blockIdx.y;
+  const double2* Ab = g.A + rhs * g.sA;
+  const double2* Bb = g.B + rhs * g.sB;
+  double2* Cb = g.C + rhs * g.sC;
+  const int tid = threadIdx.x;
+  const int tx = tid % NTX, ty = tid / NTX;
+  const int M = g.M, N = g.N, K = g.K;
+  double accr[TM][TN], acci[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      accr[i][j] = 0.0;
+      acci[i][j] = 0.0;
+    }
+  const int s0 = g.sbeg[batch], s1 = g.sbeg[batch + 1];
+  for (int s = s0; s < s1; ++s) {
+    const double2* Ap = Ab + g.aoff[s];
+    const double2* Bp = Bb + g.boff[s];
+    for (int k0 = 0; k0 < K; k0 += BK) {
+      for (int idx = tid; idx < BM * BK; idx += NT) {
+        int m, k;
+        if (!g.ta) {
+          k = idx % BK;
+          m = idx / BK;
+        } else {
+          m = idx % BM;
+          k = idx / BM;
+        }
+        const int gm = m0 + m, gk = k0 + k;
+        double2 val = make_double2(0.0, 0.0);
+        if (gm < M && gk < K) val = g.ta ? Ap[(long long)gk * g.lda + gm] : Ap[(long long)gm * g.lda + gk];
+        As[k][m] = val;
+      }
+      for (int idx = tid; idx < BK * BN; idx += NT) {
+        int k, n;
+        if (!g.tb) {
+          n = idx % BN;
+          k = idx / BN;
+        } else {
+          k = idx % BK;
+          n = idx / BK;
+        }
+        const int gn = n0 + n, gk = k0 + k;
+        double2 val = make_double2(0.0, 0.0);
+        if (gn < N && gk < K) val = g.tb ? Bp[(long long)gn * g.ldb + gk] : Bp[(long long)gk * g.ldb + gn];
+        Bs[k][n] = val;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        double2 a[TM], b[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * NTY];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + j * NTX];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) {
+            accr[i][j] = fma(a[i].x, b[j].x, accr[i][j]);
+            accr[i][j] = fma(-a[i].y, b[j].y, accr[i][j]);
+            acci[i][j] = fma(a[i].x, b[j].y, acci[i][j]);
+            acci[i][j] = fma(a[i].y, b[j].x, acci[i][j]);
+          }
+      }
+      __syncthreads();
+    }
+  }
+  double2* Cp = Cb + g.coff[batch];
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int m = m0 + ty + i * NTY;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int n = n0 + tx + j * NTX;
+      if (n >= N) continue;
+      long long addr;
+      if (g.epi == 0) {
+        addr = (long long)m * g.ldc + n;
+      } else {
+        const int a = m / g.ep2, c = m - a * g.ep2;
+        const int b = n / g.ep3, d = n - b * g.ep3;
+        addr = (((long long)a * g.ep1 + b) * g.ep2 + c) * g.ep3 + d;
+      }
+      const double vr = g.ar * accr[i][j] - g.ai * acci[i][j];
+      const double vi = g.ar * acci[i][j] + g.ai * accr[i][j];
+      if (g.epi == 0) {
+        double2 cv = Cp[addr];
+        cv.x += vr;
+        cv.y += vi;
+        Cp[addr] = cv;
+      } else {  // W-block build: the workspace slot is overwritten
+        Cp[addr] = make_double2(vr, vi);
+      }
+    }
+  }
+}
+
+void gemm_tile_dims(int tile, int* bm, int* bn) {
+  static const int d[GT_COUNT][2] = {{64, 64}, {32, 64}, {64, 32}, {32, 32}, {16, 64},
+                                     {64, 16}, {16, 16}, {8, 32},  {1, 256}, {256, 1}};
+  *bm = d[tile][0];
+  *bn = d[tile][1];
+}
+
+int gemm_pick_tile(int M, int N) {
+  int best = 0;
+  double bestw = 1e300;
+  for (int t = 0; t < GT_COUNT; ++t) {
+    int bm, bn;
+    gemm_tile_dims(t, &bm, &bn);
+    double w = (double)((M + bm - 1) / bm) * bm * (double)((N + bn - 1) / bn) * bn;
+    // prefer larger tiles on ties (fewer CTAs, fewer tile reloads)
+    w *= 1.0 + 0.02 * (4096.0 / (bm * bn));
+    if (w < bestw) {
+      bestw = w;
+      best = t;
+    }
+  }
+  return best;
+}
+
+template <int BM, int BN, int TM, int TN>
+static cudaError_t launch_t(GemmArgs g, int nrhs, cudaStream_t st) {
+  g.tiles_m = (g.M + BM - 1) / BM;
+  g.tiles_n = (g.N + BN - 1) / BN;
+  long long nblk = (long long)g.tiles_m * g.tiles_n * g.nbatch;
+  if (nblk <= 0) return cudaSuccess;
+  if (nblk > 2147483647LL || nrhs > 65535) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)nblk, (unsigned)nrhs);
+  zgemm_seg_kernel<BM, BN, 8, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_f64(const GemmArgs& g, int tile, int nrhs, cudaStream_t st) {
+  switch (tile) {
+    case GT_64x64: return launch_t<64, 64, 4, 4>(g, nrhs, st);
+    case GT_32x64: return launch_t<32, 64, 2, 4>(g, nrhs, st);
+    case GT_64x32: return launch_t<64, 32, 4, 2>(g, nrhs, st);
+    case GT_32x32: return launch_t<32, 32, 2, 2>(g, nrhs, st);
+    case GT_16x64: return launch_t<16, 64, 1, 4>(g, nrhs, st);
+    case GT_64x16: return launch_t<64, 16, 4, 1>(g, nrhs, st);
+    case GT_16x16: return launch_t<16, 16, 1, 1>(g, nrhs, st);
+    case GT_8x32: return launch_t<8, 32, 1, 1>(g, nrhs, st);
+    case GT_1x256: return launch_t<1, 256, 1, 1>(g, nrhs, st);
+    case GT_256x1: return launch_t<256, 1, 1, 1>(g, nrhs, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// --------------------------------------------------------------------------
+// layout permutation
+// --------------------------------------------------------------------------
+__device__ __forceinline__ long long lay_off(int kind, int nk, const int* n, int k1, int k2, int k3, int i1,
+                                             int i2, int i3, int i4) {
+  const long long n0 = n[0], n1 = n[1], n2 = n[2], n3 = n[3];
+  if (kind == 0) {
+    return (((long long)k1 * nk + k2) * nk + k3) * (n0 * n1 * n2 * n3) + ((i1 * n1 + i2) * n2 + i3) * n3 + i4;
+  } else if (kind == 1) {
+    const int P = kmod(k1 + k2, nk);
+    const long long rows = nk * n0 * n1, cols = nk * n2 * n3;
+    return (long long)P * rows * cols + (((long long)k1 * n0 + i1) * n1 + i2) * cols +
+           ((long long)k3 * n2 + i3) * n3 + i4;
+  } else if (kind == 2) {
+    const int q = kmod(k3 - k1, nk);
+    const int k4 = kmod(k1 + k2 - k3, nk);
+    const long long rows = nk * n0 * n2, cols = nk * n3 * n1;
+    return (long long)q * rows * cols + (((long long)k1 * n0 + i1) * n2 + i3) * cols +
+           ((long long)k4 * n3 + i4) * n1 + i2;
+  } else {
+    return (((long long)k1 * nk + k3) * nk + k2) * (n0 * n1 * n2 * n3) + ((i1 * n2 + i3) * n1 + i2) * n3 + i4;
+  }
+}
+
+__global__ void perm_kernel(PermArgs p) {
+  const long long rhs = blockIdx.y;
+  const double2* S = p.S + rhs * p.sS;
+  double2* D = p.D + rhs * p.sD;
+  const int nk = p.dnk;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < p.total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r = e;
+    int di[4], dk[4];
+    di[3] = (int)(r % p.dn[3]); r /= p.dn[3];
+    di[2] = (int)(r % p.dn[2]); r /= p.dn[2];
+    di[1] = (int)(r % p.dn[1]); r /= p.dn[1];
+    di[0] = (int)(r % p.dn[0]); r /= p.dn[0];
+    dk[2] = (int)(r % nk); r /= nk;
+    dk[1] = (int)(r % nk); r /= nk;
+    dk[0] = (int)r;
+    dk[3] = kmod(dk[0] + dk[1] - dk[2], nk);
+    const long long od = lay_off(p.dkind, nk, p.dn, dk[0], dk[1], dk[2], di[0], di[1], di[2], di[3]);
+    const long long os = lay_off(p.skind, p.snk, p.sn, dk[p.pi[0]], dk[p.pi[1]], dk[p.pi[2]], di[p.pi[0]],
+                                 di[p.pi[1]], di[p.pi[2]], di[p.pi[3]]);
+    const double2 s = S[os];
+    double2 d = D[od];
+    d.x += p.ar * s.x - p.ai * s.y;
+    d.y += p.ar * s.y + p.ai * s.x;
+    D[od] = d;
+  }
+}
+
+cudaError_t launch_perm_f64(const PermArgs& p, int nrhs, cudaStream_t st) {
+  if (p.total <= 0) return cudaSuccess;
+  long long blocks = (p.total + 255) / 256;
+  if (blocks > 152LL * 64) blocks = 152LL * 64;
+  dim3 grid((unsigned)blocks, (unsigned)nrhs);
+  perm_kernel<<<grid, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+__global__ void btrans_kernel(BTransArgs t) {
+  const long long rhs = blockIdx.y;
+  const double2* S = t.S + rhs * t.sS;
+  double2* D = t.D + rhs * t.sD;
+  const long long total = (long long)t.nb * t.R * t.C;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    // e indexes the destination [b][j][i]
+    const int i = (int)(e % t.R);
+    const long long r = e / t.R;
+    const int j = (int)(r % t.C);
+    const long long b = r / t.C;
+    const double2 s = S[(b * t.R + i) * t.C + j];
+    double2 d = D[e];
+    d.x += t.ar * s.x - t.ai * s.y;
+    d.y += t.ar * s.y + t.ai * s.x;
+    D[e] = d;
+  }
+}
+
+cudaError_t launch_btrans_f64(const BTransArgs& t, int nrhs, cudaStream_t st) {
+  long long total = (long long)t.nb * t.R * t.C;
+  if (total <= 0) return cudaSuccess;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152LL * 64) blocks = 152LL * 64;
+  dim3 grid((unsigned)blocks, (unsigned)nrhs);
+  btrans_kernel<<<grid, 256, 0, st>>>(t);
+  return cudaGetLastError();
+}
+
+__global__ void split_df_kernel(const double2* L, int nk, int Q, int o, int v, double scale, double2* Loo,
+                                double2* Lov, double2* Lvo, double2* Lvv) {
+  const int n = o + v;
+  const long long total = (long long)nk * nk * Q * n * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(e % n);
+    const int p = (int)((e / n) % n);
+    const long long kkQ = e / ((long long)n * n);  // (k1*nk + k2)*Q + Q
+    double2 x = L[e];
+    x.x *= scale;
+    x.y *= scale;
+    if (p < o && q < o) Loo[kkQ * o * o + p * o + q] = x;
+    else if (p < o) Lov[kkQ * o * v + p * v + (q - o)] = x;
+    else if (q < o) Lvo[kkQ * v * o + (p - o) * o + q] = x;
+    else Lvv[kkQ * v * v + (long long)(p - o) * v + (q - o)] = x;
+  }
+}
+
+cudaError_t launch_split_df(const double2* L, int nk, int Q, int o, int v, double scale, double2* Loo,
+                            double2* Lov, double2* Lvo, double2* Lvv, cudaStream_t st) {
+  long long total = (long long)nk * nk * Q * (o + v) * (o + v);
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152LL * 64) blocks = 152LL * 64;
+  split_df_kernel<<<(unsigned)blocks, 256, 0, st>>>(L, nk, Q, o, v, scale, Loo, Lov, Lvo, Lvv);
+  return cudaGetLastError();
+}
+
+}  // namespace lrcc

@@ -243,6 +243,7 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
   P.off_t1 = b.alloc(AR_FIX, (int64_t)nk * ov);
   P.off_t2 = b.alloc(AR_FIX, (int64_t)nk * nk * nk * o2 * v2);  // paper units
   P.off_idv = b.alloc(AR_FIX, o2);                               // identity o x o
+  P.off_derived = P.arena_size[AR_FIX];
   auto DF = [&](int64_t base, int a, int c, int k1, int k2) {
     return base + ((int64_t)k1 * nk + k2) * Q * a * c;
   };
@@ -906,6 +907,52 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
     if (op.kind == OP_GEMM) tot += (double)P.gemms[op.idx].flops();
   P.jac_flops = tot;
   return P;
+}
+
+// ---------------------------------------------------------------------------
+// bounds validation
+// ---------------------------------------------------------------------------
+std::string validate_plan(const Plan& P, const Program& pr) {
+  auto chk = [&](int ar, int64_t off, int64_t ext, const std::string& what) -> std::string {
+    if (ar < 0 || ar >= AR_COUNT) return what + ": bad arena";
+    if (off < 0 || ext < 0 || off + ext > P.arena_size[ar])
+      return what + ": out of bounds (arena " + std::to_string(ar) + ", off " + std::to_string(off) + ", extent " +
+             std::to_string(ext) + ", size " + std::to_string(P.arena_size[ar]) + ")";
+    return "";
+  };
+  for (const Op& op : pr.ops) {
+    std::string e;
+    if (op.kind == OP_GEMM) {
+      const Gemm& g = P.gemms[op.idx];
+      if (g.M <= 0 || g.N <= 0 || g.K <= 0) return "gemm " + g.tag + ": empty";
+      int64_t rA = g.ta ? g.K : g.M, cA = g.ta ? g.M : g.K;
+      int64_t rB = g.tb ? g.N : g.K, cB = g.tb ? g.K : g.N;
+      if (cA > g.lda || cB > g.ldb) return "gemm " + g.tag + ": leading dimension";
+      int64_t extA = (rA - 1) * g.lda + cA, extB = (rB - 1) * g.ldb + cB;
+      int64_t extC = g.epi == 0 ? (int64_t)(g.M - 1) * g.ldc + g.N
+                                : (int64_t)(g.M / g.ep[2]) * g.ep[1] * g.ep[2] * g.ep[3];
+      if (g.epi == 0 && g.N > g.ldc) return "gemm " + g.tag + ": ldc";
+      if ((int)g.sbeg.size() != g.nbatch() + 1) return "gemm " + g.tag + ": segment table";
+      for (int b = 0; b < g.nbatch(); ++b) {
+        if (!(e = chk(g.arC, g.coff[b], extC, "gemm C " + g.tag)).empty()) return e;
+        for (int s = g.sbeg[b]; s < g.sbeg[b + 1]; ++s) {
+          if (!(e = chk(g.arA, g.aoff[s], extA, "gemm A " + g.tag)).empty()) return e;
+          if (!(e = chk(g.arB, g.boff[s], extB, "gemm B " + g.tag)).empty()) return e;
+        }
+      }
+    } else if (op.kind == OP_PERM) {
+      const Perm& p = P.perms[op.idx];
+      if (p.src.size() != p.dst.size()) return "perm " + p.tag + ": sizes";
+      if (!(e = chk(p.arS, p.offS, p.src.size(), "perm src " + p.tag)).empty()) return e;
+      if (!(e = chk(p.arD, p.offD, p.dst.size(), "perm dst " + p.tag)).empty()) return e;
+    } else if (op.kind == OP_BTRANS) {
+      const BTrans& t = P.btrans[op.idx];
+      int64_t n = (int64_t)t.nb * t.R * t.C;
+      if (!(e = chk(t.arS, t.offS, n, "btrans src " + t.tag)).empty()) return e;
+      if (!(e = chk(t.arD, t.offD, n, "btrans dst " + t.tag)).empty()) return e;
+    }
+  }
+  return "";
 }
 
 // ---------------------------------------------------------------------------

@@ -40,7 +40,8 @@ int64_t layout_offset(const Layout& L, int k1, int k2, int k3, int i1, int i2, i
 //   op(A)(m,k) = ta ? A[k*lda + m] : A[m*lda + k]
 //   op(B)(k,n) = tb ? B[n*ldb + k] : B[k*ldb + n]
 //   epi == 0:  C[m*ldc + n]
-//   epi == 1:  m = a*nc + c, n = b*nd + d  ->  C[((a*nb + b)*nc + c)*nd + d]
+//   epi == 1:  m = a*nc + c, n = b*nd + d  ->  C[((a*nb + b)*nc + c)*nd + d] = (stored,
+//              not accumulated: W-block workspace slots are reused across chunks)
 struct Gemm {
   int M = 0, N = 0, K = 0;
   int ta = 0, tb = 0;
@@ -104,7 +105,7 @@ struct Plan {
   Program jac;       // linear in IN -> OUT (uses SCR, WS)
   // named offsets of the FIX inputs
   int64_t off_Loo = 0, off_Lov = 0, off_Lvo = 0, off_Lvv = 0, off_f0 = 0,
-          off_t1 = 0, off_t2 = 0, off_idv = 0;
+          off_t1 = 0, off_t2 = 0, off_idv = 0, off_derived = 0;
   int64_t off_x1 = 0, off_x2 = 0;    // within IN / OUT
   int64_t ws_limit = 0;
   double jac_flops = 0.0, ladder_flops = 0.0, wbuild_flops = 0.0;
@@ -112,6 +113,10 @@ struct Plan {
 
 // Build both programs.  ws_budget: complex elements for the W-block workspace.
 Plan build_plan(const Dims& d, int64_t ws_budget);
+
+// Host-side bounds check of every op against the arena sizes (per-vector sizes for
+// the vector arenas).  Returns an empty string when every access is in bounds.
+std::string validate_plan(const Plan& P, const Program& pr);
 
 // Transposed op list of the Jacobian program (reverse order, transposed ops).
 // New GEMM/PERM/BTRANS entries are appended to the plan's tables.

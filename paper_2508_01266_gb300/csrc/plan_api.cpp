@@ -67,6 +67,15 @@ int32_t lrcc_plan_num_ops(const lrcc_plan* h, int32_t which) {
   return (int32_t)prog_of(h, which).ops.size();
 }
 
+lrcc_status lrcc_plan_validate(const lrcc_plan* h, char* msg, int32_t len) {
+  if (!h || !msg || len < 1) return LRCC_EINVAL;
+  std::string e;
+  for (int w = 0; w < 3 && e.empty(); ++w) e = validate_plan(h->P, prog_of(h, w));
+  std::strncpy(msg, e.c_str(), (size_t)len - 1);
+  msg[len - 1] = 0;
+  return e.empty() ? LRCC_OK : LRCC_EINVAL;
+}
+
 lrcc_status lrcc_plan_op(const lrcc_plan* h, int32_t which, int32_t i, int32_t* kind_idx_fixed) {
   if (!h || which < 0 || which > 2 || !kind_idx_fixed) return LRCC_EINVAL;
   const Program& pr = prog_of(h, which);

@@ -1,0 +1,354 @@
+// liblrcc runtime: problem handle, device arenas, plan executor and the C-ABI
+// entry points of include/lrcc.h (except the host-only plan introspection).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lrcc.h"
+#include "kernels.cuh"
+#include "plan.h"
+#include "runtime.h"
+
+namespace lrcc {
+
+static int64_t align_up(int64_t n) { return (n + 31) / 32 * 32; }
+
+bool Runtime::ck(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return true;
+  err = std::string(what) + ": " + cudaGetErrorString(e);
+  return false;
+}
+
+void Runtime::release() {
+  for (void* p : {(void*)fix, (void*)in, (void*)out, (void*)scr, (void*)ws, (void*)desc, (void*)dip, (void*)l1,
+                  (void*)l2})
+    if (p) cudaFree(p);
+  fix = in = out = scr = ws = nullptr;
+  desc = nullptr;
+  dip = l1 = l2 = nullptr;
+  cap_rhs = 0;
+}
+
+lrcc_status Runtime::init(const lrcc_dims& d, int64_t ws_budget) {
+  dims = d;
+  try {
+    Dims dd{d.nk, d.nocc, d.nvir, d.naux};
+    plan = build_plan(dd, ws_budget);
+    jacT = transpose_program(plan, plan.jac);
+  } catch (const std::bad_alloc&) {
+    err = "host allocation failed while building the plan";
+    return LRCC_ENOMEM;
+  } catch (const std::exception& e) {
+    err = std::string("plan: ") + e.what();
+    return LRCC_EINVAL;
+  }
+  for (const Program* pr : {&plan.ground, &plan.jac, &jacT}) {
+    std::string v = validate_plan(plan, *pr);
+    if (!v.empty()) {
+      err = "plan validation: " + v;
+      return LRCC_EINVAL;
+    }
+  }
+  // device descriptor tables of every GEMM
+  size_t bytes = 0;
+  for (const Gemm& g : plan.gemms)
+    bytes += (g.coff.size() + g.aoff.size() + g.boff.size()) * 8 + align_up((int64_t)g.sbeg.size()) * 4 + 64;
+  std::vector<char> host(bytes);
+  size_t pos = 0;
+  std::vector<size_t> base(plan.gemms.size());
+  for (size_t i = 0; i < plan.gemms.size(); ++i) {
+    const Gemm& g = plan.gemms[i];
+    base[i] = pos;
+    std::memcpy(&host[pos], g.coff.data(), g.coff.size() * 8);
+    pos += g.coff.size() * 8;
+    std::memcpy(&host[pos], g.aoff.data(), g.aoff.size() * 8);
+    pos += g.aoff.size() * 8;
+    std::memcpy(&host[pos], g.boff.data(), g.boff.size() * 8);
+    pos += g.boff.size() * 8;
+    std::memcpy(&host[pos], g.sbeg.data(), g.sbeg.size() * 4);
+    pos += align_up((int64_t)g.sbeg.size()) * 4 + 64;
+  }
+  if (!ck(cudaMalloc(&desc, bytes > 0 ? bytes : 8), "cudaMalloc(descriptors)")) return LRCC_ENOMEM;
+  if (!ck(cudaMemcpy(desc, host.data(), bytes, cudaMemcpyHostToDevice), "cudaMemcpy(descriptors)"))
+    return LRCC_ECUDA;
+  gdesc.resize(plan.gemms.size());
+  for (size_t i = 0; i < plan.gemms.size(); ++i) {
+    const Gemm& g = plan.gemms[i];
+    char* p = desc + base[i];
+    gdesc[i].coff = (const long long*)p;
+    gdesc[i].aoff = (const long long*)(p + g.coff.size() * 8);
+    gdesc[i].boff = (const long long*)(p + (g.coff.size() + g.aoff.size()) * 8);
+    gdesc[i].sbeg = (const int*)(p + (g.coff.size() + g.aoff.size() + g.boff.size()) * 8);
+    gdesc[i].tile = gemm_pick_tile(g.M, g.N);
+  }
+  const int64_t nk = d.nk, n = d.nocc + d.nvir;
+  if (!ck(cudaMalloc(&fix, plan.arena_size[AR_FIX] * sizeof(double2)), "cudaMalloc(fixed arena)")) return LRCC_ENOMEM;
+  if (!ck(cudaMalloc(&ws, std::max<int64_t>(plan.arena_size[AR_WS], 1) * sizeof(double2)), "cudaMalloc(workspace)"))
+    return LRCC_ENOMEM;
+  if (!ck(cudaMalloc(&dip, 3 * nk * n * n * sizeof(double2)), "cudaMalloc(dipoles)")) return LRCC_ENOMEM;
+  if (!ck(cudaMemset(fix, 0, plan.arena_size[AR_FIX] * sizeof(double2)), "cudaMemset")) return LRCC_ECUDA;
+  return LRCC_OK;
+}
+
+lrcc_status Runtime::ensure_rhs(int nrhs) {
+  if (nrhs <= cap_rhs) return LRCC_OK;
+  for (double2** p : {&in, &out, &scr})
+    if (*p) {
+      cudaFree(*p);
+      *p = nullptr;
+    }
+  cap_rhs = 0;
+  const int64_t vin = plan.arena_size[AR_IN], vscr = plan.arena_size[AR_SCR];
+  if (!ck(cudaMalloc(&in, vin * nrhs * sizeof(double2)), "cudaMalloc(input vectors)")) return LRCC_ENOMEM;
+  if (!ck(cudaMalloc(&out, vin * nrhs * sizeof(double2)), "cudaMalloc(output vectors)")) return LRCC_ENOMEM;
+  if (!ck(cudaMalloc(&scr, std::max<int64_t>(vscr, 1) * nrhs * sizeof(double2)), "cudaMalloc(scratch)"))
+    return LRCC_ENOMEM;
+  cap_rhs = nrhs;
+  return LRCC_OK;
+}
+
+lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrhs, cudaStream_t st) {
+  long long stride[AR_COUNT] = {0, plan.arena_size[AR_IN], plan.arena_size[AR_OUT], plan.arena_size[AR_SCR], 0};
+  for (const Op& op : pr.ops) {
+    cudaError_t e = cudaSuccess;
+    const int nr = op.fixed_only ? 1 : nrhs;
+    if (op.kind == OP_GEMM) {
+      const Gemm& g = plan.gemms[op.idx];
+      const GemmDesc& d = gdesc[op.idx];
+      GemmArgs a;
+      a.M = g.M; a.N = g.N; a.K = g.K; a.ta = g.ta; a.tb = g.tb;
+      a.epi = g.epi; a.ep1 = g.ep[1]; a.ep2 = g.ep[2]; a.ep3 = g.ep[3];
+      a.lda = g.lda; a.ldb = g.ldb; a.ldc = g.ldc;
+      a.ar = g.ar; a.ai = g.ai;
+      a.coff = d.coff; a.sbeg = d.sbeg; a.aoff = d.aoff; a.boff = d.boff;
+      a.nbatch = g.nbatch();
+      a.tiles_m = a.tiles_n = 1;
+      a.A = ar[g.arA]; a.B = ar[g.arB]; a.C = ar[g.arC];
+      a.sA = op.fixed_only ? 0 : stride[g.arA];
+      a.sB = op.fixed_only ? 0 : stride[g.arB];
+      a.sC = op.fixed_only ? 0 : stride[g.arC];
+      e = launch_gemm_f64(a, d.tile, nr, st);
+      ++launches;
+    } else if (op.kind == OP_PERM) {
+      const Perm& p = plan.perms[op.idx];
+      PermArgs a;
+      a.skind = p.src.kind; a.snk = p.src.nk;
+      a.dkind = p.dst.kind; a.dnk = p.dst.nk;
+      for (int s = 0; s < 4; ++s) {
+        a.sn[s] = p.src.n[s];
+        a.dn[s] = p.dst.n[s];
+        a.pi[s] = p.pi[s];
+      }
+      a.total = p.dst.size();
+      a.S = ar[p.arS] + p.offS;
+      a.D = ar[p.arD] + p.offD;
+      a.sS = op.fixed_only ? 0 : stride[p.arS];
+      a.sD = op.fixed_only ? 0 : stride[p.arD];
+      a.ar = p.ar; a.ai = p.ai;
+      e = launch_perm_f64(a, nr, st);
+      ++launches;
+    } else if (op.kind == OP_BTRANS) {
+      const BTrans& t = plan.btrans[op.idx];
+      BTransArgs a;
+      a.nb = t.nb; a.R = t.R; a.C = t.C;
+      a.S = ar[t.arS] + t.offS;
+      a.D = ar[t.arD] + t.offD;
+      a.sS = op.fixed_only ? 0 : stride[t.arS];
+      a.sD = op.fixed_only ? 0 : stride[t.arD];
+      a.ar = t.ar; a.ai = t.ai;
+      e = launch_btrans_f64(a, nr, st);
+      ++launches;
+    }
+    if (!ck(e, "kernel launch")) return LRCC_ECUDA;
+  }
+  return LRCC_OK;
+}
+
+lrcc_status Runtime::apply(int transpose, int nrhs, cudaStream_t st) {
+  double2* ar[AR_COUNT] = {fix, in, out, scr, ws};
+  const int64_t vin = plan.arena_size[AR_IN], vscr = plan.arena_size[AR_SCR];
+  // zero the result side and the scratch (every op accumulates)
+  double2* res = transpose ? in : out;
+  if (!ck(cudaMemsetAsync(res, 0, vin * nrhs * sizeof(double2), st), "cudaMemsetAsync")) return LRCC_ECUDA;
+  if (vscr > 0 && !ck(cudaMemsetAsync(scr, 0, vscr * nrhs * sizeof(double2), st), "cudaMemsetAsync"))
+    return LRCC_ECUDA;
+  return run(transpose ? jacT : plan.jac, ar, nrhs, st);
+}
+
+}  // namespace lrcc
+
+using namespace lrcc;
+
+struct lrcc_problem {
+  Runtime rt;
+  bool have_int = false, have_t = false, have_l = false;
+};
+
+static lrcc_status fail(lrcc_problem* p, lrcc_status s, const std::string& m) {
+  if (p) p->rt.err = m;
+  return s;
+}
+
+extern "C" {
+
+void lrcc_default_options(lrcc_options* o) {
+  if (!o) return;
+  o->conv_tol = 1e-10;
+  o->refine_tol = 1e-7;
+  o->max_iter = 200;
+  o->diis_depth = 8;
+  o->diis_period = 1;
+  o->precision = 0;
+  o->autotune = 0;
+  o->use_graphs = 0;
+  o->spin_timeout_cycles = 0;
+}
+
+lrcc_status lrcc_create(const lrcc_dims* dims, lrcc_problem** out) {
+  if (!dims || !out) return LRCC_EINVAL;
+  *out = nullptr;
+  if (dims->nk < 1 || dims->nocc < 1 || dims->nvir < 1 || dims->naux < 1 || dims->kmesh < 0 || dims->kmesh > 2)
+    return LRCC_EINVAL;
+  lrcc_problem* p = new (std::nothrow) lrcc_problem();
+  if (!p) return LRCC_ENOMEM;
+  // W-block workspace: up to ~1 GiB of complex128 (at least one block)
+  lrcc_status s = p->rt.init(*dims, (int64_t)1 << 26);
+  if (s != LRCC_OK) {
+    // keep the handle so that lrcc_last_error can report; caller must destroy
+    *out = p;
+    return s;
+  }
+  *out = p;
+  return LRCC_OK;
+}
+
+void lrcc_destroy(lrcc_problem* p) {
+  if (!p) return;
+  p->rt.release();
+  delete p;
+}
+
+const char* lrcc_last_error(const lrcc_problem* p) {
+  if (!p) return "null problem handle";
+  return p->rt.err.c_str();
+}
+
+lrcc_status lrcc_set_integrals(lrcc_problem* p, const void* L, const double* eps, const void* dip,
+                               int32_t on_device) {
+  if (!p || !L || !eps || !dip) return fail(p, LRCC_EINVAL, "set_integrals: null argument");
+  Runtime& rt = p->rt;
+  if (!rt.fix) return fail(p, LRCC_EINVAL, "set_integrals: problem not initialised");
+  const int nk = rt.dims.nk, o = rt.dims.nocc, v = rt.dims.nvir, Q = rt.dims.naux, n = o + v;
+  const Plan& P = rt.plan;
+  const size_t Lbytes = (size_t)nk * nk * Q * n * n * sizeof(double2);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  double2* tmp = nullptr;
+  if (!rt.ck(cudaMalloc(&tmp, Lbytes), "cudaMalloc(L staging)")) return LRCC_ENOMEM;
+  lrcc_status st = LRCC_OK;
+  if (!rt.ck(cudaMemcpy(tmp, L, Lbytes, kind), "cudaMemcpy(L)")) st = LRCC_ECUDA;
+  if (st == LRCC_OK &&
+      !rt.ck(launch_split_df(tmp, nk, Q, o, v, 1.0 / std::sqrt((double)nk), rt.fix + P.off_Loo, rt.fix + P.off_Lov,
+                             rt.fix + P.off_Lvo, rt.fix + P.off_Lvv, 0),
+             "split_df"))
+    st = LRCC_ECUDA;
+  if (st == LRCC_OK && !rt.ck(cudaDeviceSynchronize(), "split_df sync")) st = LRCC_ECUDA;
+  cudaFree(tmp);
+  if (st != LRCC_OK) return st;
+  // orbital energies -> f0 = diag(eps) per k ; identity o x o
+  std::vector<double> e((size_t)nk * n);
+  if (on_device) {
+    if (!rt.ck(cudaMemcpy(e.data(), eps, e.size() * sizeof(double), cudaMemcpyDeviceToHost), "cudaMemcpy(eps)"))
+      return LRCC_ECUDA;
+  } else {
+    std::memcpy(e.data(), eps, e.size() * sizeof(double));
+  }
+  for (double x : e)
+    if (!std::isfinite(x)) return fail(p, LRCC_EINVAL, "set_integrals: non-finite orbital energy");
+  rt.eps = e;
+  std::vector<double2> f0((size_t)nk * n * n, make_double2(0.0, 0.0));
+  for (int k = 0; k < nk; ++k)
+    for (int q = 0; q < n; ++q) f0[((size_t)k * n + q) * n + q].x = e[(size_t)k * n + q];
+  std::vector<double2> idv((size_t)o * o, make_double2(0.0, 0.0));
+  for (int i = 0; i < o; ++i) idv[(size_t)i * o + i].x = 1.0;
+  if (!rt.ck(cudaMemcpy(rt.fix + P.off_f0, f0.data(), f0.size() * sizeof(double2), cudaMemcpyHostToDevice),
+             "cudaMemcpy(f0)") ||
+      !rt.ck(cudaMemcpy(rt.fix + P.off_idv, idv.data(), idv.size() * sizeof(double2), cudaMemcpyHostToDevice),
+             "cudaMemcpy(identity)") ||
+      !rt.ck(cudaMemcpy(rt.dip, dip, (size_t)3 * nk * n * n * sizeof(double2), kind), "cudaMemcpy(dipoles)"))
+    return LRCC_ECUDA;
+  p->have_int = true;
+  p->have_t = false;
+  return LRCC_OK;
+}
+
+lrcc_status lrcc_set_ground_state(lrcc_problem* p, const void* t1, const void* t2, const void* l1, const void* l2,
+                                  int32_t on_device) {
+  if (!p || !t1 || !t2) return fail(p, LRCC_EINVAL, "set_ground_state: null amplitude pointer");
+  if (!p->have_int) return fail(p, LRCC_EINVAL, "set_ground_state: integrals not set");
+  Runtime& rt = p->rt;
+  const Plan& P = rt.plan;
+  const int nk = rt.dims.nk, o = rt.dims.nocc, v = rt.dims.nvir;
+  const size_t n1 = (size_t)nk * o * v, n2 = (size_t)nk * nk * nk * o * o * v * v;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (!rt.ck(cudaMemset(rt.fix + P.off_derived, 0, (P.arena_size[AR_FIX] - P.off_derived) * sizeof(double2)),
+             "cudaMemset(derived)") ||
+      !rt.ck(cudaMemcpy(rt.fix + P.off_t1, t1, n1 * sizeof(double2), kind), "cudaMemcpy(t1)") ||
+      !rt.ck(cudaMemcpy(rt.fix + P.off_t2, t2, n2 * sizeof(double2), kind), "cudaMemcpy(t2)"))
+    return LRCC_ECUDA;
+  if (l1 && l2) {
+    if (!rt.l1 && !rt.ck(cudaMalloc(&rt.l1, n1 * sizeof(double2)), "cudaMalloc(l1)")) return LRCC_ENOMEM;
+    if (!rt.l2 && !rt.ck(cudaMalloc(&rt.l2, n2 * sizeof(double2)), "cudaMalloc(l2)")) return LRCC_ENOMEM;
+    if (!rt.ck(cudaMemcpy(rt.l1, l1, n1 * sizeof(double2), kind), "cudaMemcpy(l1)") ||
+        !rt.ck(cudaMemcpy(rt.l2, l2, n2 * sizeof(double2), kind), "cudaMemcpy(l2)"))
+      return LRCC_ECUDA;
+    p->have_l = true;
+  }
+  double2* ar[AR_COUNT] = {rt.fix, nullptr, nullptr, nullptr, rt.ws};
+  lrcc_status s = rt.run(P.ground, ar, 1, 0);
+  if (s != LRCC_OK) return s;
+  if (!rt.ck(cudaDeviceSynchronize(), "ground-state program")) return LRCC_ECUDA;
+  p->have_t = true;
+  return LRCC_OK;
+}
+
+lrcc_status lrcc_jacobian_apply(lrcc_problem* p, int32_t transpose, int32_t nrhs, const void* x1, const void* x2,
+                                void* y1, void* y2, const lrcc_options* opt, void* stream) {
+  if (!p) return LRCC_EINVAL;
+  if (!p->have_t) return fail(p, LRCC_EINVAL, "jacobian_apply: ground state not set");
+  if (nrhs < 1 || !x1 || !x2 || !y1 || !y2 || (transpose != 0 && transpose != 1))
+    return fail(p, LRCC_EINVAL, "jacobian_apply: bad arguments");
+  if (opt && opt->precision != 0)
+    return fail(p, LRCC_EUNSUPPORTED, "jacobian_apply: only precision 0 (FP64) in this call");
+  Runtime& rt = p->rt;
+  lrcc_status s = rt.ensure_rhs(nrhs);
+  if (s != LRCC_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Plan& P = rt.plan;
+  const int nk = rt.dims.nk, o = rt.dims.nocc, v = rt.dims.nvir;
+  const size_t b1 = (size_t)nk * o * v * sizeof(double2), b2 = (size_t)nk * nk * nk * o * o * v * v * sizeof(double2);
+  const size_t pitch = (size_t)P.arena_size[AR_IN] * sizeof(double2);
+  double2* src = transpose ? rt.out : rt.in;
+  double2* dst = transpose ? rt.in : rt.out;
+  if (!rt.ck(cudaMemcpy2DAsync(src + P.off_x1, pitch, x1, b1, b1, nrhs, cudaMemcpyDeviceToDevice, st), "copy x1") ||
+      !rt.ck(cudaMemcpy2DAsync(src + P.off_x2, pitch, x2, b2, b2, nrhs, cudaMemcpyDeviceToDevice, st), "copy x2"))
+    return LRCC_ECUDA;
+  s = rt.apply(transpose, nrhs, st);
+  if (s != LRCC_OK) return s;
+  if (!rt.ck(cudaMemcpy2DAsync(y1, b1, dst + P.off_x1, pitch, b1, nrhs, cudaMemcpyDeviceToDevice, st), "copy y1") ||
+      !rt.ck(cudaMemcpy2DAsync(y2, b2, dst + P.off_x2, pitch, b2, nrhs, cudaMemcpyDeviceToDevice, st), "copy y2"))
+    return LRCC_ECUDA;
+  return LRCC_OK;
+}
+
+lrcc_status lrcc_polarizability(lrcc_problem* p, const int32_t* comps, int32_t ncomp, const double* omegas,
+                                int32_t nomega, const lrcc_options* opt, void* alpha, int32_t* info) {
+  if (!p) return LRCC_EINVAL;
+  return lrcc_polarize_impl(p->rt, p->have_t, p->have_l, comps, ncomp, omegas, nomega, opt, alpha, info);
+}
+
+int64_t lrcc_kernel_launches(const lrcc_problem* p) { return p ? p->rt.launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,47 @@
+// Internal runtime state shared by the ABI implementation and the solvers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lrcc.h"
+#include "plan.h"
+
+namespace lrcc {
+
+struct GemmDesc {
+  const long long* coff = nullptr;
+  const int* sbeg = nullptr;
+  const long long* aoff = nullptr;
+  const long long* boff = nullptr;
+  int tile = 0;
+};
+
+struct Runtime {
+  lrcc_dims dims{};
+  Plan plan;
+  Program jacT;
+  std::vector<GemmDesc> gdesc;
+  char* desc = nullptr;
+  double2 *fix = nullptr, *in = nullptr, *out = nullptr, *scr = nullptr, *ws = nullptr;
+  double2 *dip = nullptr, *l1 = nullptr, *l2 = nullptr;
+  std::vector<double> eps;
+  int cap_rhs = 0;
+  long long launches = 0;
+  std::string err;
+
+  bool ck(cudaError_t e, const char* what);
+  lrcc_status init(const lrcc_dims& d, int64_t ws_budget);
+  lrcc_status ensure_rhs(int nrhs);
+  lrcc_status run(const Program& pr, double2* const ar[AR_COUNT], int nrhs, cudaStream_t st);
+  lrcc_status apply(int transpose, int nrhs, cudaStream_t st);
+  void release();
+};
+
+}  // namespace lrcc
+
+// Polarizability driver (solver.cu).
+lrcc_status lrcc_polarize_impl(lrcc::Runtime& rt, bool have_t, bool have_l, const int32_t* comps, int32_t ncomp,
+                               const double* omegas, int32_t nomega, const lrcc_options* opt, void* alpha,
+                               int32_t* info);

@@ -28,12 +28,16 @@ class PlanView:
         lib.lrcc_plan_create.restype = C.c_int
         lib.lrcc_plan_num_ops.restype = C.c_int32
 
-        class Dims(C.Structure):
-            _fields_ = [("nk", C.c_int32), ("nocc", C.c_int32), ("nvir", C.c_int32),
-                        ("naux", C.c_int32), ("kmesh", C.c_int32)]
+        at = getattr(lib.lrcc_plan_create, "argtypes", None)
+        if at:
+            Dims = at[0]._type_
+        else:
+            class Dims(C.Structure):
+                _fields_ = [("nk", C.c_int32), ("nocc", C.c_int32), ("nvir", C.c_int32),
+                            ("naux", C.c_int32), ("kmesh", C.c_int32)]
         d = Dims(nk, o, v, Q, 0)
         h = C.c_void_p()
-        st = lib.lrcc_plan_create(C.byref(d), C.c_int64(ws_budget), C.byref(h))
+        st = lib.lrcc_plan_create(C.byref(d), ws_budget, C.byref(h))
         assert st == 0, st
         self.h = h
         self.dims = (nk, o, v, Q)
@@ -138,7 +142,7 @@ def run(ops, arenas):
                     a_, c_ = m // nc, m % nc
                     b_, d_ = n // nd, n % nd
                     addr = c0 + ((a_ * nbb + b_) * nc + c_) * nd + d_
-                    np.add.at(Cm, addr.ravel(), (al * acc).ravel())
+                    Cm[addr.ravel()] = (al * acc).ravel()
         elif kind == "perm":
             v = list(map(int, d["ints"]))
             skind, snk, sn = v[0], v[1], v[2:6]

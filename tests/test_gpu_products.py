@@ -1,0 +1,105 @@
+"""GPU parity of the Jacobian products (FP64 path) against the CPU oracle.
+
+Forward products are the exact derivative of the oracle's residual (5-point
+polynomial stencil); transpose products are the oracle's reverse-mode gradient of
+<Y, Omega>.  FP64 tolerance: 1e-12 of the largest output element.
+"""
+import numpy as np
+import pytest
+import torch
+
+from synth import make_problem, random_amplitudes, random_probe, CONFIGS
+from oracle import rcc
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def lr():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2508_01266_gb300 as m
+    return m
+
+
+def _setup(lr, nk, o, v, Q, seed=11, sigma=0.1, tscale=0.02):
+    p = make_problem(nk, o, v, Q, seed=seed, sigma_l=sigma)
+    t1, t2 = random_amplitudes(nk, o, v, seed=seed + 1, scale1=tscale, scale2=tscale)
+    prob = lr.Problem(nk, o, v, Q)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    prob.set_ground_state(t1, t2 * nk)
+    return p, prob, t1, t2
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("nk,o,v,Q", [(1, 2, 3, 4), (2, 1, 3, 5), (3, 2, 4, 6), (4, 3, 5, 7), (3, 4, 16, 48)])
+def test_forward_and_transpose_vs_oracle(lr, nk, o, v, Q):
+    p, prob, t1, t2 = _setup(lr, nk, o, v, Q)
+    x1, x2 = random_amplitudes(nk, o, v, seed=99, scale1=1.0, scale2=1.0)
+    dev = torch.device("cuda")
+    X1 = torch.as_tensor(x1, device=dev)[None].contiguous()
+    X2 = torch.as_tensor(x2 * nk, device=dev)[None].contiguous()
+    y1, y2 = prob.jacobian_apply(X1, X2)
+    z1, z2 = prob.jacobian_apply(X1, X2, transpose=True)
+    R = rcc.RCC(p)
+    T = torch.as_tensor
+    a1, a2 = R.jacobian(T(t1), T(t2), T(x1), T(x2))
+    b1, b2 = R.transpose(T(t1), T(t2), T(x1), T(x2 * nk))
+    assert _rel(y1[0].cpu().numpy(), a1.numpy()) < TOL
+    assert _rel(y2[0].cpu().numpy(), nk * a2.numpy()) < TOL
+    assert _rel(z1[0].cpu().numpy(), b1.numpy()) < TOL
+    assert _rel(z2[0].cpu().numpy(), b2.numpy() / nk) < TOL
+
+
+def test_multi_rhs_and_determinism(lr):
+    nk, o, v, Q = 3, 2, 5, 8
+    p, prob, t1, t2 = _setup(lr, nk, o, v, Q)
+    x1, x2 = random_probe(nk, o, v, seed=7, nrhs=3)
+    dev = torch.device("cuda")
+    X1 = torch.as_tensor(x1, device=dev).contiguous()
+    X2 = torch.as_tensor(x2 * nk, device=dev).contiguous()
+    y1, y2 = prob.jacobian_apply(X1, X2)
+    y1b, y2b = prob.jacobian_apply(X1, X2)
+    assert torch.equal(y1, y1b) and torch.equal(y2, y2b)
+    for r in range(3):
+        s1, s2 = prob.jacobian_apply(X1[r:r + 1].contiguous(), X2[r:r + 1].contiguous())
+        assert torch.equal(s1[0], y1[r]) and torch.equal(s2[0], y2[r])
+
+
+def test_zero_and_pair_symmetry(lr):
+    nk, o, v, Q = 3, 2, 4, 6
+    p, prob, t1, t2 = _setup(lr, nk, o, v, Q)
+    dev = torch.device("cuda")
+    z1 = torch.zeros((1, nk, o, v), dtype=torch.complex128, device=dev)
+    z2 = torch.zeros((1, nk, nk, nk, o, o, v, v), dtype=torch.complex128, device=dev)
+    y1, y2 = prob.jacobian_apply(z1, z2)
+    assert float(y1.abs().max()) == 0.0 and float(y2.abs().max()) == 0.0
+    x1, x2 = random_amplitudes(nk, o, v, seed=3, scale1=1.0, scale2=1.0)
+    y1, y2 = prob.jacobian_apply(torch.as_tensor(x1, device=dev)[None], torch.as_tensor(x2, device=dev)[None])
+    y = y2[0].cpu().numpy()
+    kb = lambda i, j, a: (i + j - a) % nk  # noqa: E731
+    for ki in range(nk):
+        for kj in range(nk):
+            for ka in range(nk):
+                assert np.allclose(y[ki, kj, ka], y[kj, ki, kb(ki, kj, ka)].transpose(1, 0, 3, 2), rtol=0, atol=1e-13)
+
+
+def test_c2_sampled_blocks(lr):
+    """Full C2 size (Nk=5, o=8, v=40, naux=160): doubles blocks sampled one by one."""
+    c = CONFIGS["c2"]
+    nk, o, v, Q = c["nk"], c["nocc"], c["nvir"], c["naux"]
+    p, prob, t1, t2 = _setup(lr, nk, o, v, Q, seed=1266, sigma=0.02, tscale=0.01)
+    x1, x2 = random_amplitudes(nk, o, v, seed=5, scale1=1.0, scale2=1.0)
+    dev = torch.device("cuda")
+    y1, y2 = prob.jacobian_apply(torch.as_tensor(x1, device=dev)[None], torch.as_tensor(x2 * nk, device=dev)[None])
+    R = rcc.RCC(p)
+    T = torch.as_tensor
+    blocks = [(0, 0, 0), (1, 3, 4), (4, 2, 1)]
+    a1, a2 = R.jacobian(T(t1), T(t2), T(x1), T(x2), blocks=blocks)
+    y2 = y2[0].cpu().numpy()
+    for bk in blocks:
+        assert _rel(y2[bk], nk * a2[bk].numpy()) < TOL, bk
