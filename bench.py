@@ -1,0 +1,297 @@
+#!/usr/bin/env python
+"""Benchmark: periodic LR-CCSD Jacobian products on GB300.
+
+One step = one pass of the response solver's hot path over a batch of right-hand
+sides: the full Jacobian product A.X (particle-particle ladder with W built from the
+dressed DF factors, hole-hole, ring, singles-coupling and Fock-like terms) on every
+vector of the batch.  The default workload is the Nk=5, nocc=8, nvir=40, naux=160
+chain with the 15 (component, +-omega) systems of the 3x3 alpha tensor at
+omega in {0, 0.05, 0.1} Ha.  Inputs are seeded synthetic data (synth.make_problem);
+ground-state amplitudes are random with the magnitude of converged ones (the cost of
+a product does not depend on their values).
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 pipe, nominal (profiling recipe table)
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("LRCC_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+        return dist, dist.get_rank(), ws
+    return None, 0, 1
+
+
+def _max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(cfg_name):
+    from synth import CONFIGS
+    c = dict(CONFIGS[cfg_name])
+    comps = [0, 1, 2]
+    omegas = [0.0, 0.05, 0.1]
+    nsys = sum(len(comps) * (1 if w == 0 else 2) for w in omegas)
+    return c, comps, omegas, nsys
+
+
+def cpu_oracle_rate(cfg, nblocks, seed=1266):
+    """Oracle Jacobian product on `nblocks` sampled doubles blocks; returns
+    (products per second scaled to a full product, seconds, threads, sample text)."""
+    import numpy as np
+    import torch
+    from synth import make_problem, random_amplitudes
+    from oracle import rcc
+    nk, o, v, Q = cfg["nk"], cfg["nocc"], cfg["nvir"], cfg["naux"]
+    p = make_problem(nk, o, v, Q, seed=seed)
+    R = rcc.RCC(p)
+    t1, t2 = random_amplitudes(nk, o, v, seed=seed + 1, scale1=0.01, scale2=0.01)
+    x1, x2 = random_amplitudes(nk, o, v, seed=seed + 2, scale1=1.0, scale2=1.0)
+    rng = np.random.default_rng(seed)
+    allb = [(a, b, c) for a in range(nk) for b in range(nk) for c in range(nk)]
+    pick = [allb[i] for i in rng.choice(len(allb), size=nblocks, replace=False)]
+    T = torch.as_tensor
+    t0 = time.perf_counter()
+    R.jacobian(T(t1), T(t2), T(x1), T(x2), blocks=pick)
+    dt = time.perf_counter() - t0
+    frac = nblocks / len(allb)
+    sample = (f"oracle A.X (exact 5-point stencil of the residual) on {nblocks} of {len(allb)} doubles "
+              f"blocks of one vector, scaled by the block fraction")
+    return frac / dt, dt, torch.get_num_threads(), sample
+
+
+def run_reference(args):
+    dist, rank, ws = _dist()
+    if rank != 0:
+        return
+    cfg, comps, omegas, nsys = workload(args.config)
+    nb = args.ref_blocks
+    for _ in range(args.warmup):
+        cpu_oracle_rate(cfg, nb)
+    rates, secs = [], 0.0
+    threads, sample = None, ""
+    for _ in range(args.steps):
+        r, dt, threads, sample = cpu_oracle_rate(cfg, nb)
+        rates.append(r)
+        secs += dt
+    value = args.steps / sum(1.0 / r for r in rates)
+    line = {"impl": "reference", "metric": "LR-CCSD Jacobian products/s", "value": value,
+            "unit": "products/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128", "data": "synthetic",
+            "config": {"workload": f"{args.config}: Nk={cfg['nk']} nocc={cfg['nocc']} nvir={cfg['nvir']} "
+                                   f"naux={cfg['naux']}", "rhs_per_step": 1},
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "sample": sample, "value": value,
+                             "unit": "products/s"},
+            "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--nrhs", type=int, default=0, help="vectors per step (default: all systems of the workload)")
+    ap.add_argument("--ref-blocks", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    dist, rank, ws = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    if rank == 0:
+        g.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_2508_01266_gb300 as lr
+    from synth import make_problem, random_amplitudes, random_probe
+
+    cfg, comps, omegas, nsys = workload(args.config)
+    nk, o, v, Q = cfg["nk"], cfg["nocc"], cfg["nvir"], cfg["naux"]
+    nrhs = args.nrhs or nsys
+    p = make_problem(nk, o, v, Q, seed=1266)
+    t1, t2 = random_amplitudes(nk, o, v, seed=1267, scale1=0.01, scale2=0.01)
+    prob = lr.Problem(nk, o, v, Q)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    prob.set_ground_state(t1, t2 * nk)
+    x1, x2 = random_probe(nk, o, v, seed=2000 + 97 * rank, nrhs=nrhs)
+    dev = torch.device("cuda", local)
+    X1 = torch.as_tensor(x1, device=dev).contiguous()
+    X2 = torch.as_tensor(x2 * nk, device=dev).contiguous()
+    Y1 = torch.empty_like(X1)
+    Y2 = torch.empty_like(X2)
+    st = torch.cuda.current_stream()
+
+    def step():
+        prob.jacobian_apply(X1, X2, y1=Y1, y2=Y2)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    prob.profile(True)
+    n0 = prob.kernel_launches
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = prob.kernel_launches - n0
+    lad_ms, lad_n, lad_fl = prob.profile_query("ladder")
+    wb_ms, wb_n, wb_fl = prob.profile_query("W build")
+    all_ms, all_n, all_fl = prob.profile_query("")
+    prob.profile(False)
+    clk = clocks.stop()
+    ms = _max_over_ranks(dist, ms)
+    products = nrhs * args.steps * ws
+    value = products / (ms / 1000.0)
+
+    # end to end through the Python/C-ABI call with pinned host buffers
+    h1 = torch.as_tensor(x1).pin_memory()
+    h2 = torch.as_tensor(x2 * nk).pin_memory()
+    o1 = torch.empty_like(h1).pin_memory()
+    o2 = torch.empty_like(h2).pin_memory()
+
+    def e2e_step():
+        d1 = h1.to(dev, non_blocking=True)
+        d2 = h2.to(dev, non_blocking=True)
+        r1, r2 = prob.jacobian_apply(d1, d2)
+        o1.copy_(r1, non_blocking=True)
+        o2.copy_(r2, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = _max_over_ranks(dist, time.perf_counter() - t0)
+    e2e = {"value": products / e2e_s, "unit": "products/s",
+           "h2d_bytes_per_step": int(h1.numel() * 16 + h2.numel() * 16),
+           "d2h_bytes_per_step": int(o1.numel() * 16 + o2.numel() * 16)}
+
+    lad_per_launch_fl = lad_fl / max(lad_n, 1)
+    lad_avg_ms = lad_ms / max(lad_n, 1)
+    achieved = lad_per_launch_fl / (lad_avg_ms * 1e-3) / 1e9 if lad_n else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+            "frac": (achieved / FP64_NOMINAL_GFLOPS) if achieved else None, "traffic": None,
+            "kernel": "zgemm_seg_kernel (ladder contraction)",
+            "peak_source": "FP64 nominal 1.25 TFLOP/s of the profiling recipe (DFMA probe measured 1.195)",
+            "ladder_share_of_step": lad_ms / max(all_ms, 1e-9), "wbuild_share_of_step": wb_ms / max(all_ms, 1e-9),
+            "step_gflops_algorithmic": all_fl / (all_ms * 1e-3) / 1e9 if all_ms else None}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        r, dt, threads, sample = cpu_oracle_rate(cfg, args.ref_blocks)
+        cpu = {"value": r, "unit": "products/s", "cores": threads, "kind": "oracle", "sample": sample,
+               "seconds": dt}
+    if rank == 0:
+        line = {"metric": "LR-CCSD Jacobian products/s", "value": value, "unit": "products/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+                "data": "synthetic",
+                "config": {"workload": (f"{args.config}: Nk={nk} nocc={o} nvir={v} naux={Q}, {nrhs} vectors per "
+                                        f"step (3 dipole components x omega in {{0,0.05,0.1}} Ha, +-omega)"),
+                           "precision": "fp64", "rhs_per_step": nrhs, "parallelism": f"replicas x{ws}",
+                           "l2": "working set larger than L2 (vector 205 MB, intermediates > 1 GB)"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+if __name__ == "__main__":
+    main()

@@ -120,6 +120,15 @@ void lrcc_default_options(lrcc_options* opt);
  * the executor; -1 for a NULL handle). */
 int64_t lrcc_kernel_launches(const lrcc_problem* p);
 
+/* Per-op timing: when enabled, every op the executor launches is bracketed by CUDA
+ * events recorded on its launching stream (cleared on each call to this function).
+ * lrcc_profile_query sums, over the recorded ops whose tag equals `tag` (an empty
+ * string selects all), the event-timed milliseconds, the launch count and the
+ * algorithmic real flops (8 per complex multiply-add).  Query synchronizes the
+ * device.  Tags are the op names of the plan (e.g. "ladder", "W build"). */
+lrcc_status lrcc_profile(lrcc_problem* p, int32_t enable);
+lrcc_status lrcc_profile_query(lrcc_problem* p, const char* tag, double* ms, int64_t* count, double* flops);
+
 /* ---------------------------------------------------------------------------
  * Plan introspection (host only; never touches the GPU)
  *
@@ -128,12 +137,13 @@ int64_t lrcc_kernel_launches(const lrcc_problem* p);
  * arenas (0 fixed data, 1 input vector, 2 output vector, 3 per-vector scratch,
  * 4 W-block workspace).  These calls expose that list so its index arithmetic can
  * be checked on a CPU.  which: 0 ground-state program, 1 Jacobian, 2 transposed
- * Jacobian.
+ * Jacobian, 3 perturbation right-hand side (Eq. 12), 4 energy second derivative.
  * ------------------------------------------------------------------------- */
 lrcc_status lrcc_plan_create(const lrcc_dims* dims, int64_t ws_budget, lrcc_plan** out);
 void lrcc_plan_destroy(lrcc_plan* h);
-/* arena_sizes int64[5] (complex elements); offsets int64[10]: Loo, Lov, Lvo, Lvv,
- * f0, t1, t2, identity, x1, x2; flops double[3]: Jacobian, ladder, W build. */
+/* arena_sizes int64[5] (complex elements); offsets int64[11]: Loo, Lov, Lvo, Lvv,
+ * f0, t1, t2, identity, x1, x2, one-body operator blocks; flops double[3]:
+ * Jacobian, ladder, W build. */
 lrcc_status lrcc_plan_info(const lrcc_plan* h, int64_t* arena_sizes, int64_t* offsets, double* flops);
 int32_t lrcc_plan_num_ops(const lrcc_plan* h, int32_t which);
 /* Bounds check of every op of every program against the arena sizes; writes a

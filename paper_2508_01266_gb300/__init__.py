@@ -14,7 +14,8 @@ import torch
 from ._lib import lib, lrcc_dims, lrcc_options, STATUS, LIB_PATH
 
 __all__ = ["LrccError", "Problem", "default_options", "create", "set_integrals", "set_ground_state",
-           "jacobian_apply", "polarizability", "last_error", "destroy", "kernel_launches", "LIB_PATH"]
+           "jacobian_apply", "polarizability", "last_error", "destroy", "kernel_launches", "profile",
+           "profile_query", "LIB_PATH"]
 
 
 class LrccError(RuntimeError):
@@ -70,6 +71,17 @@ def last_error(h) -> str:
 
 def kernel_launches(h) -> int:
     return int(lib.lrcc_kernel_launches(h))
+
+
+def profile(h, enable=True):
+    _check(lib.lrcc_profile(h, int(bool(enable))), h)
+
+
+def profile_query(h, tag=""):
+    ms, fl = C.c_double(), C.c_double()
+    cnt = C.c_int64()
+    _check(lib.lrcc_profile_query(h, tag.encode(), C.byref(ms), C.byref(cnt), C.byref(fl)), h)
+    return ms.value, cnt.value, fl.value
 
 
 def set_integrals(h, L, eps, dip):
@@ -135,6 +147,12 @@ class Problem:
 
     def polarizability(self, comps, omegas, options=None):
         return polarizability(self.h, comps, omegas, options)
+
+    def profile(self, enable=True):
+        profile(self.h, enable)
+
+    def profile_query(self, tag=""):
+        return profile_query(self.h, tag)
 
     @property
     def kernel_launches(self):

@@ -41,6 +41,9 @@ _SIGS = {
     "lrcc_destroy": (None, [VP]),
     "lrcc_default_options": (None, [C.POINTER(lrcc_options)]),
     "lrcc_kernel_launches": (C.c_int64, [VP]),
+    "lrcc_profile": (C.c_int, [VP, C.c_int32]),
+    "lrcc_profile_query": (C.c_int, [VP, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_double)]),
     "lrcc_plan_create": (C.c_int, [C.POINTER(lrcc_dims), C.c_int64, C.POINTER(VP)]),
     "lrcc_plan_destroy": (None, [VP]),
     "lrcc_plan_info": (C.c_int, [VP, VP, VP, VP]),

@@ -77,6 +77,7 @@ struct T4 {
 struct B {
   Plan& P;
   int nk, o, v, Q;
+  bool nonlinear = false;  // programs that are never transposed may multiply two vector-arena operands
   explicit B(Plan& p) : P(p), nk(p.d.nk), o(p.d.o), v(p.d.v), Q(p.d.Q) {}
 
   int64_t alloc(int ar, int64_t n) {
@@ -182,7 +183,7 @@ struct B {
       return;
     }
     int nvar = (is_var(g.arA) ? 1 : 0) + (is_var(g.arB) ? 1 : 0);
-    if (nvar > 1) throw std::runtime_error("gemm with two variable operands: " + g.tag);
+    if (nvar > 1 && !nonlinear) throw std::runtime_error("gemm with two variable operands: " + g.tag);
     bool fixed = !is_var(g.arA) && !is_var(g.arB) && !is_var(g.arC);
     if (!fixed && !is_var(g.arC)) throw std::runtime_error("variable gemm into fixed arena: " + g.tag);
     push(pr, OP_GEMM, (int)P.gemms.size() - 1, fixed ? 1 : 0);
@@ -615,9 +616,9 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
   b.pair_gemm(J, Zd, WD, 0, Ud, 0, 0.5, 0.0, "ring D");
   b.pair_gemm(J, Zd, YD, 0, ud, 0, 0.25, 0.0, "ring D quad");
   // [E] Fock-like terms in K3 blocks
-  auto e_vv = [&](Program& pr, const T4& A, int64_t Bvv, int arB, double alpha, const char* tag) {
+  auto e_vv = [&](Program& pr, const T4& r, const T4& A, int64_t Bvv, int arB, double alpha, const char* tag) {
     // r[ki,kj,ka](ij a, b) += alpha sum_c A[ki,kj,ka](ij a, c) Bvv[kb](b, c)
-    Gemm& g = b.g_new((int)(o2 * v), v, v, 0, 1, v, v, v, A.ar, arB, AR_SCR, alpha, 0.0, tag);
+    Gemm& g = b.g_new((int)(o2 * v), v, v, 0, 1, v, v, v, A.ar, arB, r.ar, alpha, 0.0, tag);
     for (int ki = 0; ki < nk; ++ki)
       for (int kj = 0; kj < nk; ++kj)
         for (int ka = 0; ka < nk; ++ka) {
@@ -627,9 +628,9 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
         }
     b.g_push(pr);
   };
-  auto e_oo = [&](Program& pr, const T4& Bx, int64_t Aoo, int arA, double alpha, const char* tag) {
+  auto e_oo = [&](Program& pr, const T4& r, const T4& Bx, int64_t Aoo, int arA, double alpha, const char* tag) {
     // r[ki,kj,ka](i, j, ab) += alpha sum_k Aoo[kj](k, j) Bx[ki,kj,ka](i, k, ab)
-    Gemm& g = b.g_new(o, (int)v2, o, 1, 0, o, v2, v2, arA, Bx.ar, AR_SCR, alpha, 0.0, tag);
+    Gemm& g = b.g_new(o, (int)v2, o, 1, 0, o, v2, v2, arA, Bx.ar, r.ar, alpha, 0.0, tag);
     for (int ki = 0; ki < nk; ++ki)
       for (int kj = 0; kj < nk; ++kj)
         for (int ka = 0; ka < nk; ++ka)
@@ -639,13 +640,13 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
           }
     b.g_push(pr);
   };
-  e_vv(J, xs, Fv, AR_FIX, 1.0, "E vv");
-  e_oo(J, xs, Fo, AR_FIX, -1.0, "E oo");
+  e_vv(J, r, xs, Fv, AR_FIX, 1.0, "E vv");
+  e_oo(J, r, xs, Fo, AR_FIX, -1.0, "E oo");
   int64_t YEv = b.alloc(AR_SCR, nk * v2), YEo = b.alloc(AR_SCR, nk * o2);
   yev(J, YEv, AR_SCR, Uk3, 1.0, "YEv");
   yeo(J, YEo, AR_SCR, Uk3, 1.0, "YEo");
-  e_vv(J, Tk3, YEv, AR_SCR, -1.0, "E vv quad");
-  e_oo(J, Tk3, YEo, AR_SCR, -1.0, "E oo quad");
+  e_vv(J, r, Tk3, YEv, AR_SCR, -1.0, "E vv quad");
+  e_oo(J, r, Tk3, YEo, AR_SCR, -1.0, "E oo quad");
 
   // singles from X2: y1 += Ud_0 fovT + sum_mef U (ae|mf) - sum_mne U (ne|mi)
   {
@@ -850,8 +851,8 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
     b.g_push(J);
   }
   // (16) E' : r += sum_c T_ij^ac f'_bc - sum_k T_ik^ab f'_kj
-  e_vv(J, Tk3, dfvv, AR_SCR, 1.0, "E' vv");
-  e_oo(J, Tk3, dfoo, AR_SCR, -1.0, "E' oo");
+  e_vv(J, r, Tk3, dfvv, AR_SCR, 1.0, "E' vv");
+  e_oo(J, r, Tk3, dfoo, AR_SCR, -1.0, "E' oo");
   // (17) singles from X1
   {
     // sum_e f~vv[k](a,e) x(i,e) -> y1[k](i,a)
@@ -901,6 +902,84 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
   b.perm(J, r, Zd, {0, 1, 2, 3}, 1.0, 0.0, "Zd -> r");
   b.perm(J, yout, r, {0, 1, 2, 3}, sNk, 0.0, "y2 a");
   b.perm(J, yout, r, {1, 0, 3, 2}, sNk, 0.0, "y2 b");
+
+  // =====================================================================
+  // xi program: xi^X(t', mu) = dOmega(t'; h + eps mu)/d eps (paper units), the
+  // perturbed-amplitude right-hand side of Eq. 12.  t' is read from IN (x1/x2
+  // regions, paper units), the one-body operator mu from FIX (oo/ov/vo/vv blocks and
+  // ov transposed).  Omega is linear in the one-body part, so
+  //   xi_1 = mu~_ai + sum_me u_im^ae mu~_me,
+  //   xi_2 = P_ij^ab [sum_c t_ij^ac mu~_bc - sum_k t_ik^ab mu~_kj],   mu~ = (1-tau) mu (1+tau).
+  // Not linear in IN, never transposed.
+  // =====================================================================
+  {
+    P.off_mu = b.alloc(AR_FIX, nk * (o2 + 2 * ov + v2 + ov));
+    const int64_t muoo = P.off_mu, muov = muoo + nk * o2, muvo = muov + nk * ov, muvv = muvo + nk * ov,
+                  muovT = muvv + nk * v2;
+    Program& X = P.xi;
+    b.nonlinear = true;
+    T4 tin{AR_IN, P.off_x2, Layout{LK_K3, nk, {o, o, v, v}}};
+    T4 tk = b.t4(AR_SCR, LK_K3, o, o, v, v);
+    b.perm(X, tk, tin, {0, 1, 2, 3}, 1.0 / sNk, 0.0, "xi t");
+    T4 ux = b.relayout(tk, AR_SCR, LK_PH);
+    b.perm(X, ux, tk, {0, 1, 2, 3}, 2.0, 0.0, "xi u a");
+    b.perm(X, ux, tk, {0, 1, 3, 2}, -1.0, 0.0, "xi u b");
+    int64_t moo = b.alloc(AR_SCR, nk * o2), mvv = b.alloc(AR_SCR, nk * v2), mvo = b.alloc(AR_SCR, nk * ov);
+    auto flat = [&](int ar, int64_t off, int64_t nel) { return T4{ar, off, Layout{LK_K3, 1, {1, 1, 1, (int)nel}}}; };
+    b.perm(X, flat(AR_SCR, moo, nk * o2), flat(AR_FIX, muoo, nk * o2), {0, 1, 2, 3}, 1.0, 0.0, "mu~oo");
+    b.perm(X, flat(AR_SCR, mvv, nk * v2), flat(AR_FIX, muvv, nk * v2), {0, 1, 2, 3}, 1.0, 0.0, "mu~vv");
+    b.perm(X, flat(AR_SCR, mvo, nk * ov), flat(AR_FIX, muvo, nk * ov), {0, 1, 2, 3}, 1.0, 0.0, "mu~vo");
+    {
+      Gemm& g = b.g_new(o, o, v, 0, 1, v, v, o, AR_FIX, AR_IN, AR_SCR, 1.0, 0.0, "mu~oo t");
+      for (int k = 0; k < nk; ++k) {
+        B::batch(g, moo + (int64_t)k * o2);
+        B::seg(g, muov + (int64_t)k * ov, P.off_x1 + (int64_t)k * ov);
+      }
+      b.g_push(X);
+      Gemm& h = b.g_new(v, v, o, 1, 0, v, v, v, AR_IN, AR_FIX, AR_SCR, -1.0, 0.0, "mu~vv t");
+      for (int k = 0; k < nk; ++k) {
+        B::batch(h, mvv + (int64_t)k * v2);
+        B::seg(h, P.off_x1 + (int64_t)k * ov, muov + (int64_t)k * ov);
+      }
+      b.g_push(X);
+      Gemm& h2 = b.g_new(v, o, v, 0, 1, v, v, o, AR_SCR, AR_IN, AR_SCR, 1.0, 0.0, "mu~vo a");
+      for (int k = 0; k < nk; ++k) {
+        B::batch(h2, mvo + (int64_t)k * ov);
+        B::seg(h2, mvv + (int64_t)k * v2, P.off_x1 + (int64_t)k * ov);
+      }
+      b.g_push(X);
+      Gemm& h3 = b.g_new(v, o, o, 1, 0, v, o, o, AR_IN, AR_FIX, AR_SCR, -1.0, 0.0, "mu~vo b");
+      for (int k = 0; k < nk; ++k) {
+        B::batch(h3, mvo + (int64_t)k * ov);
+        B::seg(h3, P.off_x1 + (int64_t)k * ov, muoo + (int64_t)k * o2);
+      }
+      b.g_push(X);
+    }
+    T4 rx = b.t4(AR_SCR, LK_K3, o, o, v, v);
+    e_vv(X, rx, tk, mvv, AR_SCR, 1.0, "xi E vv");
+    e_oo(X, rx, tk, moo, AR_SCR, -1.0, "xi E oo");
+    b.perm(X, yout, rx, {0, 1, 2, 3}, sNk, 0.0, "xi y2 a");
+    b.perm(X, yout, rx, {1, 0, 3, 2}, sNk, 0.0, "xi y2 b");
+    b.btr(X, nk, v, o, AR_OUT, Y1(0), AR_SCR, mvo, 1.0, "xi mu~vo -> y1");
+    Gemm& g = b.g_new((int)(nk * ov), 1, (int)(nk * ov), 0, 0, nk * ov, 1, 1, AR_SCR, AR_FIX, AR_OUT, 1.0, 0.0,
+                      "xi u mu");
+    B::batch(g, Y1(0));
+    B::seg(g, ux.off, muovT);
+    b.g_push(X);
+    b.nonlinear = false;
+  }
+  // egrad program: y1 += 2 sum_jb L_iajb x1_jb, L_iajb = 2(ia|jb) - (ib|ja): the singles-singles
+  // second derivative of the supercell energy (Eq. 6), needed by the quadratic term of Eq. 15.
+  {
+    Program& E = P.egrad;
+    int64_t tmp = b.alloc(AR_SCR, nk * ov);
+    Gemm& g = b.g_new((int)(nk * ov), 1, (int)(nk * ov), 0, 0, nk * ov, 1, 1, AR_FIX, AR_IN, AR_SCR, 2.0, 0.0,
+                      "egrad");
+    B::batch(g, tmp);
+    B::seg(g, MLph.off, P.off_x1);
+    b.g_push(E);
+    b.btr(E, nk, v, o, AR_OUT, Y1(0), AR_SCR, tmp, 1.0, "egrad -> y1");
+  }
 
   double tot = 0;
   for (const Op& op : J.ops)

@@ -103,10 +103,13 @@ struct Plan {
   std::vector<ZeroSpec> zeros;
   Program ground;    // fixed-only ops: ground-state intermediates
   Program jac;       // linear in IN -> OUT (uses SCR, WS)
+  Program xi;        // perturbation right-hand side xi^X(t', mu): IN = t' (paper units) -> OUT
+  Program egrad;     // IN x1 -> OUT y1 += 2 L x1 (energy second derivative, singles)
   // named offsets of the FIX inputs
   int64_t off_Loo = 0, off_Lov = 0, off_Lvo = 0, off_Lvv = 0, off_f0 = 0,
           off_t1 = 0, off_t2 = 0, off_idv = 0, off_derived = 0;
   int64_t off_x1 = 0, off_x2 = 0;    // within IN / OUT
+  int64_t off_mu = 0;                // FIX: one-body operator blocks oo, ov, vo, vv, ov^T
   int64_t ws_limit = 0;
   double jac_flops = 0.0, ladder_flops = 0.0, wbuild_flops = 0.0;
 };

@@ -17,9 +17,13 @@ struct lrcc_plan {
 };
 
 static const Program& prog_of(const lrcc_plan* h, int which) {
-  if (which == 0) return h->P.ground;
-  if (which == 1) return h->P.jac;
-  return h->jacT;
+  switch (which) {
+    case 0: return h->P.ground;
+    case 1: return h->P.jac;
+    case 2: return h->jacT;
+    case 3: return h->P.xi;
+    default: return h->P.egrad;
+  }
 }
 
 extern "C" {
@@ -50,8 +54,8 @@ lrcc_status lrcc_plan_info(const lrcc_plan* h, int64_t* arena_sizes, int64_t* of
   if (arena_sizes)
     for (int a = 0; a < AR_COUNT; ++a) arena_sizes[a] = P.arena_size[a];
   if (offsets) {
-    int64_t o[10] = {P.off_Loo, P.off_Lov, P.off_Lvo, P.off_Lvv, P.off_f0,
-                     P.off_t1,  P.off_t2,  P.off_idv, P.off_x1,  P.off_x2};
+    int64_t o[11] = {P.off_Loo, P.off_Lov, P.off_Lvo, P.off_Lvv, P.off_f0, P.off_t1,
+                     P.off_t2,  P.off_idv, P.off_x1,  P.off_x2,  P.off_mu};
     std::memcpy(offsets, o, sizeof(o));
   }
   if (flops) {
@@ -63,21 +67,21 @@ lrcc_status lrcc_plan_info(const lrcc_plan* h, int64_t* arena_sizes, int64_t* of
 }
 
 int32_t lrcc_plan_num_ops(const lrcc_plan* h, int32_t which) {
-  if (!h || which < 0 || which > 2) return -1;
+  if (!h || which < 0 || which > 4) return -1;
   return (int32_t)prog_of(h, which).ops.size();
 }
 
 lrcc_status lrcc_plan_validate(const lrcc_plan* h, char* msg, int32_t len) {
   if (!h || !msg || len < 1) return LRCC_EINVAL;
   std::string e;
-  for (int w = 0; w < 3 && e.empty(); ++w) e = validate_plan(h->P, prog_of(h, w));
+  for (int w = 0; w < 5 && e.empty(); ++w) e = validate_plan(h->P, prog_of(h, w));
   std::strncpy(msg, e.c_str(), (size_t)len - 1);
   msg[len - 1] = 0;
   return e.empty() ? LRCC_OK : LRCC_EINVAL;
 }
 
 lrcc_status lrcc_plan_op(const lrcc_plan* h, int32_t which, int32_t i, int32_t* kind_idx_fixed) {
-  if (!h || which < 0 || which > 2 || !kind_idx_fixed) return LRCC_EINVAL;
+  if (!h || which < 0 || which > 4 || !kind_idx_fixed) return LRCC_EINVAL;
   const Program& pr = prog_of(h, which);
   if (i < 0 || i >= (int32_t)pr.ops.size()) return LRCC_EINVAL;
   kind_idx_fixed[0] = pr.ops[i].kind;

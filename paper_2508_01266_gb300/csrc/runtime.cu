@@ -22,7 +22,29 @@ bool Runtime::ck(cudaError_t e, const char* what) {
   return false;
 }
 
+cudaEvent_t Runtime::prof_event() {
+  if (!prof_pool.empty()) {
+    cudaEvent_t e = prof_pool.back();
+    prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void Runtime::prof_reset() {
+  for (auto& r : prof_recs) {
+    prof_pool.push_back(r.a);
+    prof_pool.push_back(r.b);
+  }
+  prof_recs.clear();
+}
+
 void Runtime::release() {
+  prof_reset();
+  for (cudaEvent_t e : prof_pool) cudaEventDestroy(e);
+  prof_pool.clear();
   for (void* p : {(void*)fix, (void*)in, (void*)out, (void*)scr, (void*)ws, (void*)desc, (void*)dip, (void*)l1,
                   (void*)l2})
     if (p) cudaFree(p);
@@ -45,7 +67,7 @@ lrcc_status Runtime::init(const lrcc_dims& d, int64_t ws_budget) {
     err = std::string("plan: ") + e.what();
     return LRCC_EINVAL;
   }
-  for (const Program* pr : {&plan.ground, &plan.jac, &jacT}) {
+  for (const Program* pr : {&plan.ground, &plan.jac, &jacT, &plan.xi, &plan.egrad}) {
     std::string v = validate_plan(plan, *pr);
     if (!v.empty()) {
       err = "plan validation: " + v;
@@ -115,6 +137,21 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
   for (const Op& op : pr.ops) {
     cudaError_t e = cudaSuccess;
     const int nr = op.fixed_only ? 1 : nrhs;
+    ProfRec rec{};
+    if (prof) {
+      rec.a = prof_event();
+      rec.b = prof_event();
+      rec.flops = 0.0;
+      if (op.kind == OP_GEMM) {
+        rec.tag = plan.gemms[op.idx].tag;
+        rec.flops = (double)plan.gemms[op.idx].flops() * nr;
+      } else if (op.kind == OP_PERM) {
+        rec.tag = "perm:" + plan.perms[op.idx].tag;
+      } else {
+        rec.tag = "btrans:" + plan.btrans[op.idx].tag;
+      }
+      cudaEventRecord(rec.a, st);
+    }
     if (op.kind == OP_GEMM) {
       const Gemm& g = plan.gemms[op.idx];
       const GemmDesc& d = gdesc[op.idx];
@@ -161,6 +198,10 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
       a.ar = t.ar; a.ai = t.ai;
       e = launch_btrans_f64(a, nr, st);
       ++launches;
+    }
+    if (prof) {
+      cudaEventRecord(rec.b, st);
+      prof_recs.push_back(rec);
     }
     if (!ck(e, "kernel launch")) return LRCC_ECUDA;
   }
@@ -279,6 +320,10 @@ lrcc_status lrcc_set_integrals(lrcc_problem* p, const void* L, const double* eps
              "cudaMemcpy(identity)") ||
       !rt.ck(cudaMemcpy(rt.dip, dip, (size_t)3 * nk * n * n * sizeof(double2), kind), "cudaMemcpy(dipoles)"))
     return LRCC_ECUDA;
+  rt.dip_host.resize((size_t)3 * nk * n * n);
+  if (!rt.ck(cudaMemcpy(rt.dip_host.data(), rt.dip, rt.dip_host.size() * sizeof(double2), cudaMemcpyDeviceToHost),
+             "cudaMemcpy(dipoles to host)"))
+    return LRCC_ECUDA;
   p->have_int = true;
   p->have_t = false;
   return LRCC_OK;
@@ -350,5 +395,33 @@ lrcc_status lrcc_polarizability(lrcc_problem* p, const int32_t* comps, int32_t n
 }
 
 int64_t lrcc_kernel_launches(const lrcc_problem* p) { return p ? p->rt.launches : -1; }
+
+lrcc_status lrcc_profile(lrcc_problem* p, int32_t enable) {
+  if (!p) return LRCC_EINVAL;
+  p->rt.prof_reset();
+  p->rt.prof = enable != 0;
+  return LRCC_OK;
+}
+
+lrcc_status lrcc_profile_query(lrcc_problem* p, const char* tag, double* ms, int64_t* count, double* flops) {
+  if (!p || !tag) return LRCC_EINVAL;
+  Runtime& rt = p->rt;
+  if (!rt.ck(cudaDeviceSynchronize(), "profile sync")) return LRCC_ECUDA;
+  double t = 0.0, f = 0.0;
+  int64_t c = 0;
+  const std::string want(tag);
+  for (auto& r : rt.prof_recs) {
+    if (!want.empty() && r.tag != want) continue;
+    float x = 0.f;
+    if (!rt.ck(cudaEventElapsedTime(&x, r.a, r.b), "cudaEventElapsedTime")) return LRCC_ECUDA;
+    t += x;
+    f += r.flops;
+    ++c;
+  }
+  if (ms) *ms = t;
+  if (count) *count = c;
+  if (flops) *flops = f;
+  return LRCC_OK;
+}
 
 }  // extern "C"

@@ -27,9 +27,16 @@ struct Runtime {
   double2 *fix = nullptr, *in = nullptr, *out = nullptr, *scr = nullptr, *ws = nullptr;
   double2 *dip = nullptr, *l1 = nullptr, *l2 = nullptr;
   std::vector<double> eps;
+  std::vector<double2> dip_host;  // [3][nk][n][n]
   int cap_rhs = 0;
   long long launches = 0;
   std::string err;
+  // optional per-op timing with CUDA events on the launching stream
+  bool prof = false;
+  struct ProfRec { std::string tag; cudaEvent_t a, b; double flops; };
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+  cudaEvent_t prof_event();
 
   bool ck(cudaError_t e, const char* what);
   lrcc_status init(const lrcc_dims& d, int64_t ws_budget);
@@ -37,6 +44,7 @@ struct Runtime {
   lrcc_status run(const Program& pr, double2* const ar[AR_COUNT], int nrhs, cudaStream_t st);
   lrcc_status apply(int transpose, int nrhs, cudaStream_t st);
   void release();
+  void prof_reset();
 };
 
 }  // namespace lrcc

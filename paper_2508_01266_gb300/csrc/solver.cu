@@ -1,11 +1,492 @@
-// Polarizability driver: placeholder until the response solver lands.
-#include "runtime.h"
+// Polarizability driver: perturbed-amplitude solves and the linear-response function.
+//
+//  1. Right-hand sides xi^X = dOmega/d eps_X (Eq. 12) from the xi program.
+//  2. All (component, +-w) systems (A - w) t^X(w) = -xi^X (Eqs. 13-14) solved together
+//     as one batch: every iteration is one batched Jacobian product, the denominator
+//     update t += r / (D - w) (D = e_a - e_i, Eq. 9 with the opposite sign), and DIIS
+//     extrapolation with error vectors e = t^n - t^(n-1) and a Hermitian B matrix
+//     (Sec. II.D).  Convergence: max|r| / max|xi| <= conv_tol for every system.
+//  3. Symmetric linear-response function (Eq. 15 in the form of Christiansen, Jorgensen
+//     and Hattig):
+//       <<X;Y>>_w = 1/2 C^{+-w} [eta^X t^Y(w) + eta^Y t^X(-w) + F(t^X(-w), t^Y(w))],
+//     with eta^X . w = d/ds [E^X + <lam, xi^X>](t + s w) and
+//     F . u = d/ds [grad E + A^T lam](t + s u).  Both are exact 4-point stencils (the
+//     functions are polynomials of degree <= 3 in s), evaluated with the xi program
+//     and with transposed Jacobian products at rebuilt ground-state intermediates.
+//     alpha_XY(w) = -<<X;Y>>_w / Nk (per cell).
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
 
-lrcc_status lrcc_polarize_impl(lrcc::Runtime& rt, bool have_t, bool have_l, const int32_t* comps, int32_t ncomp,
-                               const double* omegas, int32_t nomega, const lrcc_options* opt, void* alpha,
+#include "kernels.cuh"
+#include "runtime.h"
+#include "solver_kernels.cuh"
+
+using namespace lrcc;
+using cd = std::complex<double>;
+
+namespace {
+
+struct Dev {
+  std::vector<void*> ptrs;
+  ~Dev() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  T* get(Runtime& rt, size_t n, bool& ok) {
+    void* p = nullptr;
+    if (!ok) return nullptr;
+    if (!rt.ck(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)), "cudaMalloc(solver)")) {
+      ok = false;
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return (T*)p;
+  }
+};
+
+// Gaussian elimination with partial pivoting on a small dense complex system.
+bool solve_small(std::vector<cd> A, std::vector<cd> b, int n, std::vector<cd>& x) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::abs(A[r * n + c]) > std::abs(A[piv * n + c])) piv = r;
+    if (std::abs(A[piv * n + c]) < 1e-300) return false;
+    if (piv != c) {
+      for (int k = 0; k < n; ++k) std::swap(A[c * n + k], A[piv * n + k]);
+      std::swap(b[c], b[piv]);
+    }
+    for (int r = c + 1; r < n; ++r) {
+      cd f = A[r * n + c] / A[c * n + c];
+      for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
+      b[r] -= f * b[c];
+    }
+  }
+  x.assign(n, 0.0);
+  for (int r = n - 1; r >= 0; --r) {
+    cd s = b[r];
+    for (int k = r + 1; k < n; ++k) s -= A[r * n + k] * x[k];
+    x[r] = s / A[r * n + r];
+  }
+  for (auto& v : x)
+    if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return false;
+  return true;
+}
+
+double u64_to_double(unsigned long long u) {
+  double d;
+  std::memcpy(&d, &u, sizeof(d));
+  return d;
+}
+
+}  // namespace
+
+lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int32_t* comps, int32_t ncomp,
+                               const double* omegas, int32_t nomega, const lrcc_options* optp, void* alpha_out,
                                int32_t* info) {
-  (void)have_t; (void)have_l; (void)comps; (void)ncomp; (void)omegas; (void)nomega; (void)opt; (void)alpha;
-  (void)info;
-  rt.err = "polarizability: not available in this build";
-  return LRCC_EUNSUPPORTED;
+  if (!have_t) {
+    rt.err = "polarizability: ground state not set";
+    return LRCC_EINVAL;
+  }
+  if (!have_l || !rt.l1 || !rt.l2) {
+    rt.err = "polarizability: Lambda multipliers not set";
+    return LRCC_EINVAL;
+  }
+  if (!comps || ncomp < 1 || ncomp > 3 || !omegas || nomega < 1 || !alpha_out) {
+    rt.err = "polarizability: bad arguments";
+    return LRCC_EINVAL;
+  }
+  lrcc_options opt;
+  lrcc_default_options(&opt);
+  if (optp) opt = *optp;
+  if (opt.precision != 0) {
+    rt.err = "polarizability: only precision 0 (FP64) in this call";
+    return LRCC_EUNSUPPORTED;
+  }
+  for (int c = 0; c < ncomp; ++c)
+    if (comps[c] < 0 || comps[c] > 2) {
+      rt.err = "polarizability: component index out of range";
+      return LRCC_EINVAL;
+    }
+  for (int w = 0; w < nomega; ++w)
+    if (!std::isfinite(omegas[w])) {
+      rt.err = "polarizability: non-finite frequency";
+      return LRCC_EINVAL;
+    }
+  const int depth = std::max(1, std::min(opt.diis_depth, 16));
+  const int maxit = std::max(1, opt.max_iter);
+  const int nk = rt.dims.nk, o = rt.dims.nocc, v = rt.dims.nvir, n = o + v;
+  const Plan& P = rt.plan;
+  const long long vec = P.arena_size[AR_IN];
+  const cudaStream_t st = 0;
+
+  // components whose integrals vanish are skipped (Sec. II.C)
+  std::vector<int> active(ncomp, 1);
+  for (int c = 0; c < ncomp; ++c) {
+    double m = 0.0;
+    const double2* d = rt.dip_host.data() + (size_t)comps[c] * nk * n * n;
+    for (size_t i = 0; i < (size_t)nk * n * n; ++i) m = std::max(m, std::hypot(d[i].x, d[i].y));
+    if (m < 1e-14) active[c] = 0;
+  }
+  struct Sys { int c; double w; };
+  std::vector<Sys> sys;
+  std::vector<std::vector<int>> sidx(ncomp, std::vector<int>(2 * nomega, -1));  // [c][2*iw + (0:+w, 1:-w)]
+  for (int c = 0; c < ncomp; ++c) {
+    if (!active[c]) continue;
+    for (int iw = 0; iw < nomega; ++iw) {
+      sidx[c][2 * iw] = (int)sys.size();
+      sys.push_back({c, omegas[iw]});
+      if (omegas[iw] != 0.0) {
+        sidx[c][2 * iw + 1] = (int)sys.size();
+        sys.push_back({c, -omegas[iw]});
+      } else {
+        sidx[c][2 * iw + 1] = sidx[c][2 * iw];
+      }
+    }
+  }
+  cd* alpha = (cd*)alpha_out;
+  for (int i = 0; i < nomega * ncomp * ncomp; ++i) alpha[i] = 0.0;
+  if (info) {
+    info[0] = 0;
+    info[1] = 0;
+    for (int c = 0; c < ncomp; ++c) info[2 + c] = active[c] ? 0 : 1;
+  }
+  const int ns = (int)sys.size();
+  if (ns == 0) return LRCC_OK;
+
+  lrcc_status s = rt.ensure_rhs(ns);
+  if (s != LRCC_OK) return s;
+  Dev dev;
+  bool ok = true;
+  double2* XI = dev.get<double2>(rt, (size_t)ns * vec, ok);
+  double2* SOL = dev.get<double2>(rt, (size_t)ns * vec, ok);
+  double2* FU = dev.get<double2>(rt, (size_t)ns * vec, ok);
+  double2* HX = dev.get<double2>(rt, (size_t)depth * ns * vec, ok);
+  double2* HE = dev.get<double2>(rt, (size_t)depth * ns * vec, ok);
+  double2* TV = dev.get<double2>(rt, (size_t)vec, ok);
+  double2* LAM = dev.get<double2>(rt, (size_t)vec, ok);
+  double* DEN = dev.get<double>(rt, (size_t)vec, ok);
+  double* OM = dev.get<double>(rt, (size_t)ns, ok);
+  unsigned long long* RMAX = dev.get<unsigned long long>(rt, (size_t)ns, ok);
+  const int maxpairs = std::max(ns * ns, depth * ns) + 8;
+  const double2** PA = dev.get<const double2*>(rt, (size_t)maxpairs, ok);
+  const double2** PB = dev.get<const double2*>(rt, (size_t)maxpairs, ok);
+  double2* PART = dev.get<double2>(rt, dot_partial_elems(maxpairs), ok);
+  double2* DOT = dev.get<double2>(rt, (size_t)maxpairs, ok);
+  double2* COEF = dev.get<double2>(rt, (size_t)depth * ns, ok);
+  const double2** PV = dev.get<const double2*>(rt, (size_t)depth, ok);
+  if (!ok) return LRCC_ENOMEM;
+#define CK(x, what) \
+  do {              \
+    if (!rt.ck((x), what)) return LRCC_ECUDA; \
+  } while (0)
+
+  // host helpers ------------------------------------------------------------
+  auto dots = [&](const std::vector<const double2*>& a, const std::vector<const double2*>& b, int conj, long long len,
+                  std::vector<cd>& out) -> lrcc_status {
+    const int np = (int)a.size();
+    out.assign(np, 0.0);
+    for (int c0 = 0; c0 < np; c0 += maxpairs) {
+      const int m = std::min(maxpairs, np - c0);
+      if (!rt.ck(cudaMemcpy(PA, a.data() + c0, m * sizeof(void*), cudaMemcpyHostToDevice), "dots") ||
+          !rt.ck(cudaMemcpy(PB, b.data() + c0, m * sizeof(void*), cudaMemcpyHostToDevice), "dots") ||
+          !rt.ck(launch_dots(PA, PB, conj, len, m, PART, DOT, st), "dots kernel"))
+        return LRCC_ECUDA;
+      rt.launches += 2;
+      std::vector<double2> h(m);
+      if (!rt.ck(cudaMemcpy(h.data(), DOT, m * sizeof(double2), cudaMemcpyDeviceToHost), "dots"))
+        return LRCC_ECUDA;
+      for (int i = 0; i < m; ++i) out[c0 + i] = cd(h[i].x, h[i].y);
+    }
+    return LRCC_OK;
+  };
+  auto run_prog = [&](const Program& pr, int nrhs) -> lrcc_status {
+    double2* ar[AR_COUNT] = {rt.fix, rt.in, rt.out, rt.scr, rt.ws};
+    if (!rt.ck(cudaMemsetAsync(rt.out, 0, (size_t)vec * nrhs * sizeof(double2), st), "memset") ||
+        !rt.ck(cudaMemsetAsync(rt.scr, 0, (size_t)P.arena_size[AR_SCR] * nrhs * sizeof(double2), st), "memset"))
+      return LRCC_ECUDA;
+    return rt.run(pr, ar, nrhs, st);
+  };
+  auto set_mu = [&](int comp) -> lrcc_status {
+    const double2* d = rt.dip_host.data() + (size_t)comp * nk * n * n;
+    std::vector<double2> blk;
+    blk.reserve((size_t)nk * (o * o + 3 * o * v + v * v));
+    auto el = [&](int k, int p, int q) { return d[((size_t)k * n + p) * n + q]; };
+    for (int k = 0; k < nk; ++k)
+      for (int p = 0; p < o; ++p)
+        for (int q = 0; q < o; ++q) blk.push_back(el(k, p, q));
+    for (int k = 0; k < nk; ++k)
+      for (int p = 0; p < o; ++p)
+        for (int q = 0; q < v; ++q) blk.push_back(el(k, p, o + q));
+    for (int k = 0; k < nk; ++k)
+      for (int p = 0; p < v; ++p)
+        for (int q = 0; q < o; ++q) blk.push_back(el(k, o + p, q));
+    for (int k = 0; k < nk; ++k)
+      for (int p = 0; p < v; ++p)
+        for (int q = 0; q < v; ++q) blk.push_back(el(k, o + p, o + q));
+    for (int k = 0; k < nk; ++k)
+      for (int q = 0; q < v; ++q)
+        for (int p = 0; p < o; ++p) blk.push_back(el(k, p, o + q));
+    CK(cudaMemcpy(rt.fix + P.off_mu, blk.data(), blk.size() * sizeof(double2), cudaMemcpyHostToDevice), "mu");
+    return LRCC_OK;
+  };
+  auto rebuild_ground = [&]() -> lrcc_status {
+    CK(cudaMemsetAsync(rt.fix + P.off_derived, 0, (P.arena_size[AR_FIX] - P.off_derived) * sizeof(double2), st),
+       "memset derived");
+    double2* ar[AR_COUNT] = {rt.fix, nullptr, nullptr, nullptr, rt.ws};
+    return rt.run(P.ground, ar, 1, st);
+  };
+  auto maxabs = [&](const double2* x, int nrhs, std::vector<double>& out) -> lrcc_status {
+    CK(cudaMemsetAsync(RMAX, 0, nrhs * sizeof(unsigned long long), st), "memset");
+    CK(launch_maxabs(x, RMAX, vec, vec, nrhs, st), "maxabs");
+    rt.launches++;
+    std::vector<unsigned long long> h(nrhs);
+    CK(cudaMemcpy(h.data(), RMAX, nrhs * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "maxabs");
+    out.resize(nrhs);
+    for (int i = 0; i < nrhs; ++i) out[i] = u64_to_double(h[i]);
+    return LRCC_OK;
+  };
+
+  // denominators, t vector, Lambda in the plain pairing of the paper-unit residual ----
+  {
+    std::vector<double> den(vec, 1.0);
+    const std::vector<double>& e = rt.eps;
+    for (int k = 0; k < nk; ++k)
+      for (int i = 0; i < o; ++i)
+        for (int a = 0; a < v; ++a) den[P.off_x1 + ((size_t)k * o + i) * v + a] = e[k * n + o + a] - e[k * n + i];
+    size_t q = P.off_x2;
+    for (int ki = 0; ki < nk; ++ki)
+      for (int kj = 0; kj < nk; ++kj)
+        for (int ka = 0; ka < nk; ++ka) {
+          const int kb = ((ki + kj - ka) % nk + nk) % nk;
+          for (int i = 0; i < o; ++i)
+            for (int j = 0; j < o; ++j)
+              for (int a = 0; a < v; ++a)
+                for (int b = 0; b < v; ++b)
+                  den[q++] = e[ka * n + o + a] + e[kb * n + o + b] - e[ki * n + i] - e[kj * n + j];
+        }
+    CK(cudaMemcpy(DEN, den.data(), vec * sizeof(double), cudaMemcpyHostToDevice), "den");
+    std::vector<double> om(ns);
+    for (int i = 0; i < ns; ++i) om[i] = sys[i].w;
+    CK(cudaMemcpy(OM, om.data(), ns * sizeof(double), cudaMemcpyHostToDevice), "omega");
+  }
+  const size_t n1 = (size_t)nk * o * v, n2 = (size_t)nk * nk * nk * o * o * v * v;
+  CK(cudaMemset(TV, 0, vec * sizeof(double2)), "memset");
+  CK(cudaMemcpy(TV + P.off_x1, rt.fix + P.off_t1, n1 * sizeof(double2), cudaMemcpyDeviceToDevice), "t1");
+  CK(cudaMemcpy(TV + P.off_x2, rt.fix + P.off_t2, n2 * sizeof(double2), cudaMemcpyDeviceToDevice), "t2");
+  {
+    // lam1 = 2 l1 ; lam2 = (2 l2 - l2(a<->b)) / Nk^2   (paper's spin-orbital Lambda -> plain pairing)
+    CK(cudaMemset(LAM, 0, vec * sizeof(double2)), "memset");
+    CK(launch_axpby(make_double2(2.0, 0.0), rt.l1, make_double2(0.0, 0.0), LAM + P.off_x1, (long long)n1, st), "lam1");
+    PermArgs pa;
+    pa.skind = pa.dkind = LK_K3;
+    pa.snk = pa.dnk = nk;
+    const int dn[4] = {o, o, v, v};
+    for (int i = 0; i < 4; ++i) pa.sn[i] = pa.dn[i] = dn[i];
+    pa.total = (long long)n2;
+    pa.S = rt.l2;
+    pa.D = LAM + P.off_x2;
+    pa.sS = pa.sD = 0;
+    pa.ai = 0.0;
+    const int id[4] = {0, 1, 2, 3}, sw[4] = {0, 1, 3, 2};
+    for (int i = 0; i < 4; ++i) pa.pi[i] = id[i];
+    pa.ar = 2.0 / ((double)nk * nk);
+    CK(launch_perm_f64(pa, 1, st), "lam2 a");
+    for (int i = 0; i < 4; ++i) pa.pi[i] = sw[i];
+    pa.ar = -1.0 / ((double)nk * nk);
+    CK(launch_perm_f64(pa, 1, st), "lam2 b");
+    rt.launches += 3;
+  }
+
+  // 1. right-hand sides -------------------------------------------------------------
+  for (int c = 0; c < ncomp; ++c) {
+    if (!active[c]) continue;
+    if ((s = set_mu(comps[c])) != LRCC_OK) return s;
+    CK(cudaMemcpy(rt.in, TV, vec * sizeof(double2), cudaMemcpyDeviceToDevice), "t -> in");
+    if ((s = run_prog(P.xi, 1)) != LRCC_OK) return s;
+    for (int i = 0; i < ns; ++i)
+      if (sys[i].c == c)
+        CK(cudaMemcpy(XI + (size_t)i * vec, rt.out, vec * sizeof(double2), cudaMemcpyDeviceToDevice), "xi");
+  }
+  std::vector<double> ximax;
+  if ((s = maxabs(XI, ns, ximax)) != LRCC_OK) return s;
+
+  // 2. batched solve -------------------------------------------------------------------
+  CK(launch_guess(XI, DEN, OM, rt.in, vec, vec, ns, st), "guess");
+  rt.launches++;
+  std::vector<std::vector<cd>> Bm(ns, std::vector<cd>(depth * depth, 0.0));
+  std::vector<int> slot_of(depth, -1);  // history age bookkeeping: slots used in order
+  int nhist = 0, it = 0;
+  bool converged = false;
+  std::vector<double> rel(ns, 1.0);
+  for (it = 0; it < maxit; ++it) {
+    if ((s = rt.apply(0, ns, st)) != LRCC_OK) return s;
+    const int slot = it % depth;
+    CK(cudaMemsetAsync(RMAX, 0, ns * sizeof(unsigned long long), st), "memset");
+    CK(launch_update(rt.in, rt.out, XI, DEN, OM, HE + (size_t)slot * ns * vec, HX + (size_t)slot * ns * vec, RMAX,
+                     vec, vec, ns, st),
+       "update");
+    rt.launches++;
+    std::vector<unsigned long long> hr(ns);
+    CK(cudaMemcpy(hr.data(), RMAX, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "rmax");
+    double worst = 0.0;
+    for (int i = 0; i < ns; ++i) {
+      rel[i] = u64_to_double(hr[i]) / std::max(ximax[i], 1e-300);
+      worst = std::max(worst, rel[i]);
+    }
+    if (worst <= opt.conv_tol) {
+      converged = true;
+      break;
+    }
+    nhist = std::min(nhist + 1, depth);
+    // new row of the Hermitian error matrix for every system
+    std::vector<const double2*> pa, pb;
+    std::vector<int> slots;
+    for (int j = 0; j < nhist; ++j) {
+      const int sj = ((it - j) % depth + depth) % depth;
+      slots.push_back(sj);
+      for (int i = 0; i < ns; ++i) {
+        pa.push_back(HE + ((size_t)slot * ns + i) * vec);
+        pb.push_back(HE + ((size_t)sj * ns + i) * vec);
+      }
+    }
+    std::vector<cd> row;
+    if ((s = dots(pa, pb, 1, vec, row)) != LRCC_OK) return s;
+    for (int j = 0; j < nhist; ++j)
+      for (int i = 0; i < ns; ++i) {
+        const int sj = slots[j];
+        Bm[i][slot * depth + sj] = row[j * ns + i];
+        Bm[i][sj * depth + slot] = std::conj(row[j * ns + i]);
+      }
+    std::vector<double2> coef((size_t)nhist * ns, make_double2(0.0, 0.0));
+    for (int i = 0; i < ns; ++i) {
+      std::vector<cd> x;
+      bool good = false;
+      if (nhist >= 2 && (opt.diis_period <= 1 || (it + 1) % opt.diis_period == 0)) {
+        const int m = nhist + 1;
+        std::vector<cd> A(m * m, 0.0), b(m, 0.0);
+        double sc = 0.0;
+        for (int a = 0; a < nhist; ++a) sc = std::max(sc, std::abs(Bm[i][slots[a] * depth + slots[a]]));
+        sc = sc > 0 ? 1.0 / sc : 1.0;
+        for (int a = 0; a < nhist; ++a) {
+          for (int c = 0; c < nhist; ++c) A[a * m + c] = sc * Bm[i][slots[a] * depth + slots[c]];
+          A[a * m + nhist] = -1.0;
+          A[nhist * m + a] = -1.0;
+        }
+        b[nhist] = -1.0;
+        good = solve_small(A, b, m, x);
+      }
+      for (int j = 0; j < nhist; ++j) {
+        cd cj = good ? x[j] : (j == 0 ? cd(1.0) : cd(0.0));
+        coef[(size_t)j * ns + i] = make_double2(cj.real(), cj.imag());
+      }
+    }
+    std::vector<const double2*> pv(nhist);
+    for (int j = 0; j < nhist; ++j) pv[j] = HX + (size_t)slots[j] * ns * vec;
+    CK(cudaMemcpy(PV, pv.data(), nhist * sizeof(void*), cudaMemcpyHostToDevice), "pv");
+    CK(cudaMemcpy(COEF, coef.data(), coef.size() * sizeof(double2), cudaMemcpyHostToDevice), "coef");
+    CK(launch_lincomb(PV, COEF, nhist, rt.in, vec, vec, ns, st), "lincomb");
+    rt.launches++;
+  }
+  if (info) {
+    info[0] = it + 1;
+    info[1] = converged ? 0 : LRCC_ENOCONV;
+  }
+  if (!converged) {
+    rt.err = "polarizability: response equations did not converge";
+    return LRCC_ENOCONV;
+  }
+  CK(cudaMemcpy(SOL, rt.in, (size_t)ns * vec * sizeof(double2), cudaMemcpyDeviceToDevice), "sol");
+  std::vector<double> umax;
+  if ((s = maxabs(SOL, ns, umax)) != LRCC_OK) return s;
+  std::vector<double> hstep(ns);
+  for (int i = 0; i < ns; ++i) hstep[i] = 1e-2 / std::max(umax[i], 1e-300);
+  const double c4[4] = {-2.0, -1.0, 1.0, 2.0}, w4[4] = {1.0, -8.0, 8.0, -1.0};
+
+  // 3a. eta^X . t_sys for every active component and every solution -----------------
+  std::vector<std::vector<cd>> etaw(ncomp, std::vector<cd>(ns, 0.0));
+  for (int c = 0; c < ncomp; ++c) {
+    if (!active[c]) continue;
+    if ((s = set_mu(comps[c])) != LRCC_OK) return s;
+    for (int k = 0; k < 4; ++k) {
+      for (int i = 0; i < ns; ++i) {
+        CK(cudaMemcpy(rt.in + (size_t)i * vec, TV, vec * sizeof(double2), cudaMemcpyDeviceToDevice), "t");
+        CK(launch_axpby(make_double2(c4[k] * hstep[i], 0.0), SOL + (size_t)i * vec, make_double2(1.0, 0.0),
+                        rt.in + (size_t)i * vec, vec, st),
+           "t + s u");
+        rt.launches++;
+      }
+      if ((s = run_prog(P.xi, ns)) != LRCC_OK) return s;
+      std::vector<const double2*> pa(ns, LAM), pb(ns);
+      for (int i = 0; i < ns; ++i) pb[i] = rt.out + (size_t)i * vec;
+      std::vector<cd> g;
+      if ((s = dots(pa, pb, 0, vec, g)) != LRCC_OK) return s;
+      for (int i = 0; i < ns; ++i) etaw[c][i] += w4[k] * g[i] / (12.0 * hstep[i]);
+    }
+    // + dE^X/dt . w = 2 sum mu_ia w_ia
+    std::vector<const double2*> pa(ns, rt.fix + P.off_mu + (size_t)nk * o * o), pb(ns);
+    for (int i = 0; i < ns; ++i) pb[i] = SOL + (size_t)i * vec + P.off_x1;
+    std::vector<cd> g;
+    if ((s = dots(pa, pb, 0, (long long)n1, g)) != LRCC_OK) return s;
+    for (int i = 0; i < ns; ++i) etaw[c][i] += 2.0 * g[i];
+  }
+
+  // 3b. F . u for every solution u ---------------------------------------------------
+  CK(cudaMemset(FU, 0, (size_t)ns * vec * sizeof(double2)), "memset");
+  for (int i = 0; i < ns; ++i) {
+    const double2* u = SOL + (size_t)i * vec;
+    for (int k = 0; k < 4; ++k) {
+      const double sh = c4[k] * hstep[i];
+      CK(cudaMemcpy(rt.fix + P.off_t1, TV + P.off_x1, n1 * sizeof(double2), cudaMemcpyDeviceToDevice), "t1");
+      CK(cudaMemcpy(rt.fix + P.off_t2, TV + P.off_x2, n2 * sizeof(double2), cudaMemcpyDeviceToDevice), "t2");
+      CK(launch_axpby(make_double2(sh, 0.0), u + P.off_x1, make_double2(1.0, 0.0), rt.fix + P.off_t1, (long long)n1,
+                      st),
+         "t1 + s u1");
+      CK(launch_axpby(make_double2(sh, 0.0), u + P.off_x2, make_double2(1.0, 0.0), rt.fix + P.off_t2, (long long)n2,
+                      st),
+         "t2 + s u2");
+      rt.launches += 2;
+      if ((s = rebuild_ground()) != LRCC_OK) return s;
+      CK(cudaMemcpy(rt.out, LAM, vec * sizeof(double2), cudaMemcpyDeviceToDevice), "lam -> out");
+      if ((s = rt.apply(1, 1, st)) != LRCC_OK) return s;
+      CK(launch_axpby(make_double2(w4[k] / (12.0 * hstep[i]), 0.0), rt.in, make_double2(1.0, 0.0),
+                      FU + (size_t)i * vec, vec, st),
+         "F u");
+      rt.launches++;
+    }
+    CK(cudaMemcpy(rt.in, u, vec * sizeof(double2), cudaMemcpyDeviceToDevice), "u -> in");
+    if ((s = run_prog(P.egrad, 1)) != LRCC_OK) return s;
+    CK(launch_axpby(make_double2(1.0, 0.0), rt.out, make_double2(1.0, 0.0), FU + (size_t)i * vec, vec, st), "egrad");
+    rt.launches++;
+  }
+  // restore the ground-state intermediates
+  CK(cudaMemcpy(rt.fix + P.off_t1, TV + P.off_x1, n1 * sizeof(double2), cudaMemcpyDeviceToDevice), "t1");
+  CK(cudaMemcpy(rt.fix + P.off_t2, TV + P.off_x2, n2 * sizeof(double2), cudaMemcpyDeviceToDevice), "t2");
+  if ((s = rebuild_ground()) != LRCC_OK) return s;
+  std::vector<const double2*> pa, pb;
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b < ns; ++b) {
+      pa.push_back(FU + (size_t)a * vec);
+      pb.push_back(SOL + (size_t)b * vec);
+    }
+  std::vector<cd> F;
+  if ((s = dots(pa, pb, 0, vec, F)) != LRCC_OK) return s;
+  CK(cudaDeviceSynchronize(), "solver sync");
+
+  // 3c. response function ------------------------------------------------------------------
+  for (int iw = 0; iw < nomega; ++iw)
+    for (int x = 0; x < ncomp; ++x)
+      for (int y = 0; y < ncomp; ++y) {
+        if (!active[x] || !active[y]) continue;
+        const int xp = sidx[x][2 * iw], xm = sidx[x][2 * iw + 1];
+        const int yp = sidx[y][2 * iw], ym = sidx[y][2 * iw + 1];
+        const cd a = etaw[x][yp] + etaw[y][xm] + F[(size_t)xm * ns + yp];
+        const cd b = etaw[x][ym] + etaw[y][xp] + F[(size_t)xp * ns + ym];
+        const cd lr = 0.5 * (a + std::conj(b));
+        alpha[((size_t)iw * ncomp + x) * ncomp + y] = -lr / (double)nk;
+      }
+#undef CK
+  return LRCC_OK;
 }

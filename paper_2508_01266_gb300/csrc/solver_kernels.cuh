@@ -1,0 +1,23 @@
+// Launchers of the FP64 solver vector kernels (solver_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace lrcc {
+
+cudaError_t launch_update(const double2* x, const double2* y, const double2* xi, const double* den,
+                          const double* omega, double2* e, double2* xnew, unsigned long long* rmax, long long n,
+                          long long stride, int nrhs, cudaStream_t st);
+cudaError_t launch_guess(const double2* xi, const double* den, const double* omega, double2* x, long long n,
+                         long long stride, int nrhs, cudaStream_t st);
+cudaError_t launch_maxabs(const double2* x, unsigned long long* out, long long n, long long stride, int nrhs,
+                          cudaStream_t st);
+size_t dot_partial_elems(int npairs);
+cudaError_t launch_dots(const double2* const* a, const double2* const* b, int conj, long long n, int npairs,
+                        double2* part, double2* out, cudaStream_t st);
+cudaError_t launch_lincomb(const double2* const* v, const double2* c, int m, double2* out, long long n,
+                           long long stride, int nrhs, cudaStream_t st);
+cudaError_t launch_axpby(double2 a, const double2* x, double2 b, double2* y, long long n, cudaStream_t st);
+
+}  // namespace lrcc

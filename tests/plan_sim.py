@@ -42,11 +42,11 @@ class PlanView:
         self.h = h
         self.dims = (nk, o, v, Q)
         ar = np.zeros(5, np.int64)
-        off = np.zeros(10, np.int64)
+        off = np.zeros(11, np.int64)
         fl = np.zeros(3, np.float64)
         lib.lrcc_plan_info(h, _p(ar, I64P), _p(off, I64P), _p(fl, F64P))
         self.arena_sizes, self.offsets, self.flops = ar, off, fl
-        self.programs = [self._read(w) for w in range(3)]
+        self.programs = [self._read(w) for w in range(5)]
 
     def _read(self, which):
         lib, h = self.lib, self.h

@@ -1,0 +1,77 @@
+"""GPU polarizability (FP64 path) against the CPU oracle.
+
+The oracle converges T and Lambda; the GPU receives them (paper normalization) and
+solves the perturbed-amplitude equations and assembles alpha(w) itself.
+Tolerance: 1e-8 relative on alpha (FP64 path).
+"""
+import numpy as np
+import pytest
+import torch
+
+from synth import make_problem, CONFIGS
+from oracle import rcc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lr():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2508_01266_gb300 as m
+    return m
+
+
+def paper_lambda(nk, l1, l2):
+    """Oracle multipliers (plain pairing, supercell units) -> the paper's Lambda
+    (alpha-beta block of the spin-orbital multipliers, paper units)."""
+    kb = lambda i, j, a: (i + j - a) % nk  # noqa: E731
+    sw = torch.zeros_like(l2)
+    for ki in range(nk):
+        for kj in range(nk):
+            for ka in range(nk):
+                sw[ki, kj, ka] = l2[ki, kj, kb(ki, kj, ka)].transpose(2, 3)
+    return l1 / 2.0, nk * (2.0 * l2 + sw) / 3.0
+
+
+def _run(lr, p, comps, omegas, tol=1e-10):
+    nk, o, v, Q = p.nk, p.nocc, p.nvir, p.naux
+    R = rcc.RCC(p)
+    t1, t2, _ = rcc.solve_ccsd(R, tol=tol)
+    l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=tol)
+    ref = rcc.polarizability(R, t1, t2, l1, l2, rcc.dipole_ops(p, comps), omegas, tol=1e-11)
+    pl1, pl2 = paper_lambda(nk, l1, l2)
+    prob = lr.Problem(nk, o, v, Q)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    prob.set_ground_state(t1, t2 * nk, pl1, pl2)
+    opts = lr.default_options(conv_tol=1e-11, max_iter=300)
+    got, info = prob.polarizability(comps, omegas, opts)
+    prob.close()
+    return got, ref, info
+
+
+def test_alpha_small_vs_oracle(lr):
+    p = make_problem(2, 2, 3, 4, seed=5, sigma_l=0.15)
+    got, ref, info = _run(lr, p, [0, 2], [0.0, 0.07])
+    assert info[1] == 0
+    assert np.abs(got - ref).max() < 1e-8 * np.abs(ref).max()
+
+
+def test_alpha_skips_vanishing_component(lr):
+    p = make_problem(1, 1, 3, 4, seed=6, sigma_l=0.15)
+    p.dip[1] = 0.0
+    got, ref, info = _run(lr, p, [1, 2], [0.05])
+    assert info[2] == 1 and info[3] == 0
+    assert np.abs(got[0, 0, :]).max() == 0.0 and np.abs(got[0, :, 0]).max() == 0.0
+    assert abs(got[0, 1, 1] - ref[0, 1, 1]) < 1e-8 * abs(ref[0, 1, 1])
+
+
+def test_alpha_c1_vs_oracle(lr):
+    """C1 workload: Nk=3, nocc=4, nvir=16, naux=48, alpha_zz at w = 0 and 0.1 Ha."""
+    c = CONFIGS["c1"]
+    p = make_problem(c["nk"], c["nocc"], c["nvir"], c["naux"], seed=1266)
+    got, ref, info = _run(lr, p, [2], [0.0, 0.1])
+    assert info[1] == 0
+    rel = np.abs(got - ref).max() / np.abs(ref).max()
+    print("C1 alpha_zz gpu", got.ravel(), "oracle", ref.ravel(), "rel", rel)
+    assert rel < 1e-8

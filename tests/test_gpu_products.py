@@ -48,7 +48,7 @@ def test_forward_and_transpose_vs_oracle(lr, nk, o, v, Q):
     R = rcc.RCC(p)
     T = torch.as_tensor
     a1, a2 = R.jacobian(T(t1), T(t2), T(x1), T(x2))
-    b1, b2 = R.transpose(T(t1), T(t2), T(x1), T(x2 * nk))
+    b1, b2 = R.transpose(T(t1), T(t2), T(x1), T(x2 * nk * nk))  # A_paper^T = D_in A^T D_out
     assert _rel(y1[0].cpu().numpy(), a1.numpy()) < TOL
     assert _rel(y2[0].cpu().numpy(), nk * a2.numpy()) < TOL
     assert _rel(z1[0].cpu().numpy(), b1.numpy()) < TOL

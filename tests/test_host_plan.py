@@ -73,11 +73,12 @@ def _sim_apply(pv, ar, x1, x2p, which):
     for i in (1, 2, 3, 4):
         a[i][:] = 0
     off = pv.offsets
-    src = a[1] if which == 1 else a[2]
+    fwd = which != 2  # the transposed program reads OUT and writes IN
+    src = a[1] if fwd else a[2]
     src[off[8]:off[8] + x1.size] = x1.ravel()
     src[off[9]:off[9] + x2p.size] = x2p.ravel()
     plan_sim.run(pv.programs[which], a)
-    r = a[2] if which == 1 else a[1]
+    r = a[2] if fwd else a[1]
     return r[off[8]:off[8] + x1.size].reshape(x1.shape), r[off[9]:off[9] + x2p.size].reshape(x2p.shape)
 
 
@@ -101,3 +102,41 @@ def test_plan_simulation_matches_oracle(lib, nk, o, v, Q, ws):
     b1, b2 = b1.numpy(), b2.numpy() / nk
     assert np.abs(z1 - b1).max() < 1e-12 * np.abs(b1).max()
     assert np.abs(z2 - b2).max() < 1e-12 * np.abs(b2).max()
+
+
+def _put_mu(pv, ar, mu, o):
+    """One-body operator blocks oo, ov, vo, vv and ov^T into the FIX arena."""
+    nk = mu.shape[0]
+    off = int(pv.offsets[10])
+    blocks = [mu[:, :o, :o], mu[:, :o, o:], mu[:, o:, :o], mu[:, o:, o:], np.swapaxes(mu[:, :o, o:], 1, 2)]
+    for b in blocks:
+        ar[0][off:off + b.size] = np.ascontiguousarray(b).ravel()
+        off += b.size
+
+
+@pytest.mark.parametrize("nk,o,v,Q", [(2, 2, 3, 3), (3, 1, 2, 4)])
+def test_xi_and_egrad_programs(lib, nk, o, v, Q):
+    """Perturbation right-hand side xi^X(t) and the singles energy Hessian, simulated."""
+    p = make_problem(nk, o, v, Q, seed=8, sigma_l=0.2)
+    R = rcc.RCC(p)
+    t1, t2 = random_amplitudes(nk, o, v, seed=9, scale1=0.05, scale2=0.05)
+    pv, ar = _sim_setup(lib, p, t1, t2, 1 << 20)
+    mu = p.dip[2]
+    _put_mu(pv, ar, mu, o)
+    y1, y2 = _sim_apply(pv, ar, t1, t2 * nk, 3)
+    T = torch.as_tensor
+    x1, x2 = rcc.perturbation_rhs(R, T(t1), T(t2), T(mu))
+    assert np.abs(y1 - x1.numpy()).max() < 1e-13 * np.abs(x1.numpy()).max()
+    assert np.abs(y2 - nk * x2.numpy()).max() < 1e-13 * np.abs(nk * x2.numpy()).max()
+    # egrad: <w, egrad(u)> = d^2 E / dt^2 [u, w] restricted to singles
+    u1, _ = random_amplitudes(nk, o, v, seed=10, scale1=1, scale2=1)
+    w1, _ = random_amplitudes(nk, o, v, seed=11, scale1=1, scale2=1)
+    z = np.zeros((nk,) * 3 + (o, o, v, v), complex)
+    g1, _ = _sim_apply(pv, ar, u1, z, 4)
+    lhs = np.sum(w1 * g1)
+
+    def E(a):
+        return complex(R.energy(T(t1 + a[0] * u1 + a[1] * w1), T(t2)))
+    h = 1e-2
+    ref = (E((h, h)) - E((h, -h)) - E((-h, h)) + E((-h, -h))) / (4 * h * h)  # exact: E quadratic in t1
+    assert abs(lhs - ref) < 1e-11 * abs(ref)
