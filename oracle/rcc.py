@@ -409,6 +409,8 @@ def solve_response(R: RCC, t1, t2, xi1, xi2, omega, tol=1e-11, maxit=300, verbos
     p1, p2 = d1 - omega, d2 - omega
     x1, x2 = -xi1 / p1, -xi2 / p2
     nrm = _maxabs(xi1, xi2)
+    if nrm == 0.0:  # vanishing perturbation (Sec. II.C): the response amplitudes are zero
+        return x1, x2, 0
     diis = DIIS()
     for it in range(maxit):
         a1, a2 = R.jacobian(t1, t2, x1, x2)
