@@ -52,6 +52,11 @@ cudaError_t launch_gemm_f64(const GemmArgs& g, int tile, int nrhs, cudaStream_t 
 cudaError_t launch_perm_f64(const PermArgs& p, int nrhs, cudaStream_t st);
 cudaError_t launch_btrans_f64(const BTransArgs& t, int nrhs, cudaStream_t st);
 
+// Tensor-core GEMM (kernels_tc.cu): prec 1 = TF32, 2 = BF16x3; same semantics as the
+// FP64 kernel, FP32 accumulation.  *errflag is set when a bounded wait gives up.
+cudaError_t launch_gemm_tc(const GemmArgs& g, int prec, int nrhs, int* errflag, cudaStream_t st);
+size_t tc_smem_bytes(int prec);
+
 // DF factor split: L[k1][k2][Q][n][n] (paper units) -> oo/ov/vo/vv blocks * scale.
 cudaError_t launch_split_df(const double2* L, int nk, int Q, int o, int v, double scale, double2* Loo,
                             double2* Lov, double2* Lvo, double2* Lvv, cudaStream_t st);
