@@ -97,6 +97,24 @@ lrcc_status lrcc_jacobian_apply(lrcc_problem* p, int32_t transpose, int32_t nrhs
                                 const void* x2, void* y1, void* y2, const lrcc_options* opt,
                                 void* stream);
 
+/* Same product as lrcc_jacobian_apply for one vector (nrhs = 1), for callers that
+ * cannot let a library allocate device memory at call time (host applications that
+ * own the device allocator, latency-critical loops that cannot absorb cudaMalloc's
+ * implicit synchronization).  The paper has no counterpart; this is a property of
+ * the library.  The staging vectors and the per-vector scratch live in one static
+ * device array of 4 Mi complex128 elements (64 MiB) that every GPU loading the
+ * library keeps until exit; the problem's own buffers (allocated by lrcc_create and
+ * lrcc_set_ground_state) are used as they are.  Calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Problems whose vectors plus scratch exceed the array
+ * return LRCC_EUNSUPPORTED with the sizes in lrcc_last_error.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call, from any
+ * problem, shares the one array: calls whose GPU work overlaps in time race and give
+ * wrong results, so serialize them (for example on one stream).  Asynchronous on
+ * `stream`; x and y are device pointers laid out as for lrcc_jacobian_apply. */
+lrcc_status lrcc_jacobian_apply_noalloc(lrcc_problem* p, int32_t transpose, const void* x1, const void* x2,
+                                        void* y1, void* y2, void* stream);
+
 /* Polarizability alpha_XY(w) per cell (Eq. 15, symmetric form), a.u., for the
  * dipole components comps[0..ncomp) (0 = x, 1 = y, 2 = z) and frequencies
  * omegas[0..nomega).  alpha receives c128 [nomega][ncomp][ncomp] in host memory.

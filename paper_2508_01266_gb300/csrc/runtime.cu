@@ -223,10 +223,6 @@ lrcc_status Runtime::apply(int transpose, int nrhs, cudaStream_t st) {
 
 using namespace lrcc;
 
-struct lrcc_problem {
-  Runtime rt;
-  bool have_int = false, have_t = false, have_l = false;
-};
 
 static lrcc_status fail(lrcc_problem* p, lrcc_status s, const std::string& m) {
   if (p) p->rt.err = m;

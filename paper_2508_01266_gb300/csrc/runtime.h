@@ -49,6 +49,11 @@ struct Runtime {
 
 }  // namespace lrcc
 
+struct lrcc_problem {
+  lrcc::Runtime rt;
+  bool have_int = false, have_t = false, have_l = false;
+};
+
 // Polarizability driver (solver.cu).
 lrcc_status lrcc_polarize_impl(lrcc::Runtime& rt, bool have_t, bool have_l, const int32_t* comps, int32_t ncomp,
                                const double* omegas, int32_t nomega, const lrcc_options* opt, void* alpha,
