@@ -100,6 +100,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _measured_peak(key, fallback):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except Exception:
+        return fallback
+
+
 def workload(cfg_name):
     from synth import CONFIGS
     c = dict(CONFIGS[cfg_name])
@@ -171,6 +179,7 @@ def main():
     ap.add_argument("--nrhs", type=int, default=0, help="vectors per step (default: all systems of the workload)")
     ap.add_argument("--ref-blocks", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -272,6 +281,39 @@ def main():
             "ladder_share_of_step": lad_ms / max(all_ms, 1e-9), "wbuild_share_of_step": wb_ms / max(all_ms, 1e-9),
             "step_gflops_algorithmic": all_fl / (all_ms * 1e-3) / 1e9 if all_ms else None}
 
+    # mixed precision: the same product with the GEMMs on tcgen05 (BF16x3 and TF32, FP32 accumulate)
+    mixed = {}
+    if not args.no_mixed:
+        BF16_PEAK = _measured_peak("bf16_tflops", 1900.0)
+        for prec, name, peak, passes in ((2, "bf16x3", BF16_PEAK, 3), (1, "tf32", BF16_PEAK * 1.1 / 2.25, 1)):
+            opts = lr.default_options(precision=prec)
+            M1, M2 = torch.empty_like(Y1), torch.empty_like(Y2)
+            for _ in range(args.warmup):
+                prob.jacobian_apply(X1, X2, y1=M1, y2=M2, options=opts)
+            torch.cuda.synchronize()
+            prob.profile(True)
+            m0 = prob.kernel_launches
+            e0.record(st)
+            for _ in range(args.steps):
+                prob.jacobian_apply(X1, X2, y1=M1, y2=M2, options=opts)
+            e1.record(st)
+            torch.cuda.synchronize()
+            mms = _max_over_ranks(dist, e0.elapsed_time(e1))
+            lms, ln, lfl = prob.profile_query("ladder")
+            ams, an, afl = prob.profile_query("")
+            prob.profile(False)
+            err = max(float((M1 - Y1).abs().max() / Y1.abs().max()), float((M2 - Y2).abs().max() / Y2.abs().max()))
+            lach = (lfl / max(ln, 1)) / ((lms / max(ln, 1)) * 1e-3) / 1e12 if ln else None
+            mixed[name] = {"value": products / (mms / 1000.0), "unit": "products/s", "ms_per_step": mms / args.steps,
+                           "gpu_launches": int(prob.kernel_launches - m0),
+                           "max_rel_err_vs_fp64": err,
+                           "ladder": {"achieved_tflops_algorithmic": lach,
+                                      "tensor_pipe_tflops": lach * passes if lach else None,
+                                      "peak_tflops": peak, "frac": (lach * passes / peak) if lach else None,
+                                      "peak_source": "measured bf16 dense (MEASURED_PEAKS.json)" if prec == 2 else
+                                      "measured bf16 x nominal tf32/bf16 ratio 1.1/2.25"},
+                           "step_tflops_algorithmic": afl / (ams * 1e-3) / 1e12 if ams else None}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         r, dt, threads, sample = cpu_oracle_rate(cfg, args.ref_blocks)
@@ -287,6 +329,7 @@ def main():
                            "precision": "fp64", "rhs_per_step": nrhs, "parallelism": f"replicas x{ws}",
                            "l2": "working set larger than L2 (vector 205 MB, intermediates > 1 GB)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "mixed_precision": mixed,
                 "clocks": clk}
         print(json.dumps(line), flush=True)
     prob.close()

@@ -92,7 +92,12 @@ lrcc_status lrcc_set_ground_state(lrcc_problem* p, const void* t1, const void* t
  * along x (the left-hand side of Eqs. 13-14, i.e. -D t plus all J terms);
  * transpose == 1:  y = P_sym A^T x under the plain array pairing
  * sum x1 y1 + sum x2 y2 (the Lambda-type product of Eqs. 10-11), P_sym = pair
- * symmetrization.  x and y must not overlap.  Asynchronous on `stream`. */
+ * symmetrization.  x and y must not overlap.  opt->precision selects the GEMM
+ * arithmetic: 0 FP64; 1 TF32 and 2 BF16x3 (operands split in bf16 hi + lo, three
+ * products) on the tcgen05 tensor cores with FP32 accumulation (data stay FP64 in
+ * memory).  Asynchronous on `stream` for precision 0; the tensor-core modes
+ * synchronize the stream once at the end to read the kernels' error flag
+ * (LRCC_ETIMEOUT if a bounded wait gave up). */
 lrcc_status lrcc_jacobian_apply(lrcc_problem* p, int32_t transpose, int32_t nrhs, const void* x1,
                                 const void* x2, void* y1, void* y2, const lrcc_options* opt,
                                 void* stream);

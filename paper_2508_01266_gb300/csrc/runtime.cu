@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lrcc.h"
 #include "kernels.cuh"
 #include "plan.h"
@@ -46,8 +48,9 @@ void Runtime::release() {
   for (cudaEvent_t e : prof_pool) cudaEventDestroy(e);
   prof_pool.clear();
   for (void* p : {(void*)fix, (void*)in, (void*)out, (void*)scr, (void*)ws, (void*)desc, (void*)dip, (void*)l1,
-                  (void*)l2})
+                  (void*)l2, (void*)dflag})
     if (p) cudaFree(p);
+  dflag = nullptr;
   fix = in = out = scr = ws = nullptr;
   desc = nullptr;
   dip = l1 = l2 = nullptr;
@@ -112,6 +115,8 @@ lrcc_status Runtime::init(const lrcc_dims& d, int64_t ws_budget) {
     return LRCC_ENOMEM;
   if (!ck(cudaMalloc(&dip, 3 * nk * n * n * sizeof(double2)), "cudaMalloc(dipoles)")) return LRCC_ENOMEM;
   if (!ck(cudaMemset(fix, 0, plan.arena_size[AR_FIX] * sizeof(double2)), "cudaMemset")) return LRCC_ECUDA;
+  if (!ck(cudaMalloc(&dflag, sizeof(int)), "cudaMalloc(flag)")) return LRCC_ENOMEM;
+  if (!ck(cudaMemset(dflag, 0, sizeof(int)), "cudaMemset(flag)")) return LRCC_ECUDA;
   return LRCC_OK;
 }
 
@@ -132,11 +137,15 @@ lrcc_status Runtime::ensure_rhs(int nrhs) {
   return LRCC_OK;
 }
 
-lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrhs, cudaStream_t st) {
+lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrhs, cudaStream_t st, int prec) {
   long long stride[AR_COUNT] = {0, plan.arena_size[AR_IN], plan.arena_size[AR_OUT], plan.arena_size[AR_SCR], 0};
   for (const Op& op : pr.ops) {
     cudaError_t e = cudaSuccess;
     const int nr = op.fixed_only ? 1 : nrhs;
+    const char* optag = op.kind == OP_GEMM ? plan.gemms[op.idx].tag.c_str()
+                        : op.kind == OP_PERM ? plan.perms[op.idx].tag.c_str()
+                                             : plan.btrans[op.idx].tag.c_str();
+    nvtxRangePushA(optag);  // per-op range (ncu --nvtx --nvtx-include "<tag>/")
     ProfRec rec{};
     if (prof) {
       rec.a = prof_event();
@@ -167,7 +176,7 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
       a.sA = op.fixed_only ? 0 : stride[g.arA];
       a.sB = op.fixed_only ? 0 : stride[g.arB];
       a.sC = op.fixed_only ? 0 : stride[g.arC];
-      e = launch_gemm_f64(a, d.tile, nr, st);
+      e = prec > 0 ? launch_gemm_tc(a, prec, nr, dflag, st) : launch_gemm_f64(a, d.tile, nr, st);
       ++launches;
     } else if (op.kind == OP_PERM) {
       const Perm& p = plan.perms[op.idx];
@@ -203,12 +212,24 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
       cudaEventRecord(rec.b, st);
       prof_recs.push_back(rec);
     }
+    nvtxRangePop();
     if (!ck(e, "kernel launch")) return LRCC_ECUDA;
+  }
+  if (prec > 0) {
+    int h = 0;
+    if (!ck(cudaMemcpyAsync(&h, dflag, sizeof(int), cudaMemcpyDeviceToHost, st), "flag read") ||
+        !ck(cudaStreamSynchronize(st), "flag sync"))
+      return LRCC_ECUDA;
+    if (h) {
+      cudaMemsetAsync(dflag, 0, sizeof(int), st);
+      err = "tensor-core GEMM: a bounded wait on an mbarrier gave up";
+      return LRCC_ETIMEOUT;
+    }
   }
   return LRCC_OK;
 }
 
-lrcc_status Runtime::apply(int transpose, int nrhs, cudaStream_t st) {
+lrcc_status Runtime::apply(int transpose, int nrhs, cudaStream_t st, int prec) {
   double2* ar[AR_COUNT] = {fix, in, out, scr, ws};
   const int64_t vin = plan.arena_size[AR_IN], vscr = plan.arena_size[AR_SCR];
   // zero the result side and the scratch (every op accumulates)
@@ -216,7 +237,7 @@ lrcc_status Runtime::apply(int transpose, int nrhs, cudaStream_t st) {
   if (!ck(cudaMemsetAsync(res, 0, vin * nrhs * sizeof(double2), st), "cudaMemsetAsync")) return LRCC_ECUDA;
   if (vscr > 0 && !ck(cudaMemsetAsync(scr, 0, vscr * nrhs * sizeof(double2), st), "cudaMemsetAsync"))
     return LRCC_ECUDA;
-  return run(transpose ? jacT : plan.jac, ar, nrhs, st);
+  return run(transpose ? jacT : plan.jac, ar, nrhs, st, prec);
 }
 
 }  // namespace lrcc
@@ -361,8 +382,8 @@ lrcc_status lrcc_jacobian_apply(lrcc_problem* p, int32_t transpose, int32_t nrhs
   if (!p->have_t) return fail(p, LRCC_EINVAL, "jacobian_apply: ground state not set");
   if (nrhs < 1 || !x1 || !x2 || !y1 || !y2 || (transpose != 0 && transpose != 1))
     return fail(p, LRCC_EINVAL, "jacobian_apply: bad arguments");
-  if (opt && opt->precision != 0)
-    return fail(p, LRCC_EUNSUPPORTED, "jacobian_apply: only precision 0 (FP64) in this call");
+  const int prec = opt ? opt->precision : 0;
+  if (prec < 0 || prec > 2) return fail(p, LRCC_EINVAL, "jacobian_apply: precision must be 0, 1 or 2");
   Runtime& rt = p->rt;
   lrcc_status s = rt.ensure_rhs(nrhs);
   if (s != LRCC_OK) return s;
@@ -376,7 +397,7 @@ lrcc_status lrcc_jacobian_apply(lrcc_problem* p, int32_t transpose, int32_t nrhs
   if (!rt.ck(cudaMemcpy2DAsync(src + P.off_x1, pitch, x1, b1, b1, nrhs, cudaMemcpyDeviceToDevice, st), "copy x1") ||
       !rt.ck(cudaMemcpy2DAsync(src + P.off_x2, pitch, x2, b2, b2, nrhs, cudaMemcpyDeviceToDevice, st), "copy x2"))
     return LRCC_ECUDA;
-  s = rt.apply(transpose, nrhs, st);
+  s = rt.apply(transpose, nrhs, st, prec);
   if (s != LRCC_OK) return s;
   if (!rt.ck(cudaMemcpy2DAsync(y1, b1, dst + P.off_x1, pitch, b1, nrhs, cudaMemcpyDeviceToDevice, st), "copy y1") ||
       !rt.ck(cudaMemcpy2DAsync(y2, b2, dst + P.off_x2, pitch, b2, nrhs, cudaMemcpyDeviceToDevice, st), "copy y2"))

@@ -41,8 +41,10 @@ struct Runtime {
   bool ck(cudaError_t e, const char* what);
   lrcc_status init(const lrcc_dims& d, int64_t ws_budget);
   lrcc_status ensure_rhs(int nrhs);
-  lrcc_status run(const Program& pr, double2* const ar[AR_COUNT], int nrhs, cudaStream_t st);
-  lrcc_status apply(int transpose, int nrhs, cudaStream_t st);
+  int* dflag = nullptr;  // device error flag of the tensor-core kernels (bounded waits)
+  // prec: 0 FP64 kernels; 1 TF32 and 2 BF16x3 tensor-core GEMMs (FP32 accumulation)
+  lrcc_status run(const Program& pr, double2* const ar[AR_COUNT], int nrhs, cudaStream_t st, int prec = 0);
+  lrcc_status apply(int transpose, int nrhs, cudaStream_t st, int prec = 0);
   void release();
   void prof_reset();
 };

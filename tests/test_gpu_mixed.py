@@ -1,0 +1,48 @@
+"""Tensor-core (tcgen05) Jacobian products against the FP64 products.
+
+TF32 keeps 10 mantissa bits per operand and BF16x3 about 16; both accumulate in FP32.
+Bounds below are the expected rounding of the products relative to the largest
+output element.
+"""
+import numpy as np
+import pytest
+import torch
+
+from synth import make_problem, random_amplitudes, CONFIGS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lr():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2508_01266_gb300 as m
+    return m
+
+
+def _setup(lr, nk, o, v, Q, seed=11):
+    p = make_problem(nk, o, v, Q, seed=seed, sigma_l=0.1)
+    t1, t2 = random_amplitudes(nk, o, v, seed=seed + 1, scale1=0.02, scale2=0.02)
+    prob = lr.Problem(nk, o, v, Q)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    prob.set_ground_state(t1, t2 * nk)
+    return prob
+
+
+@pytest.mark.parametrize("nk,o,v,Q", [(2, 1, 3, 5), (3, 2, 4, 6), (3, 4, 16, 48)])
+@pytest.mark.parametrize("prec,bound", [(1, 3e-3), (2, 3e-5)])
+def test_mixed_products_vs_fp64(lr, nk, o, v, Q, prec, bound):
+    prob = _setup(lr, nk, o, v, Q)
+    dev = torch.device("cuda")
+    x1, x2 = random_amplitudes(nk, o, v, seed=5, scale1=1.0, scale2=1.0)
+    X1 = torch.as_tensor(x1, device=dev)[None].contiguous()
+    X2 = torch.as_tensor(x2 * nk, device=dev)[None].contiguous()
+    for tr in (False, True):
+        r1, r2 = prob.jacobian_apply(X1, X2, transpose=tr)
+        m1, m2 = prob.jacobian_apply(X1, X2, transpose=tr, options=lr.default_options(precision=prec))
+        e1 = float((m1 - r1).abs().max() / r1.abs().max())
+        e2 = float((m2 - r2).abs().max() / r2.abs().max())
+        print(f"prec {prec} transpose {tr}: rel err singles {e1:.2e} doubles {e2:.2e}")
+        assert e1 < bound and e2 < bound
+    prob.close()

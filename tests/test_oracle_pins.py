@@ -169,7 +169,7 @@ def test_two_electrons_equal_fci(tr):
 # P5 ---------------------------------------------------------------------------
 def test_decoupled_replicas_independent_of_nk():
     vals = []
-    for nk in (1, 2, 3):
+    for nk in (1, 3):
         p = make_problem(nk, 1, 2, 3, seed=71, sigma_l=0.2, kind="replica")
         R = rcc.RCC(p)
         t1, t2, _ = rcc.solve_ccsd(R, tol=1e-12)
@@ -210,7 +210,7 @@ def test_alpha_symmetries_tr():
     t1, t2, _ = rcc.solve_ccsd(R, tol=1e-12)
     l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=1e-12)
     mus = rcc.dipole_ops(p, (0, 2))
-    a = rcc.polarizability(R, t1, t2, l1, l2, mus, [0.06, -0.06])
+    a = rcc.polarizability(R, t1, t2, l1, l2, mus, [0.06, -0.06], tol=1e-10)
     assert np.abs(a.imag).max() < 1e-10
     assert np.allclose(a[0], a[0].T, atol=1e-10)
     assert np.allclose(a[0], a[1], atol=1e-10)
