@@ -101,9 +101,9 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
   lrcc_options opt;
   lrcc_default_options(&opt);
   if (optp) opt = *optp;
-  if (opt.precision != 0) {
-    rt.err = "polarizability: only precision 0 (FP64) in this call";
-    return LRCC_EUNSUPPORTED;
+  if (opt.precision < 0 || opt.precision > 2) {
+    rt.err = "polarizability: precision must be 0, 1 or 2";
+    return LRCC_EINVAL;
   }
   for (int c = 0; c < ncomp; ++c)
     if (comps[c] < 0 || comps[c] > 2) {
@@ -232,11 +232,11 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
     CK(cudaMemcpy(rt.fix + P.off_mu, blk.data(), blk.size() * sizeof(double2), cudaMemcpyHostToDevice), "mu");
     return LRCC_OK;
   };
-  auto rebuild_ground = [&]() -> lrcc_status {
+  auto rebuild_ground = [&](int gprec) -> lrcc_status {
     CK(cudaMemsetAsync(rt.fix + P.off_derived, 0, (P.arena_size[AR_FIX] - P.off_derived) * sizeof(double2), st),
        "memset derived");
     double2* ar[AR_COUNT] = {rt.fix, nullptr, nullptr, nullptr, rt.ws};
-    return rt.run(P.ground, ar, 1, st);
+    return rt.run(P.ground, ar, 1, st, gprec);
   };
   auto maxabs = [&](const double2* x, int nrhs, std::vector<double>& out) -> lrcc_status {
     CK(cudaMemsetAsync(RMAX, 0, nrhs * sizeof(unsigned long long), st), "memset");
@@ -314,95 +314,145 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
   if ((s = maxabs(XI, ns, ximax)) != LRCC_OK) return s;
 
   // 2. batched solve -------------------------------------------------------------------
-  CK(launch_guess(XI, DEN, OM, rt.in, vec, vec, ns, st), "guess");
-  rt.launches++;
-  std::vector<std::vector<cd>> Bm(ns, std::vector<cd>(depth * depth, 0.0));
-  std::vector<int> slot_of(depth, -1);  // history age bookkeeping: slots used in order
-  int nhist = 0, it = 0;
-  bool converged = false;
+  // Jacobi + DIIS on (A - w) x = -rhs for every system, iterate in rt.in; prec selects the
+  // GEMM arithmetic of the products.  Returns the relative residual reached in rel.
   std::vector<double> rel(ns, 1.0);
-  for (it = 0; it < maxit; ++it) {
-    if ((s = rt.apply(0, ns, st)) != LRCC_OK) return s;
-    const int slot = it % depth;
-    CK(cudaMemsetAsync(RMAX, 0, ns * sizeof(unsigned long long), st), "memset");
-    CK(launch_update(rt.in, rt.out, XI, DEN, OM, HE + (size_t)slot * ns * vec, HX + (size_t)slot * ns * vec, RMAX,
-                     vec, vec, ns, st),
-       "update");
+  int total_it = 0;
+  auto jacobi_diis = [&](const double2* rhs, const std::vector<double>& rhsmax, int prec, double tol, int maxiter,
+                         bool& conv) -> lrcc_status {
+    lrcc_status s2;
+    CK(launch_guess(rhs, DEN, OM, rt.in, vec, vec, ns, st), "guess");
     rt.launches++;
-    std::vector<unsigned long long> hr(ns);
-    CK(cudaMemcpy(hr.data(), RMAX, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "rmax");
-    double worst = 0.0;
-    for (int i = 0; i < ns; ++i) {
-      rel[i] = u64_to_double(hr[i]) / std::max(ximax[i], 1e-300);
-      worst = std::max(worst, rel[i]);
-    }
-    if (worst <= opt.conv_tol) {
-      converged = true;
-      break;
-    }
-    nhist = std::min(nhist + 1, depth);
-    // new row of the Hermitian error matrix for every system
-    std::vector<const double2*> pa, pb;
-    std::vector<int> slots;
-    for (int j = 0; j < nhist; ++j) {
-      const int sj = ((it - j) % depth + depth) % depth;
-      slots.push_back(sj);
+    std::vector<std::vector<cd>> Bm(ns, std::vector<cd>(depth * depth, 0.0));
+    int nhist = 0;
+    conv = false;
+    for (int it = 0; it < maxiter; ++it) {
+      ++total_it;
+      if ((s2 = rt.apply(0, ns, st, prec)) != LRCC_OK) return s2;
+      const int slot = it % depth;
+      CK(cudaMemsetAsync(RMAX, 0, ns * sizeof(unsigned long long), st), "memset");
+      CK(launch_update(rt.in, rt.out, rhs, DEN, OM, HE + (size_t)slot * ns * vec, HX + (size_t)slot * ns * vec, RMAX,
+                       vec, vec, ns, st),
+         "update");
+      rt.launches++;
+      std::vector<unsigned long long> hr(ns);
+      CK(cudaMemcpy(hr.data(), RMAX, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "rmax");
+      double worst = 0.0;
       for (int i = 0; i < ns; ++i) {
-        pa.push_back(HE + ((size_t)slot * ns + i) * vec);
-        pb.push_back(HE + ((size_t)sj * ns + i) * vec);
+        rel[i] = u64_to_double(hr[i]) / std::max(rhsmax[i], 1e-300);
+        worst = std::max(worst, rel[i]);
       }
-    }
-    std::vector<cd> row;
-    if ((s = dots(pa, pb, 1, vec, row)) != LRCC_OK) return s;
-    for (int j = 0; j < nhist; ++j)
-      for (int i = 0; i < ns; ++i) {
-        const int sj = slots[j];
-        Bm[i][slot * depth + sj] = row[j * ns + i];
-        Bm[i][sj * depth + slot] = std::conj(row[j * ns + i]);
+      if (worst <= tol) {
+        conv = true;
+        return LRCC_OK;
       }
-    std::vector<double2> coef((size_t)nhist * ns, make_double2(0.0, 0.0));
-    for (int i = 0; i < ns; ++i) {
-      std::vector<cd> x;
-      bool good = false;
-      if (nhist >= 2 && (opt.diis_period <= 1 || (it + 1) % opt.diis_period == 0)) {
-        const int m = nhist + 1;
-        std::vector<cd> A(m * m, 0.0), b(m, 0.0);
-        double sc = 0.0;
-        for (int a = 0; a < nhist; ++a) sc = std::max(sc, std::abs(Bm[i][slots[a] * depth + slots[a]]));
-        sc = sc > 0 ? 1.0 / sc : 1.0;
-        for (int a = 0; a < nhist; ++a) {
-          for (int c = 0; c < nhist; ++c) A[a * m + c] = sc * Bm[i][slots[a] * depth + slots[c]];
-          A[a * m + nhist] = -1.0;
-          A[nhist * m + a] = -1.0;
-        }
-        b[nhist] = -1.0;
-        good = solve_small(A, b, m, x);
-      }
+      nhist = std::min(nhist + 1, depth);
+      std::vector<const double2*> pa, pb;
+      std::vector<int> slots;
       for (int j = 0; j < nhist; ++j) {
-        cd cj = good ? x[j] : (j == 0 ? cd(1.0) : cd(0.0));
-        coef[(size_t)j * ns + i] = make_double2(cj.real(), cj.imag());
+        const int sj = ((it - j) % depth + depth) % depth;
+        slots.push_back(sj);
+        for (int i = 0; i < ns; ++i) {
+          pa.push_back(HE + ((size_t)slot * ns + i) * vec);
+          pb.push_back(HE + ((size_t)sj * ns + i) * vec);
+        }
+      }
+      std::vector<cd> row;
+      if ((s2 = dots(pa, pb, 1, vec, row)) != LRCC_OK) return s2;
+      for (int j = 0; j < nhist; ++j)
+        for (int i = 0; i < ns; ++i) {
+          const int sj = slots[j];
+          Bm[i][slot * depth + sj] = row[j * ns + i];
+          Bm[i][sj * depth + slot] = std::conj(row[j * ns + i]);
+        }
+      std::vector<double2> coef((size_t)nhist * ns, make_double2(0.0, 0.0));
+      for (int i = 0; i < ns; ++i) {
+        std::vector<cd> x;
+        bool good = false;
+        if (nhist >= 2 && (opt.diis_period <= 1 || (it + 1) % opt.diis_period == 0)) {
+          const int m = nhist + 1;
+          std::vector<cd> A(m * m, 0.0), b(m, 0.0);
+          double sc = 0.0;
+          for (int a = 0; a < nhist; ++a) sc = std::max(sc, std::abs(Bm[i][slots[a] * depth + slots[a]]));
+          sc = sc > 0 ? 1.0 / sc : 1.0;
+          for (int a = 0; a < nhist; ++a) {
+            for (int c = 0; c < nhist; ++c) A[a * m + c] = sc * Bm[i][slots[a] * depth + slots[c]];
+            A[a * m + nhist] = -1.0;
+            A[nhist * m + a] = -1.0;
+          }
+          b[nhist] = -1.0;
+          good = solve_small(A, b, m, x);
+        }
+        for (int j = 0; j < nhist; ++j) {
+          cd cj = good ? x[j] : (j == 0 ? cd(1.0) : cd(0.0));
+          coef[(size_t)j * ns + i] = make_double2(cj.real(), cj.imag());
+        }
+      }
+      std::vector<const double2*> pv(nhist);
+      for (int j = 0; j < nhist; ++j) pv[j] = HX + (size_t)slots[j] * ns * vec;
+      CK(cudaMemcpy(PV, pv.data(), nhist * sizeof(void*), cudaMemcpyHostToDevice), "pv");
+      CK(cudaMemcpy(COEF, coef.data(), coef.size() * sizeof(double2), cudaMemcpyHostToDevice), "coef");
+      CK(launch_lincomb(PV, COEF, nhist, rt.in, vec, vec, ns, st), "lincomb");
+      rt.launches++;
+    }
+    return LRCC_OK;
+  };
+
+  bool converged = false;
+  const int prec = opt.precision;
+  if (prec == 0) {
+    if ((s = jacobi_diis(XI, ximax, 0, opt.conv_tol, maxit, converged)) != LRCC_OK) return s;
+    CK(cudaMemcpy(SOL, rt.in, (size_t)ns * vec * sizeof(double2), cudaMemcpyDeviceToDevice), "sol");
+  } else {
+    // iterative refinement: FP64 residual r = -xi - (A - w) x, tensor-core inner solve of
+    // (A - w) d = r to a loose tolerance, x += d, until max|r| / max|xi| <= refine_tol.
+    CK(launch_guess(XI, DEN, OM, SOL, vec, vec, ns, st), "guess");
+    rt.launches++;
+    const double tol64 = std::min(opt.refine_tol, 1e-3);
+    const double inner_tol = prec == 1 ? 3e-3 : 1e-4;
+    for (int outer = 0; outer < 40 && !converged; ++outer) {
+      CK(cudaMemcpy(rt.in, SOL, (size_t)ns * vec * sizeof(double2), cudaMemcpyDeviceToDevice), "x -> in");
+      if ((s = rt.apply(0, ns, st, 0)) != LRCC_OK) return s;
+      ++total_it;
+      // R = xi + A x - w x = -r ; its max is the FP64 residual
+      CK(cudaMemsetAsync(RMAX, 0, ns * sizeof(unsigned long long), st), "memset");
+      CK(launch_residual(rt.in, rt.out, XI, OM, FU, RMAX, vec, vec, ns, st), "residual");
+      rt.launches++;
+      std::vector<unsigned long long> hr(ns);
+      CK(cudaMemcpy(hr.data(), RMAX, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "rmax");
+      double worst = 0.0;
+      std::vector<double> rmx(ns);
+      for (int i = 0; i < ns; ++i) {
+        rmx[i] = u64_to_double(hr[i]);
+        rel[i] = rmx[i] / std::max(ximax[i], 1e-300);
+        worst = std::max(worst, rel[i]);
+      }
+      if (worst <= tol64) {
+        converged = true;
+        break;
+      }
+      bool inner_conv = false;
+      if ((s = jacobi_diis(FU, rmx, prec, inner_tol, maxit, inner_conv)) != LRCC_OK) return s;
+      for (int i = 0; i < ns; ++i) {
+        CK(launch_axpby(make_double2(1.0, 0.0), rt.in + (size_t)i * vec, make_double2(1.0, 0.0), SOL + (size_t)i * vec,
+                        vec, st),
+           "x += d");
+        rt.launches++;
       }
     }
-    std::vector<const double2*> pv(nhist);
-    for (int j = 0; j < nhist; ++j) pv[j] = HX + (size_t)slots[j] * ns * vec;
-    CK(cudaMemcpy(PV, pv.data(), nhist * sizeof(void*), cudaMemcpyHostToDevice), "pv");
-    CK(cudaMemcpy(COEF, coef.data(), coef.size() * sizeof(double2), cudaMemcpyHostToDevice), "coef");
-    CK(launch_lincomb(PV, COEF, nhist, rt.in, vec, vec, ns, st), "lincomb");
-    rt.launches++;
   }
   if (info) {
-    info[0] = it + 1;
+    info[0] = total_it;
     info[1] = converged ? 0 : LRCC_ENOCONV;
   }
   if (!converged) {
     rt.err = "polarizability: response equations did not converge";
     return LRCC_ENOCONV;
   }
-  CK(cudaMemcpy(SOL, rt.in, (size_t)ns * vec * sizeof(double2), cudaMemcpyDeviceToDevice), "sol");
   std::vector<double> umax;
   if ((s = maxabs(SOL, ns, umax)) != LRCC_OK) return s;
   std::vector<double> hstep(ns);
-  for (int i = 0; i < ns; ++i) hstep[i] = 1e-2 / std::max(umax[i], 1e-300);
+  for (int i = 0; i < ns; ++i) hstep[i] = (opt.precision ? 1e-1 : 1e-2) / std::max(umax[i], 1e-300);
   const double c4[4] = {-2.0, -1.0, 1.0, 2.0}, w4[4] = {1.0, -8.0, 8.0, -1.0};
 
   // 3a. eta^X . t_sys for every active component and every solution -----------------
@@ -448,9 +498,9 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
                       st),
          "t2 + s u2");
       rt.launches += 2;
-      if ((s = rebuild_ground()) != LRCC_OK) return s;
+      if ((s = rebuild_ground(opt.precision)) != LRCC_OK) return s;
       CK(cudaMemcpy(rt.out, LAM, vec * sizeof(double2), cudaMemcpyDeviceToDevice), "lam -> out");
-      if ((s = rt.apply(1, 1, st)) != LRCC_OK) return s;
+      if ((s = rt.apply(1, 1, st, opt.precision)) != LRCC_OK) return s;
       CK(launch_axpby(make_double2(w4[k] / (12.0 * hstep[i]), 0.0), rt.in, make_double2(1.0, 0.0),
                       FU + (size_t)i * vec, vec, st),
          "F u");
@@ -461,10 +511,10 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
     CK(launch_axpby(make_double2(1.0, 0.0), rt.out, make_double2(1.0, 0.0), FU + (size_t)i * vec, vec, st), "egrad");
     rt.launches++;
   }
-  // restore the ground-state intermediates
+  // restore the ground-state intermediates (FP64)
   CK(cudaMemcpy(rt.fix + P.off_t1, TV + P.off_x1, n1 * sizeof(double2), cudaMemcpyDeviceToDevice), "t1");
   CK(cudaMemcpy(rt.fix + P.off_t2, TV + P.off_x2, n2 * sizeof(double2), cudaMemcpyDeviceToDevice), "t2");
-  if ((s = rebuild_ground()) != LRCC_OK) return s;
+  if ((s = rebuild_ground(0)) != LRCC_OK) return s;
   std::vector<const double2*> pa, pb;
   for (int a = 0; a < ns; ++a)
     for (int b = 0; b < ns; ++b) {

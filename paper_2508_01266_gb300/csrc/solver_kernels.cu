@@ -55,6 +55,36 @@ cudaError_t launch_update(const double2* x, const double2* y, const double2* xi,
   return cudaGetLastError();
 }
 
+// R = xi + y - w x (the negated residual of (A - w) x = -xi); rmax[r] = max |R|
+__global__ void residual_kernel(const double2* x, const double2* y, const double2* xi, const double* omega,
+                                double2* R, unsigned long long* rmax, long long n, long long stride) {
+  const long long r = blockIdx.y;
+  const double w = omega[r];
+  double m = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long q = r * stride + i;
+    const double2 xv = x[q], yv = y[q], s = xi[q];
+    const double rr = s.x + yv.x - w * xv.x, ri = s.y + yv.y - w * xv.y;
+    R[q] = make_double2(rr, ri);
+    m = fmax(m, sqrt(rr * rr + ri * ri));
+  }
+  __shared__ double sm[256];
+  sm[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMax(rmax + r, (unsigned long long)__double_as_longlong(sm[0]));
+}
+
+cudaError_t launch_residual(const double2* x, const double2* y, const double2* xi, const double* omega, double2* R,
+                            unsigned long long* rmax, long long n, long long stride, int nrhs, cudaStream_t st) {
+  dim3 grid(grid_for(n, 256 * 4), nrhs);
+  residual_kernel<<<grid, 256, 0, st>>>(x, y, xi, omega, R, rmax, n, stride);
+  return cudaGetLastError();
+}
+
 // x0 = -xi / (den - w)
 __global__ void guess_kernel(const double2* xi, const double* den, const double* omega, double2* x, long long n,
                              long long stride) {

@@ -75,3 +75,25 @@ def test_alpha_c1_vs_oracle(lr):
     rel = np.abs(got - ref).max() / np.abs(ref).max()
     print("C1 alpha_zz gpu", got.ravel(), "oracle", ref.ravel(), "rel", rel)
     assert rel < 1e-8
+
+
+@pytest.mark.parametrize("prec", [2, 1])
+def test_alpha_mixed_precision_c1(lr, prec):
+    """Tensor-core inner solves + FP64 iterative refinement: |alpha - alpha_oracle| <= 1e-5 a.u."""
+    c = CONFIGS["c1"]
+    p = make_problem(c["nk"], c["nocc"], c["nvir"], c["naux"], seed=1266)
+    nk, o, v, Q = p.nk, p.nocc, p.nvir, p.naux
+    R = rcc.RCC(p)
+    t1, t2, _ = rcc.solve_ccsd(R, tol=1e-10)
+    l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=1e-10)
+    ref = rcc.polarizability(R, t1, t2, l1, l2, rcc.dipole_ops(p, [2]), [0.0, 0.1], tol=1e-11)
+    pl1, pl2 = paper_lambda(nk, l1, l2)
+    prob = lr.Problem(nk, o, v, Q)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    prob.set_ground_state(t1, t2 * nk, pl1, pl2)
+    got, info = prob.polarizability([2], [0.0, 0.1], lr.default_options(precision=prec, refine_tol=1e-8))
+    prob.close()
+    err = np.abs(got - ref).max()
+    print(f"C1 alpha_zz prec {prec}: {got.ravel()} oracle {ref.ravel()} |err| {err:.2e} iterations {info[0]}")
+    assert info[1] == 0
+    assert err <= 1e-5
