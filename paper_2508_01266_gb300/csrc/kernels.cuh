@@ -57,6 +57,38 @@ cudaError_t launch_btrans_f64(const BTransArgs& t, int nrhs, cudaStream_t st);
 cudaError_t launch_gemm_tc(const GemmArgs& g, int prec, int nrhs, int* errflag, cudaStream_t st);
 size_t tc_smem_bytes(int prec);
 
+// Packed-operand tensor-core GEMM (kernels_tcp.cu).
+struct PackArgs {
+  const double2* src;          // arena base (per-vector stride sS)
+  unsigned char* dst;          // packed output (per-vector stride sD)
+  long long sS, sD;
+  const long long* offs;       // element offset of each operand in the arena
+  int count;                   // number of operands
+  int R, K;                    // complex rows and K of every operand
+  long long ld;
+  int trans;                   // 0: element (r,k) at r*ld + k; 1: at k*ld + r
+  int mode;                    // 0: left operand (A), 1: right operand (B, 2x2 expanded)
+  long long packed_bytes;      // bytes per packed operand
+};
+struct PGemmArgs {
+  int M, N, nkt, epi, ep1, ep2, ep3;
+  long long ldc;
+  double ar, ai;
+  const long long* coff;
+  const int* sbeg;
+  const int* ia;               // packed A operand index of each segment
+  const int* ib;               // packed B operand index of each segment
+  int tiles_m, tiles_n, nbatch;
+  const unsigned char* A;
+  const unsigned char* B;
+  double2* C;
+  long long abytes, bbytes, sA, sB, sC;
+};
+long long packed_bytes(int mode, int R, int K);
+cudaError_t launch_pack(const PackArgs& p, int prec, int nrhs, cudaStream_t st);
+cudaError_t launch_gemm_tcp(const PGemmArgs& g, int prec, int nrhs, int* errflag, cudaStream_t st);
+size_t tcp_smem_bytes();
+
 // DF factor split: L[k1][k2][Q][n][n] (paper units) -> oo/ov/vo/vv blocks * scale.
 cudaError_t launch_split_df(const double2* L, int nk, int Q, int o, int v, double scale, double2* Loo,
                             double2* Lov, double2* Lvo, double2* Lvv, cudaStream_t st);

@@ -1,0 +1,378 @@
+// Packed-operand tensor-core GEMM (tcgen05, TF32 or BF16x3) for the large GEMMs of
+// the mixed-precision path, and the kernel that packs complex FP64 operands.
+//
+// Packed operand: a complex R x K matrix (any offset / leading dimension / transpose)
+// stored as MMA-ready tiles, tile (rt, kt) at byte offset (rt * nkt + kt) * tile bytes,
+// each tile in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core
+// matrix, K-adjacent cores 128 bytes apart).  Complex numbers by real embedding:
+//   mode A (left operand):  real row r, real K 2k + {0,1} = (Re, Im) of a[r][k];
+//   mode B (right operand, stored K-major): real rows 2n, 2n+1 and real K 2k, 2k+1 hold
+//   [[Re, -Im], [Im, Re]] of b[k][n], so that C_real = A_real . B_real^T carries
+//   (Re c, Im c) interleaved along N.
+// TF32 tiles hold fp32 values (4 bytes, 32 real K per 128-byte row); BF16x3 tiles hold
+// a bf16 "hi" plane followed by a bf16 "lo" plane (x - hi), 32 real K per 64-byte row.
+//
+// GEMM: one CTA per 128 x 128 complex output tile (128 x 256 real accumulator in 256
+// TMEM columns); warp 0 streams A and B tiles with cp.async.bulk into a 4-stage ring
+// (mbarrier transaction counts), warp 1 issues tcgen05.mma (TF32: 4 per stage; BF16x3:
+// hi*hi + hi*lo + lo*hi per K=16 step) and releases stages with tcgen05.commit, warps
+// 2-5 drain the accumulator (tcgen05.ld) and add alpha * C into the FP64 destination.
+// All waits are bounded; on timeout the CTA sets the error flag, drains its own
+// outstanding copies (bounded), releases tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include "kernels.cuh"
+
+namespace lrcc {
+
+namespace {
+
+constexpr int P_BM = 128;   // real rows of an A tile (= complex rows)
+constexpr int P_BNR = 256;  // real rows of a B tile (= 128 complex columns)
+constexpr int P_BKR = 32;   // real K per stage
+constexpr int P_STAGES = 4;
+constexpr int P_ATILE = P_BM * 128;   // bytes (TF32: 128 x 32 x 4; BF16x3: 2 planes x 128 x 32 x 2)
+constexpr int P_BTILE = P_BNR * 128;
+constexpr int P_THREADS = 192;
+constexpr long long P_SPIN = 1LL << 26;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < P_SPIN; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// byte offset of real element (row, kr) in a tile (PREC 1: fp32; PREC 2: one bf16 plane)
+template <int PREC>
+__device__ __forceinline__ int tile_off(int row, int kr) {
+  constexpr int EB = PREC == 1 ? 4 : 2, T = 16 / EB;
+  return ((row >> 3) * (P_BKR / T) + kr / T) * 128 + (row & 7) * 16 + (kr % T) * EB;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------------
+// packing
+// --------------------------------------------------------------------------------
+// Every work item writes one complex element (or its zero padding) of one packed
+// operand: mode A -> 2 reals, mode B -> a 2 x 2 real block.
+template <int PREC>
+__global__ void pack_kernel(PackArgs p) {
+  const int rows_real = p.mode == 0 ? p.R : 2 * p.R;
+  const int tr = p.mode == 0 ? P_BM : P_BNR;
+  const int nrt = (rows_real + tr - 1) / tr;
+  const int nkt = (2 * p.K + P_BKR - 1) / P_BKR;
+  const int Rp = p.mode == 0 ? nrt * tr : nrt * tr / 2;  // padded complex rows
+  const int Kp = nkt * P_BKR / 2;                         // padded complex K
+  const long long per = (long long)Rp * Kp;
+  const long long total = per * p.count;
+  const long long rhs = blockIdx.y;
+  const double2* src = p.src + rhs * p.sS;
+  unsigned char* dst = p.dst + rhs * p.sD;
+  const long long tile_bytes = (long long)tr * 128;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int li = (int)(e / per);
+    const long long w = e - (long long)li * per;
+    int r, k;
+    if (p.trans) {  // consecutive threads walk rows (contiguous in the source)
+      r = (int)(w % Rp);
+      k = (int)(w / Rp);
+    } else {
+      k = (int)(w % Kp);
+      r = (int)(w / Kp);
+    }
+    double2 v = make_double2(0.0, 0.0);
+    if (r < p.R && k < p.K) {
+      const long long off = p.offs[li] + (p.trans ? (long long)k * p.ld + r : (long long)r * p.ld + k);
+      v = src[off];
+    }
+    unsigned char* base = dst + (long long)li * p.packed_bytes;
+    const int kr = 2 * k;
+    const int kt = kr / P_BKR, kk = kr % P_BKR;
+    if (p.mode == 0) {
+      const int rt = r / tr, rr = r % tr;
+      unsigned char* tile = base + ((long long)rt * nkt + kt) * tile_bytes;
+      const float xr = (float)v.x, xi = (float)v.y;
+      if (PREC == 1) {
+        *(float2*)(tile + tile_off<1>(rr, kk)) = make_float2(xr, xi);
+      } else {
+        const __nv_bfloat16 hr = __float2bfloat16_rn(xr), hi = __float2bfloat16_rn(xi);
+        const __nv_bfloat16 lr = __float2bfloat16_rn(xr - __bfloat162float(hr));
+        const __nv_bfloat16 li2 = __float2bfloat16_rn(xi - __bfloat162float(hi));
+        const int o = tile_off<2>(rr, kk);
+        *(__nv_bfloat162*)(tile + o) = __halves2bfloat162(hr, hi);
+        *(__nv_bfloat162*)(tile + tr * 64 + o) = __halves2bfloat162(lr, li2);
+      }
+    } else {
+      const int r0 = 2 * r;
+      const int rt = r0 / tr, rr = r0 % tr;  // rows 2r and 2r+1 share a tile (tr even)
+      unsigned char* tile = base + ((long long)rt * nkt + kt) * tile_bytes;
+      const float br = (float)v.x, bi = (float)v.y;
+      if (PREC == 1) {
+        *(float2*)(tile + tile_off<1>(rr, kk)) = make_float2(br, -bi);
+        *(float2*)(tile + tile_off<1>(rr + 1, kk)) = make_float2(bi, br);
+      } else {
+        const __nv_bfloat16 hr = __float2bfloat16_rn(br), hi = __float2bfloat16_rn(bi);
+        const __nv_bfloat16 lr = __float2bfloat16_rn(br - __bfloat162float(hr));
+        const __nv_bfloat16 li2 = __float2bfloat16_rn(bi - __bfloat162float(hi));
+        const int o0 = tile_off<2>(rr, kk), o1 = tile_off<2>(rr + 1, kk);
+        *(__nv_bfloat162*)(tile + o0) = __halves2bfloat162(hr, __hneg(hi));
+        *(__nv_bfloat162*)(tile + o1) = __halves2bfloat162(hi, hr);
+        *(__nv_bfloat162*)(tile + tr * 64 + o0) = __halves2bfloat162(lr, __hneg(li2));
+        *(__nv_bfloat162*)(tile + tr * 64 + o1) = __halves2bfloat162(li2, lr);
+      }
+    }
+  }
+}
+
+long long packed_bytes(int mode, int R, int K) {
+  const int rows_real = mode == 0 ? R : 2 * R;
+  const int tr = mode == 0 ? P_BM : P_BNR;
+  const long long nrt = (rows_real + tr - 1) / tr;
+  const long long nkt = (2LL * K + P_BKR - 1) / P_BKR;
+  return nrt * nkt * tr * 128;
+}
+
+cudaError_t launch_pack(const PackArgs& p, int prec, int nrhs, cudaStream_t st) {
+  const int rows_real = p.mode == 0 ? p.R : 2 * p.R;
+  const int tr = p.mode == 0 ? P_BM : P_BNR;
+  const long long nrt = (rows_real + tr - 1) / tr;
+  const long long nkt = (2LL * p.K + P_BKR - 1) / P_BKR;
+  const long long per = (p.mode == 0 ? nrt * tr : nrt * tr / 2) * (nkt * P_BKR / 2);
+  const long long total = per * p.count;
+  if (total <= 0) return cudaSuccess;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152LL * 32) blocks = 152LL * 32;
+  dim3 grid((unsigned)blocks, (unsigned)nrhs);
+  if (prec == 1) pack_kernel<1><<<grid, 256, 0, st>>>(p);
+  else pack_kernel<2><<<grid, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------------
+// packed GEMM
+// --------------------------------------------------------------------------------
+template <int PREC>
+__global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_kernel(PGemmArgs g, int* errflag) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[P_STAGES], empty[P_STAGES], accf;
+  __shared__ uint32_t tmem_sh;
+  __shared__ int fail_sh;
+
+  const int tpb = g.tiles_m * g.tiles_n;
+  const int batch = blockIdx.x / tpb;
+  const int t = blockIdx.x - batch * tpb;
+  const int mt = t / g.tiles_n, nt = t % g.tiles_n;
+  const long long rhs = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s0 = g.sbeg[batch], s1 = g.sbeg[batch + 1];
+  const int nkt = g.nkt;
+  const int total = (s1 - s0) * nkt;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P_STAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&accf)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    fail_sh = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_sh)),
+                 "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_sh;
+
+  if (warp == 0 && lane == 0 && total > 0) {
+    // producer
+    const unsigned char* Ab = g.A + rhs * g.sA;
+    const unsigned char* Bb = g.B + rhs * g.sB;
+    int issued = 0;
+    bool ok = true;
+    for (int i = 0; i < total && ok; ++i) {
+      const int s = i % P_STAGES;
+      if (i >= P_STAGES && !wait_parity(su32(&empty[s]), ((i / P_STAGES) - 1) & 1)) {
+        ok = false;
+        break;
+      }
+      const int seg = s0 + i / nkt, kt = i % nkt;
+      const unsigned char* at = Ab + (long long)g.ia[seg] * g.abytes + ((long long)mt * nkt + kt) * P_ATILE;
+      const unsigned char* bt = Bb + (long long)g.ib[seg] * g.bbytes + ((long long)nt * nkt + kt) * P_BTILE;
+      unsigned char* sa = smem + s * (P_ATILE + P_BTILE);
+      unsigned char* sb = sa + P_ATILE;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&full[s])),
+                   "r"(P_ATILE + P_BTILE)
+                   : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(sa)),
+          "l"(at), "r"(P_ATILE), "r"(su32(&full[s]))
+          : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(sb)),
+          "l"(bt), "r"(P_BTILE), "r"(su32(&full[s]))
+          : "memory");
+      ++issued;
+    }
+    if (!ok) {
+      atomicExch(&fail_sh, 1);
+      // drain the copies in flight before the CTA releases its shared memory
+      for (int i = (issued > P_STAGES ? issued - P_STAGES : 0); i < issued; ++i)
+        wait_parity(su32(&full[i % P_STAGES]), (i / P_STAGES) & 1);
+    }
+  } else if (warp == 1 && lane == 0 && total > 0) {
+    // MMA issuer
+    constexpr uint32_t LBO = 128;
+    constexpr uint32_t SBO_A = (P_BKR / (PREC == 1 ? 4 : 8)) * 128;
+    const uint32_t fmt = PREC == 1 ? 2u : 1u;
+    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(P_BNR >> 3) << 17) |
+                           ((uint32_t)(P_BM >> 4) << 24);
+    bool ok = true;
+    for (int i = 0; i < total; ++i) {
+      const int s = i % P_STAGES;
+      if (!wait_parity(su32(&full[s]), (i / P_STAGES) & 1)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a0 = su32(smem + s * (P_ATILE + P_BTILE)), b0 = a0 + P_ATILE;
+      if (PREC == 1) {
+#pragma unroll
+        for (int ks = 0; ks < P_BKR / 8; ++ks) {
+          const uint32_t ko = ks * 2 * LBO;
+          const uint64_t ad = sdesc(a0 + ko, LBO, SBO_A), bd = sdesc(b0 + ko, LBO, SBO_A);
+          const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+      } else {
+#pragma unroll
+        for (int ks = 0; ks < P_BKR / 16; ++ks) {
+          const uint32_t ko = ks * 2 * LBO;
+          const uint64_t ahi = sdesc(a0 + ko, LBO, SBO_A), bhi = sdesc(b0 + ko, LBO, SBO_A);
+          const uint64_t alo = sdesc(a0 + P_BM * 64 + ko, LBO, SBO_A), blo = sdesc(b0 + P_BNR * 64 + ko, LBO, SBO_A);
+          const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p, q;\n setp.ne.b32 p, %6, 0;\n setp.ne.b32 q, 1, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %4, %3, q;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %2, %3, q;\n}\n" ::"r"(tmem),
+              "l"(ahi), "l"(bhi), "r"(idesc), "l"(blo), "l"(alo), "r"(acc));
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       su32(&empty[s]))
+                   : "memory");
+    }
+    if (ok) {
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&accf))
+                   : "memory");
+    } else {
+      atomicExch(&fail_sh, 1);
+    }
+  } else if (warp >= 2 && total > 0) {
+    // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31
+    const int q = warp & 3;
+    const bool ok = wait_parity(su32(&accf), 0);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!ok) {
+      atomicExch(&fail_sh, 1);
+    } else {
+      const int m = mt * P_BM + q * 32 + lane;
+      double2* Cp = g.C + rhs * g.sC + g.coff[batch];
+#pragma unroll 1
+      for (int c0 = 0; c0 < P_BNR; c0 += 16) {
+        uint32_t r[16];
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+            "[%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (m < g.M) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int n = nt * (P_BNR / 2) + c0 / 2 + j;
+            if (n >= g.N) break;
+            const double ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
+            const double vr = g.ar * ar - g.ai * ai, vi = g.ar * ai + g.ai * ar;
+            if (g.epi == 0) {
+              double2* cp = Cp + (long long)m * g.ldc + n;
+              double2 cv = *cp;
+              cv.x += vr;
+              cv.y += vi;
+              *cp = cv;
+            } else {
+              const int a = m / g.ep2, c = m - a * g.ep2;
+              const int b = n / g.ep3, d = n - b * g.ep3;
+              Cp[(((long long)a * g.ep1 + b) * g.ep2 + c) * g.ep3 + d] = make_double2(vr, vi);
+            }
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (threadIdx.x == 0 && fail_sh) atomicExch(errflag, 1);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+}
+
+size_t tcp_smem_bytes() { return (size_t)P_STAGES * (P_ATILE + P_BTILE) + 1024; }
+
+cudaError_t launch_gemm_tcp(const PGemmArgs& g0, int prec, int nrhs, int* errflag, cudaStream_t st) {
+  PGemmArgs g = g0;
+  g.tiles_m = (g.M + P_BM - 1) / P_BM;
+  g.tiles_n = (g.N + P_BNR / 2 - 1) / (P_BNR / 2);
+  const long long nblk = (long long)g.tiles_m * g.tiles_n * g.nbatch;
+  if (nblk <= 0) return cudaSuccess;
+  if (nblk > 2147483647LL || nrhs > 65535) return cudaErrorInvalidConfiguration;
+  const size_t sm = tcp_smem_bytes();
+  dim3 grid((unsigned)nblk, (unsigned)nrhs);
+  if (prec == 1) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(tcp_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+    }
+    tcp_gemm_kernel<1><<<grid, P_THREADS, sm, st>>>(g, errflag);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(tcp_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+    }
+    tcp_gemm_kernel<2><<<grid, P_THREADS, sm, st>>>(g, errflag);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lrcc

@@ -1,5 +1,6 @@
 // liblrcc runtime: problem handle, device arenas, plan executor and the C-ABI
 // entry points of include/lrcc.h (except the host-only plan introspection).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -45,6 +46,18 @@ void Runtime::prof_reset() {
 
 void Runtime::release() {
   prof_reset();
+  for (PackPlan& pp : packs) {
+    for (void* p : {(void*)pp.d_aoffs, (void*)pp.d_boffs, (void*)pp.d_ia, (void*)pp.d_ib})
+      if (p) cudaFree(p);
+    for (int i = 0; i < 3; ++i) {
+      if (pp.fixA[i]) cudaFree(pp.fixA[i]);
+      if (pp.fixB[i]) cudaFree(pp.fixB[i]);
+    }
+  }
+  packs.clear();
+  if (packscr) cudaFree(packscr);
+  packscr = nullptr;
+  packscr_bytes = 0;
   for (cudaEvent_t e : prof_pool) cudaEventDestroy(e);
   prof_pool.clear();
   for (void* p : {(void*)fix, (void*)in, (void*)out, (void*)scr, (void*)ws, (void*)desc, (void*)dip, (void*)l1,
@@ -120,6 +133,123 @@ lrcc_status Runtime::init(const lrcc_dims& d, int64_t ws_budget) {
   return LRCC_OK;
 }
 
+bool Runtime::use_packed(const Gemm& g) const { return g.M >= 96 && g.N >= 96 && g.K >= 16; }
+
+static bool is_vec_arena(int ar) { return ar == AR_IN || ar == AR_OUT || ar == AR_SCR; }
+
+lrcc_status Runtime::run_packed(int gi, const Gemm& g, double2* const ar[AR_COUNT], int nr, bool fixed_only,
+                                const long long* stride, cudaStream_t st, int prec) {
+  if (packs.size() < plan.gemms.size()) packs.resize(plan.gemms.size());
+  PackPlan& pp = packs[gi];
+  if (!pp.init) {
+    std::vector<int> ia(g.aoff.size()), ib(g.boff.size());
+    std::vector<long long> la, lb;
+    for (size_t s = 0; s < g.aoff.size(); ++s) {
+      auto it = std::find(la.begin(), la.end(), g.aoff[s]);
+      ia[s] = (int)(it - la.begin());
+      if (it == la.end()) la.push_back(g.aoff[s]);
+      auto jt = std::find(lb.begin(), lb.end(), g.boff[s]);
+      ib[s] = (int)(jt - lb.begin());
+      if (jt == lb.end()) lb.push_back(g.boff[s]);
+    }
+    pp.alist = la;
+    pp.blist = lb;
+    pp.abytes = packed_bytes(0, g.M, g.K);
+    pp.bbytes = packed_bytes(1, g.N, g.K);
+    if (!ck(cudaMalloc(&pp.d_aoffs, la.size() * 8), "cudaMalloc(pack)") ||
+        !ck(cudaMalloc(&pp.d_boffs, lb.size() * 8), "cudaMalloc(pack)") ||
+        !ck(cudaMalloc(&pp.d_ia, ia.size() * 4), "cudaMalloc(pack)") ||
+        !ck(cudaMalloc(&pp.d_ib, ib.size() * 4), "cudaMalloc(pack)"))
+      return LRCC_ENOMEM;
+    if (!ck(cudaMemcpy(pp.d_aoffs, la.data(), la.size() * 8, cudaMemcpyHostToDevice), "pack upload") ||
+        !ck(cudaMemcpy(pp.d_boffs, lb.data(), lb.size() * 8, cudaMemcpyHostToDevice), "pack upload") ||
+        !ck(cudaMemcpy(pp.d_ia, ia.data(), ia.size() * 4, cudaMemcpyHostToDevice), "pack upload") ||
+        !ck(cudaMemcpy(pp.d_ib, ib.data(), ib.size() * 4, cudaMemcpyHostToDevice), "pack upload"))
+      return LRCC_ECUDA;
+    pp.init = true;
+  }
+  // operands that live in the fixed arena are packed once per precision; the others
+  // (vector arenas and the W workspace, rebuilt every product) are packed each time
+  const bool varA = g.arA != AR_FIX, varB = g.arB != AR_FIX;
+  const int nrA = (!fixed_only && is_vec_arena(g.arA)) ? nr : 1;
+  const int nrB = (!fixed_only && is_vec_arena(g.arB)) ? nr : 1;
+  const size_t needA = varA ? (size_t)pp.abytes * pp.alist.size() * nrA : 0;
+  const size_t needB = varB ? (size_t)pp.bbytes * pp.blist.size() * nrB : 0;
+  if (needA + needB + 1024 > packscr_bytes) {
+    if (!ck(cudaStreamSynchronize(st), "sync")) return LRCC_ECUDA;  // earlier ops may still read it
+    if (packscr) cudaFree(packscr);
+    packscr = nullptr;
+    packscr_bytes = 0;
+    if (!ck(cudaMalloc(&packscr, needA + needB + 1024), "cudaMalloc(pack scratch)")) return LRCC_ENOMEM;
+    packscr_bytes = needA + needB + 1024;
+  }
+  auto pack = [&](int mode, int arena, const std::vector<long long>& list, const long long* doffs, int R,
+                  long long ld, int trans, long long bytes, unsigned char* dst, int nrr) -> lrcc_status {
+    PackArgs pa;
+    pa.src = ar[arena];
+    pa.dst = dst;
+    pa.sS = nrr > 1 ? stride[arena] : 0;
+    pa.sD = (long long)bytes * list.size();
+    pa.offs = doffs;
+    pa.count = (int)list.size();
+    pa.R = R;
+    pa.K = g.K;
+    pa.ld = ld;
+    pa.trans = trans;
+    pa.mode = mode;
+    pa.packed_bytes = bytes;
+    if (!ck(launch_pack(pa, prec, nrr, st), "pack")) return LRCC_ECUDA;
+    ++launches;
+    return LRCC_OK;
+  };
+  const unsigned char* Ap;
+  const unsigned char* Bp;
+  lrcc_status s;
+  if (varA) {
+    if ((s = pack(0, g.arA, pp.alist, pp.d_aoffs, g.M, g.lda, g.ta, pp.abytes, packscr, nrA)) != LRCC_OK) return s;
+    Ap = packscr;
+  } else {
+    if (!pp.fixA[prec]) {
+      if (!ck(cudaMalloc(&pp.fixA[prec], (size_t)pp.abytes * pp.alist.size()), "cudaMalloc(packed fixed)"))
+        return LRCC_ENOMEM;
+      if ((s = pack(0, g.arA, pp.alist, pp.d_aoffs, g.M, g.lda, g.ta, pp.abytes, pp.fixA[prec], 1)) != LRCC_OK)
+        return s;
+    }
+    Ap = pp.fixA[prec];
+  }
+  if (varB) {
+    unsigned char* dst = packscr + needA;
+    if ((s = pack(1, g.arB, pp.blist, pp.d_boffs, g.N, g.ldb, g.tb ? 0 : 1, pp.bbytes, dst, nrB)) != LRCC_OK)
+      return s;
+    Bp = dst;
+  } else {
+    if (!pp.fixB[prec]) {
+      if (!ck(cudaMalloc(&pp.fixB[prec], (size_t)pp.bbytes * pp.blist.size()), "cudaMalloc(packed fixed)"))
+        return LRCC_ENOMEM;
+      if ((s = pack(1, g.arB, pp.blist, pp.d_boffs, g.N, g.ldb, g.tb ? 0 : 1, pp.bbytes, pp.fixB[prec], 1)) !=
+          LRCC_OK)
+        return s;
+    }
+    Bp = pp.fixB[prec];
+  }
+  const GemmDesc& d = gdesc[gi];
+  PGemmArgs a;
+  a.M = g.M; a.N = g.N; a.nkt = (int)((2LL * g.K + 31) / 32);
+  a.epi = g.epi; a.ep1 = g.ep[1]; a.ep2 = g.ep[2]; a.ep3 = g.ep[3];
+  a.ldc = g.ldc; a.ar = g.ar; a.ai = g.ai;
+  a.coff = d.coff; a.sbeg = d.sbeg; a.ia = pp.d_ia; a.ib = pp.d_ib;
+  a.nbatch = g.nbatch();
+  a.tiles_m = a.tiles_n = 1;
+  a.A = Ap; a.B = Bp; a.C = ar[g.arC];
+  a.abytes = pp.abytes; a.bbytes = pp.bbytes;
+  a.sA = nrA > 1 ? (long long)pp.abytes * pp.alist.size() : 0;
+  a.sB = nrB > 1 ? (long long)pp.bbytes * pp.blist.size() : 0;
+  a.sC = (!fixed_only && is_vec_arena(g.arC)) ? stride[g.arC] : 0;
+  if (!ck(launch_gemm_tcp(a, prec, fixed_only ? 1 : nr, dflag, st), "packed gemm")) return LRCC_ECUDA;
+  ++launches;
+  return LRCC_OK;
+}
+
 lrcc_status Runtime::ensure_rhs(int nrhs) {
   if (nrhs <= cap_rhs) return LRCC_OK;
   for (double2** p : {&in, &out, &scr})
@@ -176,8 +306,13 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
       a.sA = op.fixed_only ? 0 : stride[g.arA];
       a.sB = op.fixed_only ? 0 : stride[g.arB];
       a.sC = op.fixed_only ? 0 : stride[g.arC];
-      e = prec > 0 ? launch_gemm_tc(a, prec, nr, dflag, st) : launch_gemm_f64(a, d.tile, nr, st);
-      ++launches;
+      if (prec > 0 && use_packed(g)) {
+        lrcc_status ps = run_packed(op.idx, g, ar, nr, op.fixed_only != 0, stride, st, prec);
+        if (ps != LRCC_OK) return ps;
+      } else {
+        e = prec > 0 ? launch_gemm_tc(a, prec, nr, dflag, st) : launch_gemm_f64(a, d.tile, nr, st);
+        ++launches;
+      }
     } else if (op.kind == OP_PERM) {
       const Perm& p = plan.perms[op.idx];
       PermArgs a;

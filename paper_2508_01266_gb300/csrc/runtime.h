@@ -18,6 +18,17 @@ struct GemmDesc {
   int tile = 0;
 };
 
+// Packed-operand execution of one GEMM op on the tensor cores (mixed precision).
+struct PackPlan {
+  bool init = false;
+  std::vector<long long> alist, blist;    // distinct operand offsets
+  long long *d_aoffs = nullptr, *d_boffs = nullptr;
+  int *d_ia = nullptr, *d_ib = nullptr;
+  long long abytes = 0, bbytes = 0;       // bytes per packed operand
+  unsigned char* fixA[3] = {nullptr, nullptr, nullptr};  // cached packs of fixed operands per precision
+  unsigned char* fixB[3] = {nullptr, nullptr, nullptr};
+};
+
 struct Runtime {
   lrcc_dims dims{};
   Plan plan;
@@ -42,6 +53,12 @@ struct Runtime {
   lrcc_status init(const lrcc_dims& d, int64_t ws_budget);
   lrcc_status ensure_rhs(int nrhs);
   int* dflag = nullptr;  // device error flag of the tensor-core kernels (bounded waits)
+  std::vector<PackPlan> packs;            // per GEMM op (lazily built)
+  unsigned char* packscr = nullptr;       // packed vector-dependent operands
+  size_t packscr_bytes = 0;
+  bool use_packed(const Gemm& g) const;
+  lrcc_status run_packed(int gi, const Gemm& g, double2* const ar[AR_COUNT], int nr, bool fixed_only,
+                         const long long* stride, cudaStream_t st, int prec);
   // prec: 0 FP64 kernels; 1 TF32 and 2 BF16x3 tensor-core GEMMs (FP32 accumulation)
   lrcc_status run(const Program& pr, double2* const ar[AR_COUNT], int nrhs, cudaStream_t st, int prec = 0);
   lrcc_status apply(int transpose, int nrhs, cudaStream_t st, int prec = 0);

@@ -498,9 +498,12 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
                       st),
          "t2 + s u2");
       rt.launches += 2;
-      if ((s = rebuild_ground(opt.precision)) != LRCC_OK) return s;
+      // the F stencil divides product differences by the step: the mixed modes take these
+      // products in BF16x3 (about 1e-5 relative), which keeps alpha within 1e-6 of FP64
+      const int fprec = opt.precision ? 2 : 0;
+      if ((s = rebuild_ground(fprec)) != LRCC_OK) return s;
       CK(cudaMemcpy(rt.out, LAM, vec * sizeof(double2), cudaMemcpyDeviceToDevice), "lam -> out");
-      if ((s = rt.apply(1, 1, st, opt.precision)) != LRCC_OK) return s;
+      if ((s = rt.apply(1, 1, st, fprec)) != LRCC_OK) return s;
       CK(launch_axpby(make_double2(w4[k] / (12.0 * hstep[i]), 0.0), rt.in, make_double2(1.0, 0.0),
                       FU + (size_t)i * vec, vec, st),
          "F u");

@@ -66,11 +66,32 @@ def test_alpha_skips_vanishing_component(lr):
     assert abs(got[0, 1, 1] - ref[0, 1, 1]) < 1e-8 * abs(ref[0, 1, 1])
 
 
-def test_alpha_c1_vs_oracle(lr):
-    """C1 workload: Nk=3, nocc=4, nvir=16, naux=48, alpha_zz at w = 0 and 0.1 Ha."""
+@pytest.fixture(scope="module")
+def c1_ref():
+    """C1 workload (Nk=3, nocc=4, nvir=16, naux=48): oracle T, Lambda and alpha_zz at w = 0, 0.1 Ha."""
     c = CONFIGS["c1"]
     p = make_problem(c["nk"], c["nocc"], c["nvir"], c["naux"], seed=1266)
-    got, ref, info = _run(lr, p, [2], [0.0, 0.1])
+    R = rcc.RCC(p)
+    t1, t2, _ = rcc.solve_ccsd(R, tol=1e-10)
+    l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=1e-10)
+    ref = rcc.polarizability(R, t1, t2, l1, l2, rcc.dipole_ops(p, [2]), [0.0, 0.1], tol=1e-11)
+    return p, t1, t2, l1, l2, ref
+
+
+def _c1_gpu(lr, c1_ref, options):
+    p, t1, t2, l1, l2, ref = c1_ref
+    nk, o, v, Q = p.nk, p.nocc, p.nvir, p.naux
+    pl1, pl2 = paper_lambda(nk, l1, l2)
+    prob = lr.Problem(nk, o, v, Q)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    prob.set_ground_state(t1, t2 * nk, pl1, pl2)
+    got, info = prob.polarizability([2], [0.0, 0.1], options)
+    prob.close()
+    return got, ref, info
+
+
+def test_alpha_c1_vs_oracle(lr, c1_ref):
+    got, ref, info = _c1_gpu(lr, c1_ref, lr.default_options(conv_tol=1e-11, max_iter=300))
     assert info[1] == 0
     rel = np.abs(got - ref).max() / np.abs(ref).max()
     print("C1 alpha_zz gpu", got.ravel(), "oracle", ref.ravel(), "rel", rel)
@@ -78,21 +99,9 @@ def test_alpha_c1_vs_oracle(lr):
 
 
 @pytest.mark.parametrize("prec", [2, 1])
-def test_alpha_mixed_precision_c1(lr, prec):
+def test_alpha_mixed_precision_c1(lr, c1_ref, prec):
     """Tensor-core inner solves + FP64 iterative refinement: |alpha - alpha_oracle| <= 1e-5 a.u."""
-    c = CONFIGS["c1"]
-    p = make_problem(c["nk"], c["nocc"], c["nvir"], c["naux"], seed=1266)
-    nk, o, v, Q = p.nk, p.nocc, p.nvir, p.naux
-    R = rcc.RCC(p)
-    t1, t2, _ = rcc.solve_ccsd(R, tol=1e-10)
-    l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=1e-10)
-    ref = rcc.polarizability(R, t1, t2, l1, l2, rcc.dipole_ops(p, [2]), [0.0, 0.1], tol=1e-11)
-    pl1, pl2 = paper_lambda(nk, l1, l2)
-    prob = lr.Problem(nk, o, v, Q)
-    prob.set_integrals(p.L, p.eps, p.dip)
-    prob.set_ground_state(t1, t2 * nk, pl1, pl2)
-    got, info = prob.polarizability([2], [0.0, 0.1], lr.default_options(precision=prec, refine_tol=1e-8))
-    prob.close()
+    got, ref, info = _c1_gpu(lr, c1_ref, lr.default_options(precision=prec, refine_tol=1e-8))
     err = np.abs(got - ref).max()
     print(f"C1 alpha_zz prec {prec}: {got.ravel()} oracle {ref.ravel()} |err| {err:.2e} iterations {info[0]}")
     assert info[1] == 0

@@ -30,7 +30,7 @@ def _setup(lr, nk, o, v, Q, seed=11):
     return prob
 
 
-@pytest.mark.parametrize("nk,o,v,Q", [(2, 1, 3, 5), (3, 2, 4, 6), (3, 4, 16, 48)])
+@pytest.mark.parametrize("nk,o,v,Q", [(2, 1, 3, 5), (3, 2, 4, 6), (3, 4, 16, 48), (2, 8, 16, 40), (5, 8, 40, 160)])
 @pytest.mark.parametrize("prec,bound", [(1, 3e-3), (2, 3e-5)])
 def test_mixed_products_vs_fp64(lr, nk, o, v, Q, prec, bound):
     prob = _setup(lr, nk, o, v, Q)
