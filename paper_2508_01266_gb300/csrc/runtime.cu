@@ -209,11 +209,13 @@ lrcc_status Runtime::run_packed(int gi, const Gemm& g, double2* const ar[AR_COUN
     if ((s = pack(0, g.arA, pp.alist, pp.d_aoffs, g.M, g.lda, g.ta, pp.abytes, packscr, nrA)) != LRCC_OK) return s;
     Ap = packscr;
   } else {
-    if (!pp.fixA[prec]) {
-      if (!ck(cudaMalloc(&pp.fixA[prec], (size_t)pp.abytes * pp.alist.size()), "cudaMalloc(packed fixed)"))
-        return LRCC_ENOMEM;
+    if (!pp.fixA[prec] &&
+        !ck(cudaMalloc(&pp.fixA[prec], (size_t)pp.abytes * pp.alist.size()), "cudaMalloc(packed fixed)"))
+      return LRCC_ENOMEM;
+    if (pp.verA[prec] != fix_version) {
       if ((s = pack(0, g.arA, pp.alist, pp.d_aoffs, g.M, g.lda, g.ta, pp.abytes, pp.fixA[prec], 1)) != LRCC_OK)
         return s;
+      pp.verA[prec] = fix_version;
     }
     Ap = pp.fixA[prec];
   }
@@ -223,12 +225,14 @@ lrcc_status Runtime::run_packed(int gi, const Gemm& g, double2* const ar[AR_COUN
       return s;
     Bp = dst;
   } else {
-    if (!pp.fixB[prec]) {
-      if (!ck(cudaMalloc(&pp.fixB[prec], (size_t)pp.bbytes * pp.blist.size()), "cudaMalloc(packed fixed)"))
-        return LRCC_ENOMEM;
+    if (!pp.fixB[prec] &&
+        !ck(cudaMalloc(&pp.fixB[prec], (size_t)pp.bbytes * pp.blist.size()), "cudaMalloc(packed fixed)"))
+      return LRCC_ENOMEM;
+    if (pp.verB[prec] != fix_version) {
       if ((s = pack(1, g.arB, pp.blist, pp.d_boffs, g.N, g.ldb, g.tb ? 0 : 1, pp.bbytes, pp.fixB[prec], 1)) !=
           LRCC_OK)
         return s;
+      pp.verB[prec] = fix_version;
     }
     Bp = pp.fixB[prec];
   }
@@ -268,6 +272,7 @@ lrcc_status Runtime::ensure_rhs(int nrhs) {
 }
 
 lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrhs, cudaStream_t st, int prec) {
+  if (&pr == &plan.ground) ++fix_version;  // cached tensor-core packs of fixed operands are stale
   long long stride[AR_COUNT] = {0, plan.arena_size[AR_IN], plan.arena_size[AR_OUT], plan.arena_size[AR_SCR], 0};
   for (const Op& op : pr.ops) {
     cudaError_t e = cudaSuccess;

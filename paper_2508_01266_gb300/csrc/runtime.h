@@ -27,6 +27,7 @@ struct PackPlan {
   long long abytes = 0, bbytes = 0;       // bytes per packed operand
   unsigned char* fixA[3] = {nullptr, nullptr, nullptr};  // cached packs of fixed operands per precision
   unsigned char* fixB[3] = {nullptr, nullptr, nullptr};
+  long long verA[3] = {-1, -1, -1}, verB[3] = {-1, -1, -1};  // fixed-arena version the packs were made from
 };
 
 struct Runtime {
@@ -54,6 +55,7 @@ struct Runtime {
   lrcc_status ensure_rhs(int nrhs);
   int* dflag = nullptr;  // device error flag of the tensor-core kernels (bounded waits)
   std::vector<PackPlan> packs;            // per GEMM op (lazily built)
+  long long fix_version = 0;              // bumped whenever the ground-state program rewrites FIX
   unsigned char* packscr = nullptr;       // packed vector-dependent operands
   size_t packscr_bytes = 0;
   bool use_packed(const Gemm& g) const;

