@@ -151,6 +151,10 @@ int64_t lrcc_kernel_launches(const lrcc_problem* p);
  * device.  Tags are the op names of the plan (e.g. "ladder", "W build"). */
 lrcc_status lrcc_profile(lrcc_problem* p, int32_t enable);
 lrcc_status lrcc_profile_query(lrcc_problem* p, const char* tag, double* ms, int64_t* count, double* flops);
+/* All recorded ops aggregated by tag, slowest first: one line per tag,
+ * "tag<TAB>ms<TAB>count<TAB>flops<LF>", NUL-terminated in buf[len].  Returns
+ * LRCC_EINVAL (with the report truncated) when len is too small. */
+lrcc_status lrcc_profile_report(lrcc_problem* p, char* buf, int64_t len);
 
 /* ---------------------------------------------------------------------------
  * Plan introspection (host only; never touches the GPU)
@@ -172,8 +176,8 @@ int32_t lrcc_plan_num_ops(const lrcc_plan* h, int32_t which);
 /* Bounds check of every op of every program against the arena sizes; writes a
  * NUL-terminated message (empty when every access is in bounds) into msg[len]. */
 lrcc_status lrcc_plan_validate(const lrcc_plan* h, char* msg, int32_t len);
-/* kind_idx_fixed int32[3]: kind (0 GEMM, 1 permute, 2 2-D transpose), table index,
- * fixed-only flag. */
+/* kind_idx_fixed int32[3]: kind (0 GEMM, 1 permute, 2 2-D transpose, 3 zero a
+ * scratch range), table index, fixed-only flag. */
 lrcc_status lrcc_plan_op(const lrcc_plan* h, int32_t which, int32_t i, int32_t* kind_idx_fixed);
 /* ints int32[15]: M N K ta tb arA arB arC epi ep0..ep3 nbatch nseg; lds int64[3];
  * alpha double[2]; coff int64[nbatch], sbeg int32[nbatch+1], aoff/boff int64[nseg]. */
@@ -183,6 +187,10 @@ lrcc_status lrcc_plan_gemm(const lrcc_plan* h, int32_t idx, int32_t* ints, int64
 lrcc_status lrcc_plan_perm(const lrcc_plan* h, int32_t idx, int32_t* ints, int64_t* offs, double* alpha);
 /* ints int32[5]: nb R C arS arD; offs int64[2]. */
 lrcc_status lrcc_plan_btrans(const lrcc_plan* h, int32_t idx, int32_t* ints, int64_t* offs, double* alpha);
+/* Zero op: arena, first element and element count of the range set to zero in every
+ * right-hand side's copy of the arena.  Scratch buffers whose lifetimes do not overlap
+ * share memory; each starts its lifetime with such an op. */
+lrcc_status lrcc_plan_zero(const lrcc_plan* h, int32_t idx, int32_t* arena, int64_t* off_n);
 
 #ifdef __cplusplus
 }

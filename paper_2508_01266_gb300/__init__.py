@@ -84,6 +84,17 @@ def profile_query(h, tag=""):
     return ms.value, cnt.value, fl.value
 
 
+def profile_report(h):
+    """Per-tag totals of the recorded ops, slowest first: [(tag, ms, count, flops)]."""
+    buf = C.create_string_buffer(1 << 20)
+    _check(lib.lrcc_profile_report(h, buf, len(buf)), h)
+    rows = []
+    for line in buf.value.decode().splitlines():
+        tag, ms, n, fl = line.split("\t")
+        rows.append((tag, float(ms), int(n), float(fl)))
+    return rows
+
+
 def set_integrals(h, L, eps, dip):
     dev = torch.device("cuda")
     Lt, dt = _c128(L, dev), _c128(dip, dev)
@@ -153,6 +164,9 @@ class Problem:
 
     def profile_query(self, tag=""):
         return profile_query(self.h, tag)
+
+    def profile_report(self):
+        return profile_report(self.h)
 
     @property
     def kernel_launches(self):

@@ -44,6 +44,7 @@ _SIGS = {
     "lrcc_profile": (C.c_int, [VP, C.c_int32]),
     "lrcc_profile_query": (C.c_int, [VP, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_double)]),
+    "lrcc_profile_report": (C.c_int, [VP, C.c_char_p, C.c_int64]),
     "lrcc_plan_create": (C.c_int, [C.POINTER(lrcc_dims), C.c_int64, C.POINTER(VP)]),
     "lrcc_plan_destroy": (None, [VP]),
     "lrcc_plan_info": (C.c_int, [VP, VP, VP, VP]),
@@ -53,6 +54,7 @@ _SIGS = {
     "lrcc_plan_gemm": (C.c_int, [VP, C.c_int32, VP, VP, VP, VP, VP, VP, VP]),
     "lrcc_plan_perm": (C.c_int, [VP, C.c_int32, VP, VP, VP]),
     "lrcc_plan_btrans": (C.c_int, [VP, C.c_int32, VP, VP, VP]),
+    "lrcc_plan_zero": (C.c_int, [VP, C.c_int32, VP, VP]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)

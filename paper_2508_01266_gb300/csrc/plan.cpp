@@ -84,6 +84,7 @@ struct B {
     int64_t off = P.arena_size[ar];
     n = (n + 31) / 32 * 32;  // 512-byte alignment of every buffer
     P.arena_size[ar] += n;
+    if (ar == AR_SCR) P.scr_bufs.push_back({off, n});
     return off;
   }
   T4 t4(int ar, int kind, int a, int b, int c, int d) {
@@ -220,6 +221,148 @@ struct B {
     g_push(pr);
   }
 };
+
+// scratch buffer containing element offset `off` (buffers sorted by offset)
+int scr_find(const std::vector<ScrBuf>& bufs, int64_t off) {
+  int lo = 0, hi = (int)bufs.size() - 1, ans = -1;
+  while (lo <= hi) {
+    int mid = (lo + hi) / 2;
+    if (bufs[mid].off <= off) {
+      ans = mid;
+      lo = mid + 1;
+    } else {
+      hi = mid - 1;
+    }
+  }
+  if (ans < 0 || off >= bufs[ans].off + bufs[ans].n) throw std::runtime_error("scratch offset outside every buffer");
+  return ans;
+}
+
+// scratch buffers touched by an op
+void scr_touched(const Plan& P, const Op& op, const std::vector<ScrBuf>& bufs, std::vector<int>& out) {
+  out.clear();
+  if (op.kind == OP_GEMM) {
+    const Gemm& g = P.gemms[op.idx];
+    if (g.arC == AR_SCR)
+      for (int64_t x : g.coff) out.push_back(scr_find(bufs, x));
+    if (g.arA == AR_SCR)
+      for (int64_t x : g.aoff) out.push_back(scr_find(bufs, x));
+    if (g.arB == AR_SCR)
+      for (int64_t x : g.boff) out.push_back(scr_find(bufs, x));
+  } else if (op.kind == OP_PERM) {
+    const Perm& p = P.perms[op.idx];
+    if (p.arS == AR_SCR) out.push_back(scr_find(bufs, p.offS));
+    if (p.arD == AR_SCR) out.push_back(scr_find(bufs, p.offD));
+  } else if (op.kind == OP_BTRANS) {
+    const BTrans& t = P.btrans[op.idx];
+    if (t.arS == AR_SCR) out.push_back(scr_find(bufs, t.offS));
+    if (t.arD == AR_SCR) out.push_back(scr_find(bufs, t.offD));
+  }
+  std::sort(out.begin(), out.end());
+  out.erase(std::unique(out.begin(), out.end()), out.end());
+}
+
+// Place scratch buffers so that buffers whose lifetimes overlap (within one program)
+// never share memory, rewrite every scratch offset, and insert OP_ZERO ops so that each
+// buffer starts at zero: forward programs zero it before its first use; for the
+// transposed Jacobian, the op of its last forward use records it in `zl`.
+void pack_scratch(Plan& P, const std::vector<Program*>& progs) {
+  std::vector<ScrBuf> bufs = P.scr_bufs;
+  const int nb = (int)bufs.size();
+  if (nb == 0) return;
+  std::vector<int> prog_of(nb, -1), first(nb, -1), last(nb, -1);
+  std::vector<int> t;
+  for (int pi = 0; pi < (int)progs.size(); ++pi) {
+    const Program& pr = *progs[pi];
+    for (int i = 0; i < (int)pr.ops.size(); ++i) {
+      scr_touched(P, pr.ops[i], bufs, t);
+      for (int b : t) {
+        if (prog_of[b] >= 0 && prog_of[b] != pi) throw std::runtime_error("scratch buffer shared by two programs");
+        prog_of[b] = pi;
+        if (first[b] < 0) first[b] = i;
+        last[b] = i;
+      }
+    }
+  }
+  std::vector<int> order(nb);
+  for (int i = 0; i < nb; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(),
+            [&](int a, int b) { return bufs[a].n > bufs[b].n || (bufs[a].n == bufs[b].n && a < b); });
+  std::vector<int64_t> place(nb, 0);
+  int64_t top = 0;
+  std::vector<int> placed;
+  for (int b : order) {
+    if (prog_of[b] < 0) continue;  // never used
+    std::vector<std::pair<int64_t, int64_t>> busy;
+    for (int q : placed)
+      if (prog_of[q] == prog_of[b] && !(last[q] < first[b] || last[b] < first[q]))
+        busy.push_back({place[q], place[q] + bufs[q].n});
+    std::sort(busy.begin(), busy.end());
+    int64_t off = 0;
+    for (auto& iv : busy) {
+      if (off + bufs[b].n <= iv.first) break;
+      off = std::max(off, iv.second);
+    }
+    place[b] = off;
+    top = std::max(top, off + bufs[b].n);
+    placed.push_back(b);
+  }
+  // zero points (physical regions), by program and op index, before remapping
+  std::vector<std::vector<std::vector<int>>> zfirst(progs.size());
+  for (size_t pi = 0; pi < progs.size(); ++pi) zfirst[pi].assign(progs[pi]->ops.size(), {});
+  std::vector<std::vector<int>> zlast(progs[0]->ops.size());
+  for (int b = 0; b < nb; ++b) {
+    if (prog_of[b] < 0) continue;
+    P.zeros.push_back({AR_SCR, place[b], bufs[b].n});
+    const int zi = (int)P.zeros.size() - 1;
+    zfirst[prog_of[b]][first[b]].push_back(zi);
+    if (prog_of[b] == 0) zlast[last[b]].push_back(zi);
+  }
+  auto remap = [&](int64_t x) {
+    const int b = scr_find(bufs, x);
+    return place[b] + (x - bufs[b].off);
+  };
+  for (Program* pr : progs)
+    for (const Op& op : pr->ops) {
+      if (op.kind == OP_GEMM) {
+        Gemm& g = P.gemms[op.idx];
+        if (g.arC == AR_SCR)
+          for (auto& x : g.coff) x = remap(x);
+        if (g.arA == AR_SCR)
+          for (auto& x : g.aoff) x = remap(x);
+        if (g.arB == AR_SCR)
+          for (auto& x : g.boff) x = remap(x);
+      } else if (op.kind == OP_PERM) {
+        Perm& p = P.perms[op.idx];
+        if (p.arS == AR_SCR) p.offS = remap(p.offS);
+        if (p.arD == AR_SCR) p.offD = remap(p.offD);
+      } else if (op.kind == OP_BTRANS) {
+        BTrans& q = P.btrans[op.idx];
+        if (q.arS == AR_SCR) q.offS = remap(q.offS);
+        if (q.arD == AR_SCR) q.offD = remap(q.offD);
+      }
+    }
+  for (size_t pi = 0; pi < progs.size(); ++pi) {
+    Program& pr = *progs[pi];
+    std::vector<Op> out;
+    for (size_t i = 0; i < pr.ops.size(); ++i) {
+      for (int zi : zfirst[pi][i]) {
+        Op z;
+        z.kind = OP_ZERO;
+        z.idx = zi;
+        out.push_back(z);
+      }
+      Op op = pr.ops[i];
+      if (pi == 0 && !zlast[i].empty()) {
+        P.zlists.push_back(zlast[i]);
+        op.zl = (int)P.zlists.size() - 1;
+      }
+      out.push_back(op);
+    }
+    pr.ops = out;
+  }
+  P.arena_size[AR_SCR] = top;
+}
 
 }  // namespace
 
@@ -981,6 +1124,8 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
     b.btr(E, nk, v, o, AR_OUT, Y1(0), AR_SCR, tmp, 1.0, "egrad -> y1");
   }
 
+  pack_scratch(P, {&P.jac, &P.xi, &P.egrad});
+
   double tot = 0;
   for (const Op& op : J.ops)
     if (op.kind == OP_GEMM) tot += (double)P.gemms[op.idx].flops();
@@ -1029,6 +1174,12 @@ std::string validate_plan(const Plan& P, const Program& pr) {
       int64_t n = (int64_t)t.nb * t.R * t.C;
       if (!(e = chk(t.arS, t.offS, n, "btrans src " + t.tag)).empty()) return e;
       if (!(e = chk(t.arD, t.offD, n, "btrans dst " + t.tag)).empty()) return e;
+    } else if (op.kind == OP_ZERO) {
+      if (op.idx < 0 || op.idx >= (int)P.zeros.size()) return "zero: bad index";
+      const ZeroSpec& z = P.zeros[op.idx];
+      if (!(e = chk(z.arena, z.off, z.n, "zero")).empty()) return e;
+    } else {
+      return "unknown op kind";
     }
   }
   return "";
@@ -1048,7 +1199,14 @@ Program transpose_program(Plan& P, const Program& fwd) {
   std::vector<int> pending;  // index in fwd of fixed-only ops not yet emitted
   for (int i = (int)fwd.ops.size() - 1; i >= 0; --i) {
     const Op& op = fwd.ops[i];
-    if (op.fixed_only) continue;
+    if (op.fixed_only || op.kind == OP_ZERO) continue;
+    if (op.zl >= 0)
+      for (int zi : P.zlists[op.zl]) {
+        Op z;
+        z.kind = OP_ZERO;
+        z.idx = zi;
+        out.ops.push_back(z);
+      }
     if (op.kind == OP_GEMM) {
       const Gemm& g = P.gemms[op.idx];
       if (g.arA == AR_WS || g.arB == AR_WS) {

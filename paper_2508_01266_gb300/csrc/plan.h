@@ -82,11 +82,15 @@ enum OpKind : int { OP_GEMM = 0, OP_PERM = 1, OP_BTRANS = 2, OP_ZERO = 3 };
 
 struct Op {
   int kind = OP_GEMM;
-  int idx = 0;        // index into the plan's gemms / perms / btrans
+  int idx = 0;        // index into the plan's gemms / perms / btrans / zeros
   int fixed_only = 0; // 1: reads/writes only FIX/WS (e.g. a W-block build); not transposed
+  int zl = -1;        // index into Plan::zlists: scratch buffers whose last use is this op
+                      // (the transposed program zeroes them before this op's transpose)
 };
 
-struct ZeroSpec { int arena; int64_t off, n; };
+struct ZeroSpec { int arena; int64_t off, n; };  // zero n elements before the next op
+
+struct ScrBuf { int64_t off, n; };
 
 struct Program {
   std::vector<Op> ops;
@@ -101,6 +105,8 @@ struct Plan {
   std::vector<Perm> perms;
   std::vector<BTrans> btrans;
   std::vector<ZeroSpec> zeros;
+  std::vector<ScrBuf> scr_bufs;     // scratch buffers (logical, before liveness packing)
+  std::vector<std::vector<int>> zlists;  // lists of indices into `zeros`
   Program ground;    // fixed-only ops: ground-state intermediates
   Program jac;       // linear in IN -> OUT (uses SCR, WS)
   Program xi;        // perturbation right-hand side xi^X(t', mu): IN = t' (paper units) -> OUT

@@ -155,3 +155,14 @@ lrcc_status lrcc_plan_btrans(const lrcc_plan* h, int32_t idx, int32_t* ints, int
 }
 
 }  // extern "C"
+
+lrcc_status lrcc_plan_zero(const lrcc_plan* h, int32_t idx, int32_t* arena, int64_t* off_n) {
+  if (!h || idx < 0 || idx >= (int32_t)h->P.zeros.size()) return LRCC_EINVAL;
+  const ZeroSpec& z = h->P.zeros[idx];
+  if (arena) *arena = z.arena;
+  if (off_n) {
+    off_n[0] = z.off;
+    off_n[1] = z.n;
+  }
+  return LRCC_OK;
+}

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -277,9 +278,10 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
   for (const Op& op : pr.ops) {
     cudaError_t e = cudaSuccess;
     const int nr = op.fixed_only ? 1 : nrhs;
-    const char* optag = op.kind == OP_GEMM ? plan.gemms[op.idx].tag.c_str()
-                        : op.kind == OP_PERM ? plan.perms[op.idx].tag.c_str()
-                                             : plan.btrans[op.idx].tag.c_str();
+    const char* optag = op.kind == OP_GEMM     ? plan.gemms[op.idx].tag.c_str()
+                        : op.kind == OP_PERM   ? plan.perms[op.idx].tag.c_str()
+                        : op.kind == OP_BTRANS ? plan.btrans[op.idx].tag.c_str()
+                                               : "zero";
     nvtxRangePushA(optag);  // per-op range (ncu --nvtx --nvtx-include "<tag>/")
     ProfRec rec{};
     if (prof) {
@@ -291,8 +293,10 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
         rec.flops = (double)plan.gemms[op.idx].flops() * nr;
       } else if (op.kind == OP_PERM) {
         rec.tag = "perm:" + plan.perms[op.idx].tag;
-      } else {
+      } else if (op.kind == OP_BTRANS) {
         rec.tag = "btrans:" + plan.btrans[op.idx].tag;
+      } else {
+        rec.tag = "zero";
       }
       cudaEventRecord(rec.a, st);
     }
@@ -347,6 +351,11 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
       a.ar = t.ar; a.ai = t.ai;
       e = launch_btrans_f64(a, nr, st);
       ++launches;
+    } else if (op.kind == OP_ZERO) {
+      // a scratch buffer starts its lifetime at zero (buffers with disjoint lifetimes share memory)
+      const ZeroSpec& z = plan.zeros[op.idx];
+      const size_t pitch = (size_t)std::max<long long>(stride[z.arena], z.n) * sizeof(double2);
+      e = cudaMemset2DAsync(ar[z.arena] + z.off, pitch, 0, (size_t)z.n * sizeof(double2), nr, st);
     }
     if (prof) {
       cudaEventRecord(rec.b, st);
@@ -371,12 +380,11 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
 
 lrcc_status Runtime::apply(int transpose, int nrhs, cudaStream_t st, int prec) {
   double2* ar[AR_COUNT] = {fix, in, out, scr, ws};
-  const int64_t vin = plan.arena_size[AR_IN], vscr = plan.arena_size[AR_SCR];
-  // zero the result side and the scratch (every op accumulates)
+  const int64_t vin = plan.arena_size[AR_IN];
+  // zero the result side (every op accumulates); scratch buffers are zeroed by the
+  // program's own zero ops at the start of their lifetimes
   double2* res = transpose ? in : out;
   if (!ck(cudaMemsetAsync(res, 0, vin * nrhs * sizeof(double2), st), "cudaMemsetAsync")) return LRCC_ECUDA;
-  if (vscr > 0 && !ck(cudaMemsetAsync(scr, 0, vscr * nrhs * sizeof(double2), st), "cudaMemsetAsync"))
-    return LRCC_ECUDA;
   return run(transpose ? jacT : plan.jac, ar, nrhs, st, prec);
 }
 
@@ -579,6 +587,38 @@ lrcc_status lrcc_profile_query(lrcc_problem* p, const char* tag, double* ms, int
   if (count) *count = c;
   if (flops) *flops = f;
   return LRCC_OK;
+}
+
+lrcc_status lrcc_profile_report(lrcc_problem* p, char* buf, int64_t len) {
+  if (!p || !buf || len < 1) return LRCC_EINVAL;
+  Runtime& rt = p->rt;
+  if (!rt.ck(cudaDeviceSynchronize(), "profile sync")) return LRCC_ECUDA;
+  struct Agg {
+    double ms = 0.0, flops = 0.0;
+    int64_t n = 0;
+  };
+  std::map<std::string, Agg> agg;
+  for (auto& r : rt.prof_recs) {
+    float x = 0.f;
+    if (!rt.ck(cudaEventElapsedTime(&x, r.a, r.b), "cudaEventElapsedTime")) return LRCC_ECUDA;
+    Agg& a = agg[r.tag];
+    a.ms += x;
+    a.flops += r.flops;
+    ++a.n;
+  }
+  std::vector<std::pair<std::string, Agg>> v(agg.begin(), agg.end());
+  std::sort(v.begin(), v.end(), [](const auto& x, const auto& y) { return x.second.ms > y.second.ms; });
+  std::string out;
+  char line[256];
+  for (auto& e : v) {
+    std::snprintf(line, sizeof(line), "%s\t%.6f\t%lld\t%.6e\n", e.first.c_str(), e.second.ms, (long long)e.second.n,
+                  e.second.flops);
+    out += line;
+  }
+  const size_t n = std::min<size_t>(out.size(), (size_t)len - 1);
+  std::memcpy(buf, out.data(), n);
+  buf[n] = 0;
+  return out.size() < (size_t)len ? LRCC_OK : LRCC_EINVAL;
 }
 
 }  // extern "C"

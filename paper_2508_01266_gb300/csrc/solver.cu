@@ -204,9 +204,7 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
   };
   auto run_prog = [&](const Program& pr, int nrhs) -> lrcc_status {
     double2* ar[AR_COUNT] = {rt.fix, rt.in, rt.out, rt.scr, rt.ws};
-    if (!rt.ck(cudaMemsetAsync(rt.out, 0, (size_t)vec * nrhs * sizeof(double2), st), "memset") ||
-        !rt.ck(cudaMemsetAsync(rt.scr, 0, (size_t)P.arena_size[AR_SCR] * nrhs * sizeof(double2), st), "memset"))
-      return LRCC_ECUDA;
+    if (!rt.ck(cudaMemsetAsync(rt.out, 0, (size_t)vec * nrhs * sizeof(double2), st), "memset")) return LRCC_ECUDA;
     return rt.run(pr, ar, nrhs, st);
   };
   auto set_mu = [&](int comp) -> lrcc_status {

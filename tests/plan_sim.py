@@ -76,6 +76,11 @@ class PlanView:
                 al = np.zeros(2)
                 lib.lrcc_plan_perm(h, idx, _p(ints, I32P), _p(offs, I64P), _p(al, F64P))
                 ops.append(("perm", fixed, dict(ints=ints.copy(), offs=offs.copy(), alpha=complex(al[0], al[1]))))
+            elif kind == 3:
+                ar = np.zeros(1, np.int32)
+                on = np.zeros(2, np.int64)
+                lib.lrcc_plan_zero(h, idx, _p(ar, I32P), _p(on, I64P))
+                ops.append(("zero", fixed, dict(arena=int(ar[0]), off=int(on[0]), n=int(on[1]))))
             else:
                 ints = np.zeros(5, np.int32)
                 offs = np.zeros(2, np.int64)
@@ -167,6 +172,8 @@ def run(ops, arenas):
             Dst, Src = arenas[arD], arenas[arS]
             vals = d["alpha"] * Src[offS + os_.ravel()]
             np.add.at(Dst, offD + od.ravel(), vals)
+        elif kind == "zero":
+            arenas[d["arena"]][d["off"]:d["off"] + d["n"]] = 0
         elif kind == "btrans":
             nb, R, Cc, arS, arD = map(int, d["ints"])
             offS, offD = map(int, d["offs"])

@@ -70,8 +70,12 @@ def _sim_setup(lib, prob, t1, t2sc, ws):
 
 def _sim_apply(pv, ar, x1, x2p, which):
     a = [x.copy() for x in ar]
-    for i in (1, 2, 3, 4):
+    for i in (1, 2):
         a[i][:] = 0
+    # scratch and workspace start as garbage: the programs' own zero ops (scratch) and
+    # overwriting W builds (workspace) must make every value they read defined
+    for i in (3, 4):
+        a[i][:] = np.nan
     off = pv.offsets
     fwd = which != 2  # the transposed program reads OUT and writes IN
     src = a[1] if fwd else a[2]
