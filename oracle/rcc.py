@@ -480,6 +480,81 @@ def polarizability(R: RCC, t1, t2, l1, l2, mus, omegas, tol=1e-11, verbose=False
     return out
 
 
+def eta_vector(R: RCC, t1, t2, l1, l2, mu):
+    """eta^X = P_sym grad_t dL/d eps_X in the plain pairing (Eq. 15 ingredients).  L is
+    linear in the one-body operator, so the central difference with eps = 1 is exact."""
+    p1, p2 = lagrangian_grad(R, t1, t2, l1, l2, R.h + mu)
+    m1, m2 = lagrangian_grad(R, t1, t2, l1, l2, R.h - mu)
+    return 0.5 * (p1 - m1), 0.5 * (p2 - m2)
+
+
+def F_vector(R: RCC, t1, t2, l1, l2, u1, u2):
+    """F u = d/ds [grad_t L](t + s u): exact 4-point stencil (grad L has degree <= 3 in t)."""
+    sc = max(_maxabs(u1, u2), 1e-300)
+    hh = 1e-2 / sc
+    g = [lagrangian_grad(R, t1 + c * hh * u1, t2 + c * hh * u2, l1, l2) for c in (-2.0, -1.0, 1.0, 2.0)]
+    f1 = (g[0][0] - 8.0 * g[1][0] + 8.0 * g[2][0] - g[3][0]) / (12.0 * hh)
+    f2 = (g[0][1] - 8.0 * g[1][1] + 8.0 * g[2][1] - g[3][1]) / (12.0 * hh)
+    return f1, f2
+
+
+def solve_left_response(R: RCC, t1, t2, b1, b2, omega, tol=1e-11, maxit=300, verbose=False):
+    """Left perturbed multipliers: y (A + w) = -b, i.e. (A^T + w) y = -b on the pair-symmetric
+    subspace (transpose products), Jacobi + DIIS, relative residual <= tol."""
+    d1, d2 = R.denominators()
+    p1, p2 = d1 + omega, d2 + omega
+    y1, y2 = -b1 / p1, -b2 / p2
+    nrm = _maxabs(b1, b2)
+    if nrm == 0.0:
+        return y1, y2, 0
+    diis = DIIS()
+    for it in range(maxit):
+        a1, a2 = R.transpose(t1, t2, y1, y2)
+        r1, r2 = a1 + omega * y1 + b1, a2 + omega * y2 + b2
+        err = _maxabs(r1, r2) / nrm
+        if verbose:
+            print("left", it, err)
+        if err <= tol:
+            return y1, y2, it
+        n1, n2 = y1 - r1 / p1, y2 - r2 / p2
+        x = diis.update(_flat(n1, n2), _flat(n1 - y1, n2 - y2))
+        y1, y2 = _unflat(x, y1.shape, y2.shape)
+        y2 = R.sym(y2)
+    raise RuntimeError("left response equations did not converge")
+
+
+def _pair(a1, a2, b1, b2):
+    return complex((a1 * b1).sum() + (a2 * b2).sum())
+
+
+def polarizability_left(R: RCC, t1, t2, l1, l2, mus, omegas, tol=1e-11):
+    """alpha_XY(w) per cell from the asymmetric (left-response) form of the CC linear-
+    response function:
+        <<X;Y>>_w = 1/2 C^{+-w} [eta^Y t^X(-w) + tbar^X(-w) xi^Y],
+        tbar^X(w) (A + w) = -(eta^X + F t^X(w)).
+    Returns (symmetrised alpha = (alpha_XY + alpha_YX)/2, unsymmetrised alpha)."""
+    nc = len(mus)
+    out = np.zeros((len(omegas), nc, nc), dtype=np.complex128)
+    xis = [perturbation_rhs(R, t1, t2, m) for m in mus]
+    etas = [eta_vector(R, t1, t2, l1, l2, m) for m in mus]
+
+    def left(c, tc, ws):
+        f1, f2 = F_vector(R, t1, t2, l1, l2, *tc)
+        return solve_left_response(R, t1, t2, etas[c][0] + f1, etas[c][1] + f2, ws, tol)[:2]
+
+    for iw, w in enumerate(omegas):
+        tp = [solve_response(R, t1, t2, *xis[c], w, tol)[:2] for c in range(nc)]
+        tm = [solve_response(R, t1, t2, *xis[c], -w, tol)[:2] for c in range(nc)] if w != 0 else tp
+        lm = [left(c, tm[c], -w) for c in range(nc)]
+        lp = [left(c, tp[c], w) for c in range(nc)] if w != 0 else lm
+        for x in range(nc):
+            for y in range(nc):
+                a = _pair(*etas[y], *tm[x]) + _pair(*lm[x], *xis[y])
+                b = _pair(*etas[y], *tp[x]) + _pair(*lp[x], *xis[y])
+                out[iw, x, y] = -0.5 * (a + np.conj(b)) / R.nk
+    return 0.5 * (out + out.transpose(0, 2, 1)), out
+
+
 def dipole_ops(prob, comps=(0, 1, 2)):
     """k-diagonal dipole matrices mu[k,p,q] for the chosen components."""
     return [_t(prob.dip[c]) for c in comps]

@@ -5,7 +5,8 @@ P2 Jacobian stencil vs brute-force commutator; P3 adjoint identity; P4/P9 closed
 k-blocked residual vs the dense spin-orbital one (Nk = 1 molecular case included);
 P5 decoupled replicas; P6 two electrons = FCI (energy and sum-over-states alpha,
 with and without time-reversal symmetry); P7 finite field; P8 symmetries and
-momentum zeros; P11 zero interaction closed form; P12 first Jacobi step = MP2.
+momentum zeros; P10 left-response (asymmetric) alpha = symmetric alpha, and = FCI
+for two electrons; P11 zero interaction closed form; P12 first Jacobi step = MP2.
 """
 import numpy as np
 import pytest
@@ -164,6 +165,58 @@ def test_two_electrons_equal_fci(tr):
             assert np.abs(a_cc.imag).max() < 1e-10
         else:  # exact alpha is Hermitian, not symmetric, for complex operators
             assert np.allclose(a_cc, a_cc.conj().T, atol=1e-10)
+
+
+# P10 --------------------------------------------------------------------------
+@pytest.mark.parametrize("tr", [True, False])
+def test_left_response_alpha_equals_fci_two_electrons(tr):
+    """Two electrons: the asymmetric form (left perturbed multipliers from transpose
+    products) reproduces the FCI sum over states, with and without TR symmetry."""
+    p = make_problem(1, 1, 3, 4, seed=61, sigma_l=0.15, tr=tr)
+    R = rcc.RCC(p)
+    S = spinorb.SpinOrbitalSystem(p)
+    t1, t2, _ = rcc.solve_ccsd(R, tol=1e-12)
+    l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=1e-12)
+    comps = (0, 2)
+    mus = rcc.dipole_ops(p, comps)
+    ops = [spinorb.one_body_to_spinorb(S, p.dip[c]) for c in comps]
+    for w in (0.0, 0.07):
+        _, a_fci = fci.sos_polarizability(S, ops, w)
+        _, a_left = rcc.polarizability_left(R, t1, t2, l1, l2, mus, [w])
+        assert np.abs(a_left[0] - a_fci).max() < 1e-9 * np.abs(a_fci).max()
+
+
+def test_left_response_alpha_equals_symmetric_form():
+    """Beyond two electrons (Nk = 2: four electrons in the two-cell supercell): asymmetric
+    alpha = symmetric alpha element by element at convergence, two components at +-w."""
+    p = make_problem(2, 1, 2, 3, seed=101, sigma_l=0.2)
+    R = rcc.RCC(p)
+    t1, t2, _ = rcc.solve_ccsd(R, tol=1e-12)
+    l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=1e-12)
+    mus = rcc.dipole_ops(p, (0, 2))
+    om = [0.09]
+    a_sym = rcc.polarizability(R, t1, t2, l1, l2, mus, om)
+    a_ls, a_left = rcc.polarizability_left(R, t1, t2, l1, l2, mus, om)
+    assert np.abs(a_left - a_sym).max() < 1e-9 * np.abs(a_sym).max()
+    assert np.abs(a_ls - 0.5 * (a_sym + a_sym.transpose(0, 2, 1))).max() < 1e-9 * np.abs(a_sym).max()
+
+
+def test_eta_and_F_vectors_match_scalar_stencils():
+    """eta^X . w and (F u) . w from the vector forms equal the scalar stencils."""
+    nk, o, v = 2, 1, 2
+    p = make_problem(nk, o, v, 3, seed=103, sigma_l=0.2)
+    R = rcc.RCC(p)
+    t1, t2 = (T(x) for x in random_amplitudes(nk, o, v, seed=104, scale1=0.05, scale2=0.05))
+    l1, l2 = (T(x) for x in random_amplitudes(nk, o, v, seed=105, scale1=0.05, scale2=0.05))
+    u1, u2 = (T(x) for x in random_amplitudes(nk, o, v, seed=106, scale1=1.0, scale2=1.0))
+    w1, w2 = (T(x) for x in random_amplitudes(nk, o, v, seed=107, scale1=1.0, scale2=1.0))
+    mu = rcc.dipole_ops(p, (1,))[0]
+    e1, e2 = rcc.eta_vector(R, t1, t2, l1, l2, mu)
+    ref = complex(rcc.eta_dot(R, t1, t2, l1, l2, mu, w1, w2))
+    assert abs(complex((e1 * w1).sum() + (e2 * w2).sum()) - ref) < 1e-10 * abs(ref)
+    f1, f2 = rcc.F_vector(R, t1, t2, l1, l2, u1, u2)
+    ref = complex(rcc.F_dot(R, t1, t2, l1, l2, u1, u2, w1, w2))
+    assert abs(complex((f1 * w1).sum() + (f2 * w2).sum()) - ref) < 1e-9 * abs(ref)
 
 
 # P5 ---------------------------------------------------------------------------
