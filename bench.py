@@ -169,6 +169,47 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_mixed(lr, prob, X1, X2, Y1, Y2, args, st, dist, products):
+    """Time the tensor-core products (BF16x3 and TF32) on the same vectors; Y1/Y2 are the
+    FP64 results (None: no error column)."""
+    import torch
+    mixed = {}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    BF16_PEAK = _measured_peak("bf16_tflops", 1900.0)
+    for prec, name, peak, passes in ((2, "bf16x3", BF16_PEAK, 3), (1, "tf32", BF16_PEAK * 1.1 / 2.25, 1)):
+        opts = lr.default_options(precision=prec)
+        M1, M2 = torch.empty_like(X1), torch.empty_like(X2)
+        for _ in range(args.warmup):
+            prob.jacobian_apply(X1, X2, y1=M1, y2=M2, options=opts)
+        torch.cuda.synchronize()
+        prob.profile(True)
+        m0 = prob.kernel_launches
+        e0.record(st)
+        for _ in range(args.steps):
+            prob.jacobian_apply(X1, X2, y1=M1, y2=M2, options=opts)
+        e1.record(st)
+        torch.cuda.synchronize()
+        mms = _max_over_ranks(dist, e0.elapsed_time(e1))
+        lms, ln, lfl = prob.profile_query("ladder")
+        ams, an, afl = prob.profile_query("")
+        prob.profile(False)
+        err = None
+        if Y1 is not None:
+            err = max(float((M1 - Y1).abs().max() / Y1.abs().max()), float((M2 - Y2).abs().max() / Y2.abs().max()))
+        lach = (lfl / max(ln, 1)) / ((lms / max(ln, 1)) * 1e-3) / 1e12 if ln else None
+        mixed[name] = {"value": products / (mms / 1000.0), "unit": "products/s", "ms_per_step": mms / args.steps,
+                       "gpu_launches": int(prob.kernel_launches - m0),
+                       "max_rel_err_vs_fp64": err,
+                       "ladder": {"achieved_tflops_algorithmic": lach,
+                                  "tensor_pipe_tflops": lach * passes if lach else None,
+                                  "peak_tflops": peak, "frac": (lach * passes / peak) if lach else None,
+                                  "peak_source": "measured bf16 dense (MEASURED_PEAKS.json)" if prec == 2 else
+                                  "measured bf16 x nominal tf32/bf16 ratio 1.1/2.25"},
+                       "step_tflops_algorithmic": afl / (ams * 1e-3) / 1e12 if ams else None}
+    return mixed
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -180,6 +221,10 @@ def main():
     ap.add_argument("--ref-blocks", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--mixed-only", action="store_true",
+                    help="time only the tensor-core (mixed precision) products (profiling runs)")
+    ap.add_argument("--shape", default="",
+                    help="Nk,nocc,nvir,naux overriding the workload's sizes (small cases for ncu captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -199,6 +244,8 @@ def main():
     from synth import make_problem, random_amplitudes, random_probe
 
     cfg, comps, omegas, nsys = workload(args.config)
+    if args.shape:
+        cfg = dict(zip(("nk", "nocc", "nvir", "naux"), (int(x) for x in args.shape.split(","))))
     nk, o, v, Q = cfg["nk"], cfg["nocc"], cfg["nvir"], cfg["naux"]
     nrhs = args.nrhs or nsys
     p = make_problem(nk, o, v, Q, seed=1266)
@@ -213,6 +260,13 @@ def main():
     Y1 = torch.empty_like(X1)
     Y2 = torch.empty_like(X2)
     st = torch.cuda.current_stream()
+    if args.mixed_only:  # profiling runs: tensor-core products only, one informational line
+        mixed = time_mixed(lr, prob, X1, X2, None, None, args, st, dist, nrhs * args.steps * ws)
+        if rank == 0:
+            print(json.dumps({"profiling": True, "workload": cfg, "rhs_per_step": nrhs, "mixed_precision": mixed}),
+                  flush=True)
+        prob.close()
+        return
 
     def step():
         prob.jacobian_apply(X1, X2, y1=Y1, y2=Y2)
@@ -282,37 +336,7 @@ def main():
             "step_gflops_algorithmic": all_fl / (all_ms * 1e-3) / 1e9 if all_ms else None}
 
     # mixed precision: the same product with the GEMMs on tcgen05 (BF16x3 and TF32, FP32 accumulate)
-    mixed = {}
-    if not args.no_mixed:
-        BF16_PEAK = _measured_peak("bf16_tflops", 1900.0)
-        for prec, name, peak, passes in ((2, "bf16x3", BF16_PEAK, 3), (1, "tf32", BF16_PEAK * 1.1 / 2.25, 1)):
-            opts = lr.default_options(precision=prec)
-            M1, M2 = torch.empty_like(Y1), torch.empty_like(Y2)
-            for _ in range(args.warmup):
-                prob.jacobian_apply(X1, X2, y1=M1, y2=M2, options=opts)
-            torch.cuda.synchronize()
-            prob.profile(True)
-            m0 = prob.kernel_launches
-            e0.record(st)
-            for _ in range(args.steps):
-                prob.jacobian_apply(X1, X2, y1=M1, y2=M2, options=opts)
-            e1.record(st)
-            torch.cuda.synchronize()
-            mms = _max_over_ranks(dist, e0.elapsed_time(e1))
-            lms, ln, lfl = prob.profile_query("ladder")
-            ams, an, afl = prob.profile_query("")
-            prob.profile(False)
-            err = max(float((M1 - Y1).abs().max() / Y1.abs().max()), float((M2 - Y2).abs().max() / Y2.abs().max()))
-            lach = (lfl / max(ln, 1)) / ((lms / max(ln, 1)) * 1e-3) / 1e12 if ln else None
-            mixed[name] = {"value": products / (mms / 1000.0), "unit": "products/s", "ms_per_step": mms / args.steps,
-                           "gpu_launches": int(prob.kernel_launches - m0),
-                           "max_rel_err_vs_fp64": err,
-                           "ladder": {"achieved_tflops_algorithmic": lach,
-                                      "tensor_pipe_tflops": lach * passes if lach else None,
-                                      "peak_tflops": peak, "frac": (lach * passes / peak) if lach else None,
-                                      "peak_source": "measured bf16 dense (MEASURED_PEAKS.json)" if prec == 2 else
-                                      "measured bf16 x nominal tf32/bf16 ratio 1.1/2.25"},
-                           "step_tflops_algorithmic": afl / (ams * 1e-3) / 1e12 if ams else None}
+    mixed = {} if args.no_mixed else time_mixed(lr, prob, X1, X2, Y1, Y2, args, st, dist, products)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

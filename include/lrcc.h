@@ -64,6 +64,9 @@ typedef struct {
   int32_t autotune;
   int32_t use_graphs;
   uint64_t spin_timeout_cycles;
+  int32_t response_form; /* lrcc_polarizability: 0 symmetric form (default); 1 asymmetric
+                            (left-response) form, symmetrised (alpha_XY + alpha_YX) / 2;
+                            2 asymmetric form as computed */
 } lrcc_options;
 
 /* ---------------------------------------------------------------------------
@@ -120,9 +123,13 @@ lrcc_status lrcc_jacobian_apply(lrcc_problem* p, int32_t transpose, int32_t nrhs
 lrcc_status lrcc_jacobian_apply_noalloc(lrcc_problem* p, int32_t transpose, const void* x1, const void* x2,
                                         void* y1, void* y2, void* stream);
 
-/* Polarizability alpha_XY(w) per cell (Eq. 15, symmetric form), a.u., for the
- * dipole components comps[0..ncomp) (0 = x, 1 = y, 2 = z) and frequencies
- * omegas[0..nomega).  alpha receives c128 [nomega][ncomp][ncomp] in host memory.
+/* Polarizability alpha_XY(w) per cell (Eq. 15), a.u., for the dipole components
+ * comps[0..ncomp) (0 = x, 1 = y, 2 = z) and frequencies omegas[0..nomega).
+ * opt->response_form 0: the symmetric CC linear-response function
+ *   <<X;Y>>_w = 1/2 C^{+-w} [eta^X t^Y(w) + eta^Y t^X(-w) + F t^X(-w) t^Y(w)];
+ * 1 and 2: the asymmetric form 1/2 C^{+-w} [eta^Y t^X(-w) + tbar^X(-w) xi^Y] with the
+ * left perturbed multipliers tbar^X(w) (A + w) = -(eta^X + F t^X(w)), solved with
+ * transposed Jacobian products (equal to form 0 at convergence).  alpha receives c128 [nomega][ncomp][ncomp] in host memory.
  * info (may be NULL) receives int32 [2 + ncomp]: total iterations, status of the
  * last solve, and per component 1 if it was skipped because its integrals vanish
  * (max |mu| < 1e-14, Sec. II.C).  Requires set_integrals and set_ground_state

@@ -15,7 +15,7 @@ from ._lib import lib, lrcc_dims, lrcc_options, STATUS, LIB_PATH
 
 __all__ = ["LrccError", "Problem", "default_options", "create", "set_integrals", "set_ground_state",
            "jacobian_apply", "polarizability", "last_error", "destroy", "kernel_launches", "profile",
-           "profile_query", "LIB_PATH"]
+           "profile_query", "profile_report", "LRCCJacobian", "jacobian", "LIB_PATH"]
 
 
 class LrccError(RuntimeError):
@@ -182,3 +182,6 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+from .autograd import LRCCJacobian, jacobian  # noqa: E402

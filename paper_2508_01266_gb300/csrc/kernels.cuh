@@ -19,6 +19,12 @@ struct GemmArgs {
   const double2* B;
   double2* C;
   long long sA, sB, sC;  // per-vector strides of variable arenas (0 for shared ones)
+  // split-K: nsplit > 1 divides each batch entry's (segment, K block) iteration space
+  // into nsplit contiguous ranges; every split writes its raw partial tile to
+  // part[rhs][batch][split][M][N] and launch_split_reduce sums the splits in a fixed
+  // order, applies alpha and the epilogue (bitwise reproducible).
+  int nsplit = 1;
+  double2* part = nullptr;
 };
 
 struct PermArgs {
@@ -49,6 +55,9 @@ void gemm_tile_dims(int tile, int* bm, int* bn);
 int gemm_pick_tile(int M, int N);
 
 cudaError_t launch_gemm_f64(const GemmArgs& g, int tile, int nrhs, cudaStream_t st);
+cudaError_t launch_split_reduce(const GemmArgs& g, int nrhs, cudaStream_t st);
+constexpr int F64_BK = 8;  // complex K per iteration of the FP64 GEMM
+constexpr int TC_BK = 16;  // complex K per iteration of the unpacked tensor-core GEMM
 cudaError_t launch_perm_f64(const PermArgs& p, int nrhs, cudaStream_t st);
 cudaError_t launch_btrans_f64(const BTransArgs& t, int nrhs, cudaStream_t st);
 

@@ -24,8 +24,11 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   __shared__ double2 Bs[BK][BN];
   const int tpb = g.tiles_m * g.tiles_n;
   const int bid = blockIdx.x;
-  const int batch = bid / tpb;
-  const int t = bid - batch * tpb;
+  const int per_batch = tpb * g.nsplit;
+  const int batch = bid / per_batch;
+  const int rem = bid - batch * per_batch;
+  const int sp = rem / tpb;
+  const int t = rem - sp * tpb;
   const int m0 = (t / g.tiles_n) * BM;
   const int n0 = (t % g.tiles_n) * BN;
   const long long rhs = blockIdx.y;
@@ -43,11 +46,18 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       accr[i][j] = 0.0;
       acci[i][j] = 0.0;
     }
+  // iteration space of this batch entry: (segment, K block), segment-major; this CTA
+  // takes the split's contiguous range of it
   const int s0 = g.sbeg[batch], s1 = g.sbeg[batch + 1];
-  for (int s = s0; s < s1; ++s) {
+  const int nkb = (K + BK - 1) / BK;
+  const long long total = (long long)(s1 - s0) * nkb;
+  const long long lo = total * sp / g.nsplit, hi = total * (sp + 1) / g.nsplit;
+  int s = s0 + (int)(lo / nkb), kb = (int)(lo % nkb);
+  for (long long it = lo; it < hi; ++it) {
     const double2* Ap = Ab + g.aoff[s];
     const double2* Bp = Bb + g.boff[s];
-    for (int k0 = 0; k0 < K; k0 += BK) {
+    const int k0 = kb * BK;
+    {
       for (int idx = tid; idx < BM * BK; idx += NT) {
         int m, k;
         if (!g.ta) {
@@ -96,6 +106,24 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       }
       __syncthreads();
     }
+    if (++kb == nkb) {
+      kb = 0;
+      ++s;
+    }
+  }
+  if (g.nsplit > 1) {  // raw partial tile; alpha and the epilogue come in the reduction
+    double2* Pp = g.part + ((rhs * g.nbatch + batch) * g.nsplit + sp) * (long long)M * N;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int m = m0 + ty + i * NTY;
+      if (m >= M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int n = n0 + tx + j * NTX;
+        if (n < N) Pp[(long long)m * N + n] = make_double2(accr[i][j], acci[i][j]);
+      }
+    }
+    return;
   }
   double2* Cp = Cb + g.coff[batch];
 #pragma unroll
@@ -128,6 +156,50 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   }
 }
 
+// Sum of the split partials in split order, alpha, and the GEMM's epilogue.
+__global__ void split_reduce_kernel(GemmArgs g) {
+  const long long rhs = blockIdx.y;
+  const long long mn = (long long)g.M * g.N;
+  const long long total = (long long)g.nbatch * mn;
+  double2* Cb = g.C + rhs * g.sC;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int batch = (int)(e / mn);
+    const long long r = e - (long long)batch * mn;
+    const int m = (int)(r / g.N), n = (int)(r - (long long)m * g.N);
+    const double2* p = g.part + (rhs * g.nbatch + batch) * g.nsplit * mn + r;
+    double sr = 0.0, si = 0.0;
+    for (int k = 0; k < g.nsplit; ++k) {
+      const double2 v = p[(long long)k * mn];
+      sr += v.x;
+      si += v.y;
+    }
+    const double vr = g.ar * sr - g.ai * si, vi = g.ar * si + g.ai * sr;
+    double2* Cp = Cb + g.coff[batch];
+    if (g.epi == 0) {
+      double2* cp = Cp + (long long)m * g.ldc + n;
+      double2 cv = *cp;
+      cv.x += vr;
+      cv.y += vi;
+      *cp = cv;
+    } else {
+      const int a = m / g.ep2, c = m - a * g.ep2;
+      const int b = n / g.ep3, d = n - b * g.ep3;
+      Cp[(((long long)a * g.ep1 + b) * g.ep2 + c) * g.ep3 + d] = make_double2(vr, vi);
+    }
+  }
+}
+
+cudaError_t launch_split_reduce(const GemmArgs& g, int nrhs, cudaStream_t st) {
+  const long long total = (long long)g.nbatch * g.M * g.N;
+  if (total <= 0) return cudaSuccess;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152LL * 16) blocks = 152LL * 16;
+  dim3 grid((unsigned)blocks, (unsigned)nrhs);
+  split_reduce_kernel<<<grid, 256, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
 void gemm_tile_dims(int tile, int* bm, int* bn) {
   static const int d[GT_COUNT][2] = {{64, 64}, {32, 64}, {64, 32}, {32, 32}, {16, 64},
                                      {64, 16}, {16, 16}, {8, 32},  {1, 256}, {256, 1}};
@@ -156,11 +228,12 @@ template <int BM, int BN, int TM, int TN>
 static cudaError_t launch_t(GemmArgs g, int nrhs, cudaStream_t st) {
   g.tiles_m = (g.M + BM - 1) / BM;
   g.tiles_n = (g.N + BN - 1) / BN;
-  long long nblk = (long long)g.tiles_m * g.tiles_n * g.nbatch;
+  if (g.nsplit < 1 || (g.nsplit > 1 && !g.part)) return cudaErrorInvalidValue;
+  long long nblk = (long long)g.tiles_m * g.tiles_n * g.nbatch * g.nsplit;
   if (nblk <= 0) return cudaSuccess;
   if (nblk > 2147483647LL || nrhs > 65535) return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)nblk, (unsigned)nrhs);
-  zgemm_seg_kernel<BM, BN, 8, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(g);
+  zgemm_seg_kernel<BM, BN, F64_BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(g);
   return cudaGetLastError();
 }
 

@@ -26,7 +26,7 @@ namespace {
 
 constexpr int TC_BM = 128;          // complex rows per tile
 constexpr int TC_BNC = 64;          // complex columns per tile
-constexpr int TC_BKC = 16;          // complex K per stage
+constexpr int TC_BKC = TC_BK;       // complex K per stage
 constexpr int TC_BKR = 2 * TC_BKC;  // real K per stage
 constexpr int TC_NR = 2 * TC_BNC;   // real accumulator columns
 constexpr int TC_THREADS = 128;
@@ -80,8 +80,11 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(GemmArgs g, int* er
 
   const int tpb = g.tiles_m * g.tiles_n;
   const int bid = blockIdx.x;
-  const int batch = bid / tpb;
-  const int t = bid - batch * tpb;
+  const int per_batch = tpb * g.nsplit;
+  const int batch = bid / per_batch;
+  const int rem = bid - batch * per_batch;
+  const int sp = rem / tpb;
+  const int t = rem - sp * tpb;
   const int m0 = (t / g.tiles_n) * TC_BM;
   const int n0 = (t % g.tiles_n) * TC_BNC;
   const long long rhs = blockIdx.y;
@@ -113,15 +116,20 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(GemmArgs g, int* er
   const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_NR >> 3) << 17) |
                          ((uint32_t)(TC_BM >> 4) << 24);
 
+  // (segment, K tile) iteration space of the batch entry, segment-major; this CTA takes
+  // its split's contiguous range
   const int s0 = g.sbeg[batch], s1 = g.sbeg[batch + 1];
   const int nkt = (K + TC_BKC - 1) / TC_BKC;
-  const int total = (s1 - s0) * nkt;
+  const long long all = (long long)(s1 - s0) * nkt;
+  const long long lo = all * sp / g.nsplit, hi = all * (sp + 1) / g.nsplit;
+  const int total = (int)(hi - lo);
   bool ok = true;
   int step = 0;
-  for (int s = s0; s < s1 && ok; ++s) {
+  int s = s0 + (int)(lo / nkt), kt = (int)(lo % nkt);
+  for (; step < total && ok; ++step) {
     const double2* Ap = Ab + g.aoff[s];
     const double2* Bp = Bb + g.boff[s];
-    for (int kt = 0; kt < nkt && ok; ++kt, ++step) {
+    {
       const int buf = step & 1;
       unsigned char* st = smem + buf * STAGE;
       if (step >= 2) {
@@ -218,6 +226,10 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(GemmArgs g, int* er
                      : "memory");
       }
     }
+    if (++kt == nkt) {
+      kt = 0;
+      ++s;
+    }
   }
   // wait for the last commit (it tracks every MMA issued before it)
   if (ok && total > 0) ok = mbar_wait(smem_u32(&mbar[(total - 1) & 1]), ((total - 1) >> 1) & 1);
@@ -227,10 +239,20 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(GemmArgs g, int* er
     if (step > 0) mbar_wait(smem_u32(&mbar[(step - 1) & 1]), ((step - 1) >> 1) & 1);
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok && g.nsplit > 1 && total == 0) {  // an empty split still owns its partial tile
+    const int m = m0 + tid;
+    if (m < M) {
+      double2* Pp = g.part + ((rhs * g.nbatch + batch) * g.nsplit + sp) * (long long)M * N + (long long)m * N;
+      for (int n = n0; n < n0 + TC_BNC && n < N; ++n) Pp[n] = make_double2(0.0, 0.0);
+    }
+  }
   if (ok && total > 0) {
     const int warp = tid >> 5, lane = tid & 31;
     const int m = m0 + warp * 32 + lane;
     double2* Cp = Cb + g.coff[batch];
+    double2* Pp = g.nsplit > 1
+                      ? g.part + ((rhs * g.nbatch + batch) * g.nsplit + sp) * (long long)M * N + (long long)m * N
+                      : nullptr;
 #pragma unroll 1
     for (int c0 = 0; c0 < TC_NR; c0 += 16) {
       uint32_t r[16];
@@ -247,6 +269,10 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(GemmArgs g, int* er
           const int n = n0 + c0 / 2 + j;
           if (n >= N) break;
           const double ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
+          if (Pp) {  // raw partial; alpha and the epilogue come in the reduction
+            Pp[n] = make_double2(ar, ai);
+            continue;
+          }
           const double vr = g.ar * ar - g.ai * ai, vi = g.ar * ai + g.ai * ar;
           if (g.epi == 0) {
             double2* cp = Cp + (long long)m * g.ldc + n;
@@ -278,7 +304,8 @@ cudaError_t launch_gemm_tc(const GemmArgs& g0, int prec, int nrhs, int* errflag,
   GemmArgs g = g0;
   g.tiles_m = (g.M + TC_BM - 1) / TC_BM;
   g.tiles_n = (g.N + TC_BNC - 1) / TC_BNC;
-  long long nblk = (long long)g.tiles_m * g.tiles_n * g.nbatch;
+  if (g.nsplit < 1 || (g.nsplit > 1 && !g.part)) return cudaErrorInvalidValue;
+  long long nblk = (long long)g.tiles_m * g.tiles_n * g.nbatch * g.nsplit;
   if (nblk <= 0) return cudaSuccess;
   if (nblk > 2147483647LL || nrhs > 65535) return cudaErrorInvalidConfiguration;
   const size_t sm = tc_smem_bytes(prec);

@@ -86,9 +86,11 @@ extern "C" lrcc_status lrcc_jacobian_apply_noalloc(lrcc_problem* p, int32_t tran
     return LRCC_ECUDA;
   double2* ar[lrcc::AR_COUNT] = {rt.fix, in, out, scr, rt.ws};
   const bool prof = rt.prof;
-  rt.prof = false;  // per-op event timing would create events
+  rt.prof = false;     // per-op event timing would create events
+  rt.no_split = true;  // split-K partials would need a buffer
   lrcc_status s = rt.run(transpose ? rt.jacT : P.jac, ar, 1, st);
   rt.prof = prof;
+  rt.no_split = false;
   if (s != LRCC_OK) return s;
   if (!rt.ck(cudaMemcpyAsync(y1, res + P.off_x1, b1, cudaMemcpyDeviceToDevice, st), "noalloc copy y1") ||
       !rt.ck(cudaMemcpyAsync(y2, res + P.off_x2, b2, cudaMemcpyDeviceToDevice, st), "noalloc copy y2"))

@@ -59,6 +59,9 @@ void Runtime::release() {
   if (packscr) cudaFree(packscr);
   packscr = nullptr;
   packscr_bytes = 0;
+  if (part) cudaFree(part);
+  part = nullptr;
+  part_bytes = 0;
   for (cudaEvent_t e : prof_pool) cudaEventDestroy(e);
   prof_pool.clear();
   for (void* p : {(void*)fix, (void*)in, (void*)out, (void*)scr, (void*)ws, (void*)desc, (void*)dip, (void*)l1,
@@ -122,6 +125,9 @@ lrcc_status Runtime::init(const lrcc_dims& d, int64_t ws_budget) {
     gdesc[i].boff = (const long long*)(p + (g.coff.size() + g.aoff.size()) * 8);
     gdesc[i].sbeg = (const int*)(p + (g.coff.size() + g.aoff.size() + g.boff.size()) * 8);
     gdesc[i].tile = gemm_pick_tile(g.M, g.N);
+    int ms = 1;
+    for (size_t b = 0; b + 1 < g.sbeg.size(); ++b) ms = std::max(ms, g.sbeg[b + 1] - g.sbeg[b]);
+    gdesc[i].max_seg = ms;
   }
   const int64_t nk = d.nk, n = d.nocc + d.nvir;
   if (!ck(cudaMalloc(&fix, plan.arena_size[AR_FIX] * sizeof(double2)), "cudaMalloc(fixed arena)")) return LRCC_ENOMEM;
@@ -135,6 +141,36 @@ lrcc_status Runtime::init(const lrcc_dims& d, int64_t ws_budget) {
 }
 
 bool Runtime::use_packed(const Gemm& g) const { return g.M >= 96 && g.N >= 96 && g.K >= 16; }
+
+// The unpacked tensor-core tile is 128 x 64 complex with K in steps of 16: below 15%
+// useful work per tile the FP64 kernel (small tiles) is used instead.
+static bool tc_tile_useful(const Gemm& g) {
+  const double tm = (double)((g.M + 127) / 128) * 128, tn = (double)((g.N + 63) / 64) * 64;
+  const double tk = (double)((g.K + 15) / 16) * 16;
+  return (double)g.M * g.N * g.K / (tm * tn * tk) >= 0.15;
+}
+
+// Split-K factor: enough CTAs to fill the 152 SMs a few times over when the output
+// tiles of one vector cannot, keeping at least 8 K iterations per split and the
+// partials of one vector under 64 MiB.  The choice does not depend on the number of
+// vectors, so a vector's result is bitwise the same in any batch.
+int Runtime::pick_split(const Gemm& g, const GemmDesc& d, int nr, bool tc) const {
+  (void)nr;
+  if (no_split) return 1;
+  int bm = 128, bn = 64;
+  if (!tc) gemm_tile_dims(d.tile, &bm, &bn);
+  const long long tiles = (long long)((g.M + bm - 1) / bm) * ((g.N + bn - 1) / bn) * g.nbatch();
+  const long long target = tc ? 152LL * 3 : 152LL * 6;
+  if (tiles >= target) return 1;
+  const int bk = tc ? TC_BK : F64_BK;
+  const long long iters = (long long)d.max_seg * ((g.K + bk - 1) / bk);
+  long long s = (target + tiles - 1) / tiles;
+  s = std::min<long long>(s, iters / 8);
+  s = std::min<long long>(s, 1024);
+  const long long per = (long long)g.nbatch() * g.M * g.N * (long long)sizeof(double2);
+  if (per > 0) s = std::min<long long>(s, (64LL << 20) / per);
+  return (int)std::max<long long>(s, 1);
+}
 
 static bool is_vec_arena(int ar) { return ar == AR_IN || ar == AR_OUT || ar == AR_SCR; }
 
@@ -319,8 +355,28 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
         lrcc_status ps = run_packed(op.idx, g, ar, nr, op.fixed_only != 0, stride, st, prec);
         if (ps != LRCC_OK) return ps;
       } else {
-        e = prec > 0 ? launch_gemm_tc(a, prec, nr, dflag, st) : launch_gemm_f64(a, d.tile, nr, st);
+        const bool tc = prec > 0 && tc_tile_useful(g);
+        a.nsplit = pick_split(g, d, nr, tc);
+        if (a.nsplit > 1) {
+          const size_t need = (size_t)nr * g.nbatch() * a.nsplit * g.M * g.N * sizeof(double2);
+          if (need > part_bytes) {
+            if (part) {
+              if (!ck(cudaStreamSynchronize(st), "split-K sync")) return LRCC_ECUDA;
+              cudaFree(part);
+              part = nullptr;
+              part_bytes = 0;
+            }
+            if (!ck(cudaMalloc(&part, need), "cudaMalloc(split-K partials)")) return LRCC_ENOMEM;
+            part_bytes = need;
+          }
+          a.part = part;
+        }
+        e = tc ? launch_gemm_tc(a, prec, nr, dflag, st) : launch_gemm_f64(a, d.tile, nr, st);
         ++launches;
+        if (e == cudaSuccess && a.nsplit > 1) {
+          e = launch_split_reduce(a, nr, st);
+          ++launches;
+        }
       }
     } else if (op.kind == OP_PERM) {
       const Perm& p = plan.perms[op.idx];
@@ -411,6 +467,7 @@ void lrcc_default_options(lrcc_options* o) {
   o->autotune = 0;
   o->use_graphs = 0;
   o->spin_timeout_cycles = 0;
+  o->response_form = 0;
 }
 
 lrcc_status lrcc_create(const lrcc_dims* dims, lrcc_problem** out) {

@@ -16,6 +16,7 @@ struct GemmDesc {
   const long long* aoff = nullptr;
   const long long* boff = nullptr;
   int tile = 0;
+  int max_seg = 1;  // most segments of any batch entry
 };
 
 // Packed-operand execution of one GEMM op on the tensor cores (mixed precision).
@@ -59,6 +60,11 @@ struct Runtime {
   unsigned char* packscr = nullptr;       // packed vector-dependent operands
   size_t packscr_bytes = 0;
   bool use_packed(const Gemm& g) const;
+  // split-K partials (grown on demand; never during a call that must not allocate)
+  double2* part = nullptr;
+  size_t part_bytes = 0;
+  bool no_split = false;
+  int pick_split(const Gemm& g, const GemmDesc& d, int nr, bool tc) const;
   lrcc_status run_packed(int gi, const Gemm& g, double2* const ar[AR_COUNT], int nr, bool fixed_only,
                          const long long* stride, cudaStream_t st, int prec);
   // prec: 0 FP64 kernels; 1 TF32 and 2 BF16x3 tensor-core GEMMs (FP32 accumulation)

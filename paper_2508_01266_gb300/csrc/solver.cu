@@ -105,6 +105,11 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
     rt.err = "polarizability: precision must be 0, 1 or 2";
     return LRCC_EINVAL;
   }
+  if (opt.response_form < 0 || opt.response_form > 2) {
+    rt.err = "polarizability: response_form must be 0, 1 or 2";
+    return LRCC_EINVAL;
+  }
+  const int form = opt.response_form;
   for (int c = 0; c < ncomp; ++c)
     if (comps[c] < 0 || comps[c] > 2) {
       rt.err = "polarizability: component index out of range";
@@ -177,6 +182,11 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
   double2* DOT = dev.get<double2>(rt, (size_t)maxpairs, ok);
   double2* COEF = dev.get<double2>(rt, (size_t)depth * ns, ok);
   const double2** PV = dev.get<const double2*>(rt, (size_t)depth, ok);
+  // left-response form: eta vectors, left right-hand sides and solutions, shifts -w
+  double2* ETA = form ? dev.get<double2>(rt, (size_t)ncomp * vec, ok) : nullptr;
+  double2* RHSL = form ? dev.get<double2>(rt, (size_t)ns * vec, ok) : nullptr;
+  double2* TBAR = form ? dev.get<double2>(rt, (size_t)ns * vec, ok) : nullptr;
+  double* OMN = form ? dev.get<double>(rt, (size_t)ns, ok) : nullptr;
   if (!ok) return LRCC_ENOMEM;
 #define CK(x, what) \
   do {              \
@@ -308,29 +318,29 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
       if (sys[i].c == c)
         CK(cudaMemcpy(XI + (size_t)i * vec, rt.out, vec * sizeof(double2), cudaMemcpyDeviceToDevice), "xi");
   }
-  std::vector<double> ximax;
-  if ((s = maxabs(XI, ns, ximax)) != LRCC_OK) return s;
-
-  // 2. batched solve -------------------------------------------------------------------
-  // Jacobi + DIIS on (A - w) x = -rhs for every system, iterate in rt.in; prec selects the
-  // GEMM arithmetic of the products.  Returns the relative residual reached in rel.
+  // 2. batched solves ------------------------------------------------------------------
+  // Jacobi + DIIS on (A - w) x = -rhs (tr = 0, iterate in rt.in) or (A^T - w) x = -rhs
+  // (tr = 1, transposed products, iterate in rt.out) for every system; prec selects the
+  // GEMM arithmetic of the products.  rel receives the relative residual reached.
   std::vector<double> rel(ns, 1.0);
   int total_it = 0;
-  auto jacobi_diis = [&](const double2* rhs, const std::vector<double>& rhsmax, int prec, double tol, int maxiter,
-                         bool& conv) -> lrcc_status {
+  auto jacobi_diis = [&](int tr, const double2* rhs, const std::vector<double>& rhsmax, const double* om, int prec,
+                         double tol, int maxiter, bool& conv) -> lrcc_status {
     lrcc_status s2;
-    CK(launch_guess(rhs, DEN, OM, rt.in, vec, vec, ns, st), "guess");
+    double2* X = tr ? rt.out : rt.in;
+    double2* Y = tr ? rt.in : rt.out;
+    CK(launch_guess(rhs, DEN, om, X, vec, vec, ns, st), "guess");
     rt.launches++;
     std::vector<std::vector<cd>> Bm(ns, std::vector<cd>(depth * depth, 0.0));
     int nhist = 0;
     conv = false;
     for (int it = 0; it < maxiter; ++it) {
       ++total_it;
-      if ((s2 = rt.apply(0, ns, st, prec)) != LRCC_OK) return s2;
+      if ((s2 = rt.apply(tr, ns, st, prec)) != LRCC_OK) return s2;
       const int slot = it % depth;
       CK(cudaMemsetAsync(RMAX, 0, ns * sizeof(unsigned long long), st), "memset");
-      CK(launch_update(rt.in, rt.out, rhs, DEN, OM, HE + (size_t)slot * ns * vec, HX + (size_t)slot * ns * vec, RMAX,
-                       vec, vec, ns, st),
+      CK(launch_update(X, Y, rhs, DEN, om, HE + (size_t)slot * ns * vec, HX + (size_t)slot * ns * vec, RMAX, vec, vec,
+                       ns, st),
          "update");
       rt.launches++;
       std::vector<unsigned long long> hr(ns);
@@ -390,31 +400,40 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
       for (int j = 0; j < nhist; ++j) pv[j] = HX + (size_t)slots[j] * ns * vec;
       CK(cudaMemcpy(PV, pv.data(), nhist * sizeof(void*), cudaMemcpyHostToDevice), "pv");
       CK(cudaMemcpy(COEF, coef.data(), coef.size() * sizeof(double2), cudaMemcpyHostToDevice), "coef");
-      CK(launch_lincomb(PV, COEF, nhist, rt.in, vec, vec, ns, st), "lincomb");
+      CK(launch_lincomb(PV, COEF, nhist, X, vec, vec, ns, st), "lincomb");
       rt.launches++;
     }
     return LRCC_OK;
   };
 
-  bool converged = false;
+  // Solve every system into sol: FP64 Jacobi + DIIS, or (mixed precision) iterative
+  // refinement: FP64 residual r = -rhs - (A - w) x, tensor-core inner solve of
+  // (A - w) d = r to a loose tolerance, x += d, until max|r| / max|rhs| <= refine_tol.
+  // FU serves as the residual buffer.
   const int prec = opt.precision;
-  if (prec == 0) {
-    if ((s = jacobi_diis(XI, ximax, 0, opt.conv_tol, maxit, converged)) != LRCC_OK) return s;
-    CK(cudaMemcpy(SOL, rt.in, (size_t)ns * vec * sizeof(double2), cudaMemcpyDeviceToDevice), "sol");
-  } else {
-    // iterative refinement: FP64 residual r = -xi - (A - w) x, tensor-core inner solve of
-    // (A - w) d = r to a loose tolerance, x += d, until max|r| / max|xi| <= refine_tol.
-    CK(launch_guess(XI, DEN, OM, SOL, vec, vec, ns, st), "guess");
+  auto solve = [&](int tr, const double2* rhs, const double* om, double2* sol, bool& converged) -> lrcc_status {
+    lrcc_status s2;
+    double2* X = tr ? rt.out : rt.in;
+    double2* Y = tr ? rt.in : rt.out;
+    std::vector<double> rhsmax;
+    if ((s2 = maxabs(rhs, ns, rhsmax)) != LRCC_OK) return s2;
+    converged = false;
+    if (prec == 0) {
+      if ((s2 = jacobi_diis(tr, rhs, rhsmax, om, 0, opt.conv_tol, maxit, converged)) != LRCC_OK) return s2;
+      CK(cudaMemcpy(sol, X, (size_t)ns * vec * sizeof(double2), cudaMemcpyDeviceToDevice), "sol");
+      return LRCC_OK;
+    }
+    CK(launch_guess(rhs, DEN, om, sol, vec, vec, ns, st), "guess");
     rt.launches++;
     const double tol64 = std::min(opt.refine_tol, 1e-3);
     const double inner_tol = prec == 1 ? 3e-3 : 1e-4;
     for (int outer = 0; outer < 40 && !converged; ++outer) {
-      CK(cudaMemcpy(rt.in, SOL, (size_t)ns * vec * sizeof(double2), cudaMemcpyDeviceToDevice), "x -> in");
-      if ((s = rt.apply(0, ns, st, 0)) != LRCC_OK) return s;
+      CK(cudaMemcpy(X, sol, (size_t)ns * vec * sizeof(double2), cudaMemcpyDeviceToDevice), "x -> in");
+      if ((s2 = rt.apply(tr, ns, st, 0)) != LRCC_OK) return s2;
       ++total_it;
-      // R = xi + A x - w x = -r ; its max is the FP64 residual
+      // R = rhs + A x - w x = -r ; its max is the FP64 residual
       CK(cudaMemsetAsync(RMAX, 0, ns * sizeof(unsigned long long), st), "memset");
-      CK(launch_residual(rt.in, rt.out, XI, OM, FU, RMAX, vec, vec, ns, st), "residual");
+      CK(launch_residual(X, Y, rhs, om, FU, RMAX, vec, vec, ns, st), "residual");
       rt.launches++;
       std::vector<unsigned long long> hr(ns);
       CK(cudaMemcpy(hr.data(), RMAX, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "rmax");
@@ -422,7 +441,7 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
       std::vector<double> rmx(ns);
       for (int i = 0; i < ns; ++i) {
         rmx[i] = u64_to_double(hr[i]);
-        rel[i] = rmx[i] / std::max(ximax[i], 1e-300);
+        rel[i] = rmx[i] / std::max(rhsmax[i], 1e-300);
         worst = std::max(worst, rel[i]);
       }
       if (worst <= tol64) {
@@ -430,15 +449,19 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
         break;
       }
       bool inner_conv = false;
-      if ((s = jacobi_diis(FU, rmx, prec, inner_tol, maxit, inner_conv)) != LRCC_OK) return s;
+      if ((s2 = jacobi_diis(tr, FU, rmx, om, prec, inner_tol, maxit, inner_conv)) != LRCC_OK) return s2;
       for (int i = 0; i < ns; ++i) {
-        CK(launch_axpby(make_double2(1.0, 0.0), rt.in + (size_t)i * vec, make_double2(1.0, 0.0), SOL + (size_t)i * vec,
+        CK(launch_axpby(make_double2(1.0, 0.0), X + (size_t)i * vec, make_double2(1.0, 0.0), sol + (size_t)i * vec,
                         vec, st),
            "x += d");
         rt.launches++;
       }
     }
-  }
+    return LRCC_OK;
+  };
+
+  bool converged = false;
+  if ((s = solve(0, XI, OM, SOL, converged)) != LRCC_OK) return s;
   if (info) {
     info[0] = total_it;
     info[1] = converged ? 0 : LRCC_ENOCONV;
@@ -527,17 +550,110 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
   CK(cudaDeviceSynchronize(), "solver sync");
 
   // 3c. response function ------------------------------------------------------------------
-  for (int iw = 0; iw < nomega; ++iw)
-    for (int x = 0; x < ncomp; ++x)
-      for (int y = 0; y < ncomp; ++y) {
-        if (!active[x] || !active[y]) continue;
-        const int xp = sidx[x][2 * iw], xm = sidx[x][2 * iw + 1];
-        const int yp = sidx[y][2 * iw], ym = sidx[y][2 * iw + 1];
-        const cd a = etaw[x][yp] + etaw[y][xm] + F[(size_t)xm * ns + yp];
-        const cd b = etaw[x][ym] + etaw[y][xp] + F[(size_t)xp * ns + ym];
-        const cd lr = 0.5 * (a + std::conj(b));
-        alpha[((size_t)iw * ncomp + x) * ncomp + y] = -lr / (double)nk;
+  if (form == 0) {
+    for (int iw = 0; iw < nomega; ++iw)
+      for (int x = 0; x < ncomp; ++x)
+        for (int y = 0; y < ncomp; ++y) {
+          if (!active[x] || !active[y]) continue;
+          const int xp = sidx[x][2 * iw], xm = sidx[x][2 * iw + 1];
+          const int yp = sidx[y][2 * iw], ym = sidx[y][2 * iw + 1];
+          const cd a = etaw[x][yp] + etaw[y][xm] + F[(size_t)xm * ns + yp];
+          const cd b = etaw[x][ym] + etaw[y][xp] + F[(size_t)xp * ns + ym];
+          const cd lr = 0.5 * (a + std::conj(b));
+          alpha[((size_t)iw * ncomp + x) * ncomp + y] = -lr / (double)nk;
+        }
+    return LRCC_OK;
+  }
+
+  // 4. asymmetric (left-response) form -------------------------------------------------------
+  // 4a. eta^X as vectors: the Jacobian is linear in the one-body operator, so
+  //     (A^X)^T lam = [A(f + mu)^T lam - A(f - mu)^T lam] / 2 exactly; plus dE^X/dt = 2 mu_ia.
+  {
+    std::vector<double2> f0h((size_t)nk * n * n);
+    CK(cudaMemcpy(f0h.data(), rt.fix + P.off_f0, f0h.size() * sizeof(double2), cudaMemcpyDeviceToHost), "f0");
+    std::vector<double2> fm(f0h.size());
+    for (int c = 0; c < ncomp; ++c) {
+      if (!active[c]) continue;
+      const double2* mu = rt.dip_host.data() + (size_t)comps[c] * nk * n * n;
+      double2* E = ETA + (size_t)c * vec;
+      for (int sg = 1; sg >= -1; sg -= 2) {
+        for (size_t i = 0; i < fm.size(); ++i)
+          fm[i] = make_double2(f0h[i].x + sg * mu[i].x, f0h[i].y + sg * mu[i].y);
+        CK(cudaMemcpy(rt.fix + P.off_f0, fm.data(), fm.size() * sizeof(double2), cudaMemcpyHostToDevice), "f0 +- mu");
+        if ((s = rebuild_ground(0)) != LRCC_OK) return s;
+        CK(cudaMemcpy(rt.out, LAM, vec * sizeof(double2), cudaMemcpyDeviceToDevice), "lam -> out");
+        if ((s = rt.apply(1, 1, st, 0)) != LRCC_OK) return s;
+        if (sg > 0) {
+          CK(cudaMemcpy(E, rt.in, vec * sizeof(double2), cudaMemcpyDeviceToDevice), "eta +");
+        } else {
+          CK(launch_axpby(make_double2(-0.5, 0.0), rt.in, make_double2(0.5, 0.0), E, vec, st), "eta -");
+          rt.launches++;
+        }
       }
+      if ((s = set_mu(comps[c])) != LRCC_OK) return s;
+      CK(launch_axpby(make_double2(2.0, 0.0), rt.fix + P.off_mu + (size_t)nk * o * o, make_double2(1.0, 0.0),
+                      E + P.off_x1, (long long)n1, st),
+         "eta 2 mu");
+      rt.launches++;
+    }
+    CK(cudaMemcpy(rt.fix + P.off_f0, f0h.data(), f0h.size() * sizeof(double2), cudaMemcpyHostToDevice), "f0");
+    if ((s = rebuild_ground(0)) != LRCC_OK) return s;
+  }
+  // 4b. left perturbed multipliers: (A^T + w_s) tbar_s = -(eta^X + F t^X(w_s)) for every system
+  {
+    std::vector<double> omn(ns);
+    for (int i = 0; i < ns; ++i) omn[i] = -sys[i].w;
+    CK(cudaMemcpy(OMN, omn.data(), ns * sizeof(double), cudaMemcpyHostToDevice), "-omega");
+    for (int i = 0; i < ns; ++i) {
+      CK(cudaMemcpy(RHSL + (size_t)i * vec, ETA + (size_t)sys[i].c * vec, vec * sizeof(double2),
+                    cudaMemcpyDeviceToDevice),
+         "eta -> rhs");
+      CK(launch_axpby(make_double2(1.0, 0.0), FU + (size_t)i * vec, make_double2(1.0, 0.0), RHSL + (size_t)i * vec,
+                      vec, st),
+         "rhs += F t");
+      rt.launches++;
+    }
+    bool lconv = false;
+    if ((s = solve(1, RHSL, OMN, TBAR, lconv)) != LRCC_OK) return s;
+    if (info) {
+      info[0] = total_it;
+      info[1] = lconv ? 0 : LRCC_ENOCONV;
+    }
+    if (!lconv) {
+      rt.err = "polarizability: left response equations did not converge";
+      return LRCC_ENOCONV;
+    }
+  }
+  // 4c. <<X;Y>>_w = 1/2 C^{+-w} [eta^Y t^X(-w) + tbar^X(-w) xi^Y]
+  {
+    std::vector<int> xi_of(ncomp, -1);
+    for (int c = 0; c < ncomp; ++c)
+      if (active[c]) xi_of[c] = sidx[c][0];
+    std::vector<const double2*> qa, qb;
+    for (int i = 0; i < ns; ++i)
+      for (int c = 0; c < ncomp; ++c) {
+        qa.push_back(TBAR + (size_t)i * vec);
+        qb.push_back(XI + (size_t)std::max(xi_of[c], 0) * vec);
+      }
+    std::vector<cd> TX;
+    if ((s = dots(qa, qb, 0, vec, TX)) != LRCC_OK) return s;
+    std::vector<cd> asym((size_t)nomega * ncomp * ncomp, 0.0);
+    for (int iw = 0; iw < nomega; ++iw)
+      for (int x = 0; x < ncomp; ++x)
+        for (int y = 0; y < ncomp; ++y) {
+          if (!active[x] || !active[y]) continue;
+          const int xp = sidx[x][2 * iw], xm = sidx[x][2 * iw + 1];
+          const cd a = etaw[y][xm] + TX[(size_t)xm * ncomp + y];
+          const cd b = etaw[y][xp] + TX[(size_t)xp * ncomp + y];
+          asym[((size_t)iw * ncomp + x) * ncomp + y] = -0.5 * (a + std::conj(b)) / (double)nk;
+        }
+    for (int iw = 0; iw < nomega; ++iw)
+      for (int x = 0; x < ncomp; ++x)
+        for (int y = 0; y < ncomp; ++y) {
+          const size_t i = ((size_t)iw * ncomp + x) * ncomp + y, j = ((size_t)iw * ncomp + y) * ncomp + x;
+          alpha[i] = form == 1 ? 0.5 * (asym[i] + asym[j]) : asym[i];
+        }
+  }
 #undef CK
   return LRCC_OK;
 }

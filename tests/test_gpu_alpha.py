@@ -106,3 +106,39 @@ def test_alpha_mixed_precision_c1(lr, c1_ref, prec):
     print(f"C1 alpha_zz prec {prec}: {got.ravel()} oracle {ref.ravel()} |err| {err:.2e} iterations {info[0]}")
     assert info[1] == 0
     assert err <= 1e-5
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_left_response_alpha_vs_oracle(lr, form):
+    """Asymmetric (left-response) alpha on the GPU vs the oracle's asymmetric form
+    (form 2, as computed) and its symmetrisation (form 1); non-TR data so that the
+    two differ."""
+    p = make_problem(2, 2, 3, 4, seed=7, sigma_l=0.15, tr=False)
+    nk, o, v, Q = p.nk, p.nocc, p.nvir, p.naux
+    R = rcc.RCC(p)
+    t1, t2, _ = rcc.solve_ccsd(R, tol=1e-11)
+    l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=1e-11)
+    comps, omegas = [0, 2], [0.0, 0.06]
+    sym, asym = rcc.polarizability_left(R, t1, t2, l1, l2, rcc.dipole_ops(p, comps), omegas, tol=1e-11)
+    ref = sym if form == 1 else asym
+    pl1, pl2 = paper_lambda(nk, l1, l2)
+    prob = lr.Problem(nk, o, v, Q)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    prob.set_ground_state(t1, t2 * nk, pl1, pl2)
+    got, info = prob.polarizability(comps, omegas, lr.default_options(conv_tol=1e-11, max_iter=300,
+                                                                      response_form=form))
+    sym_gpu, _ = prob.polarizability(comps, omegas, lr.default_options(conv_tol=1e-11, max_iter=300))
+    prob.close()
+    assert info[1] == 0
+    assert np.abs(got - ref).max() < 1e-8 * np.abs(ref).max()
+    if form == 2:  # at convergence the asymmetric form equals the symmetric one element by element
+        assert np.abs(got - sym_gpu).max() < 1e-8 * np.abs(sym_gpu).max()
+
+
+def test_left_response_alpha_mixed_c1(lr, c1_ref):
+    """Left-response form with tensor-core inner solves: within 1e-5 a.u. of the oracle."""
+    got, ref, info = _c1_gpu(lr, c1_ref, lr.default_options(precision=2, refine_tol=1e-8, response_form=1))
+    err = np.abs(got - ref).max()
+    print(f"C1 left-response alpha_zz BF16x3: {got.ravel()} oracle {ref.ravel()} |err| {err:.2e}")
+    assert info[1] == 0
+    assert err <= 1e-5
