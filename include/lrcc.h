@@ -61,8 +61,9 @@ typedef struct {
   int32_t diis_depth;  /* default 8 */
   int32_t diis_period; /* extrapolate every n iterations (default 1) */
   int32_t precision;   /* 0 FP64, 1 TF32, 2 BF16x3 (split bf16, FP32 accumulate) */
-  int32_t autotune;
-  int32_t use_graphs;
+  int32_t autotune;    /* 1: time the candidate GEMM tilings of each op once per problem and keep the fastest */
+  int32_t use_graphs;  /* 1: replay each product (per direction, batch size, precision) as a CUDA graph;
+                          the first call per key runs eagerly and captures the graph */
   uint64_t spin_timeout_cycles;
   int32_t response_form; /* lrcc_polarizability: 0 symmetric form (default); 1 asymmetric
                             (left-response) form, symmetrised (alpha_XY + alpha_YX) / 2;
@@ -137,6 +138,35 @@ lrcc_status lrcc_jacobian_apply_noalloc(lrcc_problem* p, int32_t transpose, cons
 lrcc_status lrcc_polarizability(lrcc_problem* p, const int32_t* comps, int32_t ncomp, const double* omegas,
                                 int32_t nomega, const lrcc_options* opt, void* alpha, int32_t* info);
 
+/* CCSD residual Omega(t) (Eqs. 7-8, paper units, layouts as for set_ground_state) for the
+ * amplitudes t1, t2 (device pointers), into r1, r2 (device).  Evaluated from Jacobian
+ * products: Omega(t) = Omega(0) + 1/2 [A(s1 t) t + A(s2 t) t], s1,2 = (1 -+ 1/sqrt 3)/2,
+ * exact because Omega is a polynomial of degree 4.  Requires set_integrals; the
+ * problem's ground state (if set) is restored afterwards.  Synchronous. */
+lrcc_status lrcc_residual(lrcc_problem* p, const void* t1, const void* t2, void* r1, void* r2);
+
+/* Ground state on the GPU: CCSD amplitudes (Jacobi + DIIS on the residual above, until
+ * max |Omega| <= opt->conv_tol) and the Lambda multipliers of Eqs. 10-11 (transpose
+ * products, relative residual <= opt->conv_tol), both in FP64.  On success they become
+ * the problem's ground state (as set_ground_state with Lambda) and are also copied to
+ * t1, t2, l1, l2 (each may be NULL; device memory when on_device, else host) in the
+ * paper's normalization.  energy (may be NULL): CCSD correlation energy per cell.
+ * info (may be NULL): int32 [4] = CCSD iterations, CCSD status, Lambda iterations,
+ * Lambda status.  Requires set_integrals.  Synchronous. */
+lrcc_status lrcc_solve_ground_state(lrcc_problem* p, const lrcc_options* opt, void* t1, void* t2, void* l1,
+                                    void* l2, int32_t on_device, double* energy, int32_t* info);
+
+/* Polarizabilities of several independent problems (for example chains of different
+ * Nk, o, v) in one call, all with the same components, frequencies and options.  Each
+ * problem's solve runs on its own host thread and that thread's default stream, so
+ * the problems' kernels share the GPU.  alphas[i] and infos[i] are as for
+ * lrcc_polarizability (infos, or any entry of it, may be NULL).  The problems must be
+ * distinct handles on the calling thread's current device.  Every problem is
+ * attempted; returns the first non-OK status in problem order.  Synchronous. */
+lrcc_status lrcc_batch_polarizability(lrcc_problem* const* probs, int32_t nprob, const int32_t* comps,
+                                      int32_t ncomp, const double* omegas, int32_t nomega,
+                                      const lrcc_options* opt, void* const* alphas, int32_t* const* infos);
+
 /* Last error message of a problem (static storage owned by the handle). */
 const char* lrcc_last_error(const lrcc_problem* p);
 
@@ -171,7 +201,8 @@ lrcc_status lrcc_profile_report(lrcc_problem* p, char* buf, int64_t len);
  * arenas (0 fixed data, 1 input vector, 2 output vector, 3 per-vector scratch,
  * 4 W-block workspace).  These calls expose that list so its index arithmetic can
  * be checked on a CPU.  which: 0 ground-state program, 1 Jacobian, 2 transposed
- * Jacobian, 3 perturbation right-hand side (Eq. 12), 4 energy second derivative.
+ * Jacobian, 3 perturbation right-hand side (Eq. 12), 4 energy second derivative,
+ * 5 residual at zero amplitudes, 6 energy gradient with respect to the amplitudes.
  * ------------------------------------------------------------------------- */
 lrcc_status lrcc_plan_create(const lrcc_dims* dims, int64_t ws_budget, lrcc_plan** out);
 void lrcc_plan_destroy(lrcc_plan* h);

@@ -15,7 +15,7 @@ from ._lib import lib, lrcc_dims, lrcc_options, STATUS, LIB_PATH
 
 __all__ = ["LrccError", "Problem", "default_options", "create", "set_integrals", "set_ground_state",
            "jacobian_apply", "polarizability", "last_error", "destroy", "kernel_launches", "profile",
-           "profile_query", "profile_report", "LRCCJacobian", "jacobian", "LIB_PATH"]
+           "profile_query", "profile_report", "batch_polarizability", "residual", "solve_ground_state", "LRCCJacobian", "jacobian", "LIB_PATH"]
 
 
 class LrccError(RuntimeError):
@@ -140,6 +140,50 @@ def polarizability(h, comps, omegas, options=None):
     return out, info
 
 
+def residual(h, t1: torch.Tensor, t2: torch.Tensor):
+    """CCSD residual Omega(t) (paper units) of CUDA complex128 amplitudes t1, t2."""
+    t1 = t1.contiguous()
+    t2 = t2.contiguous()
+    r1, r2 = torch.empty_like(t1), torch.empty_like(t2)
+    _check(lib.lrcc_residual(h, _ptr(t1), _ptr(t2), _ptr(r1), _ptr(r2)), h)
+    return r1, r2
+
+
+def solve_ground_state(h, nk, nocc, nvir, options=None):
+    """CCSD T and Lambda on the GPU; returns (t1, t2, l1, l2, energy_per_cell, info) with
+    CUDA tensors in the paper's normalization.  They become the problem's ground state."""
+    dev = torch.device("cuda")
+    t1 = torch.empty((nk, nocc, nvir), dtype=torch.complex128, device=dev)
+    t2 = torch.empty((nk, nk, nk, nocc, nocc, nvir, nvir), dtype=torch.complex128, device=dev)
+    l1, l2 = torch.empty_like(t1), torch.empty_like(t2)
+    e = C.c_double()
+    info = np.zeros(4, dtype=np.int32)
+    opt = options if options is not None else default_options()
+    _check(lib.lrcc_solve_ground_state(h, C.byref(opt), _ptr(t1), _ptr(t2), _ptr(l1), _ptr(l2), 1, C.byref(e),
+                                       info.ctypes.data_as(C.POINTER(C.c_int32))), h)
+    return t1, t2, l1, l2, e.value, info
+
+
+def batch_polarizability(problems, comps, omegas, options=None):
+    """alpha for several independent problems in one call (one host thread and stream
+    each); returns a list of (alpha, info) in the order of `problems`."""
+    comps = np.ascontiguousarray(comps, dtype=np.int32)
+    om = np.ascontiguousarray(omegas, dtype=np.float64)
+    n = len(problems)
+    outs = [np.zeros((len(om), len(comps), len(comps)), dtype=np.complex128) for _ in range(n)]
+    infos = [np.zeros(2 + len(comps), dtype=np.int32) for _ in range(n)]
+    hs = (C.c_void_p * n)(*[pr.h if isinstance(pr, Problem) else pr for pr in problems])
+    ap = (C.c_void_p * n)(*[o.ctypes.data for o in outs])
+    ip = (C.c_void_p * n)(*[i.ctypes.data for i in infos])
+    opt = options if options is not None else default_options()
+    st = lib.lrcc_batch_polarizability(hs, n, comps.ctypes.data_as(C.POINTER(C.c_int32)), len(comps),
+                                       om.ctypes.data_as(C.POINTER(C.c_double)), len(om), C.byref(opt), ap, ip)
+    if st != 0:
+        msgs = "; ".join((lib.lrcc_last_error(h) or b"").decode() for h in hs)
+        raise LrccError(st, msgs)
+    return list(zip(outs, infos))
+
+
 class Problem:
     """Owning wrapper around an lrcc_problem handle."""
 
@@ -158,6 +202,12 @@ class Problem:
 
     def polarizability(self, comps, omegas, options=None):
         return polarizability(self.h, comps, omegas, options)
+
+    def residual(self, t1, t2):
+        return residual(self.h, t1, t2)
+
+    def solve_ground_state(self, options=None):
+        return solve_ground_state(self.h, self.nk, self.nocc, self.nvir, options)
 
     def profile(self, enable=True):
         profile(self.h, enable)

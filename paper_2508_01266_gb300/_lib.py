@@ -46,6 +46,12 @@ _SIGS = {
     "lrcc_profile_query": (C.c_int, [VP, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_double)]),
     "lrcc_profile_report": (C.c_int, [VP, C.c_char_p, C.c_int64]),
+    "lrcc_residual": (C.c_int, [VP, VP, VP, VP, VP]),
+    "lrcc_solve_ground_state": (C.c_int, [VP, C.POINTER(lrcc_options), VP, VP, VP, VP, C.c_int32,
+                                          C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "lrcc_batch_polarizability": (C.c_int, [C.POINTER(VP), C.c_int32, C.POINTER(C.c_int32), C.c_int32,
+                                            C.POINTER(C.c_double), C.c_int32, C.POINTER(lrcc_options),
+                                            C.POINTER(VP), C.POINTER(VP)]),
     "lrcc_plan_create": (C.c_int, [C.POINTER(lrcc_dims), C.c_int64, C.POINTER(VP)]),
     "lrcc_plan_destroy": (None, [VP]),
     "lrcc_plan_info": (C.c_int, [VP, VP, VP, VP]),

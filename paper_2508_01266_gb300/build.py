@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "liblrcc.so")
-SOURCES = ["plan.cpp", "plan_api.cpp", "kernels_f64.cu", "runtime.cu", "solver.cu", "solver_kernels.cu", "kernels_tc.cu", "noalloc.cu", "kernels_tcp.cu"]
+SOURCES = ["plan.cpp", "plan_api.cpp", "kernels_f64.cu", "runtime.cu", "solver.cu", "solver_kernels.cu", "kernels_tc.cu", "noalloc.cu", "kernels_tcp.cu", "ground.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 
@@ -43,7 +43,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def comp(src):
         obj = os.path.join(BUILD, src + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        # per-thread default streams: the solvers of a batch of problems run on their own
+        # host threads without serialising on the legacy default stream
+        cmd = [nvcc, *ARCH, *FLAGS, "--default-stream", "per-thread", "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cpp"):
             cmd = [nvcc, *FLAGS, "-x", "c++", "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -56,7 +58,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(comp, SOURCES))
     tmp = LIB + ".tmp"
-    r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)
+    r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

@@ -311,18 +311,14 @@ cudaError_t launch_gemm_tc(const GemmArgs& g0, int prec, int nrhs, int* errflag,
   const size_t sm = tc_smem_bytes(prec);
   dim3 grid((unsigned)nblk, (unsigned)nrhs);
   if (prec == 1) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      attr = true;
-    }
+    static const cudaError_t attr =  // thread-safe one-time setup
+        cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (attr != cudaSuccess) return attr;
     tc_gemm_kernel<1><<<grid, TC_THREADS, sm, st>>>(g, errflag);
   } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(tc_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      attr = true;
-    }
+    static const cudaError_t attr =  // thread-safe one-time setup
+        cudaFuncSetAttribute(tc_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (attr != cudaSuccess) return attr;
     tc_gemm_kernel<2><<<grid, TC_THREADS, sm, st>>>(g, errflag);
   }
   return cudaGetLastError();

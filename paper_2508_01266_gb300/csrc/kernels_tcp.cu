@@ -358,18 +358,14 @@ cudaError_t launch_gemm_tcp(const PGemmArgs& g0, int prec, int nrhs, int* errfla
   const size_t sm = tcp_smem_bytes();
   dim3 grid((unsigned)nblk, (unsigned)nrhs);
   if (prec == 1) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(tcp_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      attr = true;
-    }
+    static const cudaError_t attr =  // thread-safe one-time setup
+        cudaFuncSetAttribute(tcp_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (attr != cudaSuccess) return attr;
     tcp_gemm_kernel<1><<<grid, P_THREADS, sm, st>>>(g, errflag);
   } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(tcp_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      attr = true;
-    }
+    static const cudaError_t attr =  // thread-safe one-time setup
+        cudaFuncSetAttribute(tcp_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (attr != cudaSuccess) return attr;
     tcp_gemm_kernel<2><<<grid, P_THREADS, sm, st>>>(g, errflag);
   }
   return cudaGetLastError();

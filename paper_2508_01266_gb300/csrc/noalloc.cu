@@ -68,7 +68,9 @@ extern "C" lrcc_status lrcc_jacobian_apply_noalloc(lrcc_problem* p, int32_t tran
     }
     base = g_noalloc_ptr[dev];
   }
-  cudaStream_t st = (cudaStream_t)stream;
+  // a null handle is the caller's legacy default stream (this library is built with
+  // per-thread default streams, under which 0 would name the calling thread's stream)
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamLegacy;
   double2* in = base;
   double2* out = base + vin;
   double2* scr = base + 2 * vin;

@@ -1120,7 +1120,38 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
     b.btr(E, nk, v, o, AR_OUT, Y1(0), AR_SCR, tmp, 1.0, "egrad -> y1");
   }
 
-  pack_scratch(P, {&P.jac, &P.xi, &P.egrad});
+  // omega0 program: the residual at t = 0 in paper units.  Doubles: <ab|ij> of the
+  // alpha-beta block, (ai|bj) summed over the undressed DF factors (times Nk for paper
+  // units; pair-symmetric by construction); singles: f_ai = 0 for the canonical Fock
+  // matrix the boundary takes.  With it Omega(t) = Omega(0) + 1/2 [A(s1 t) t + A(s2 t) t],
+  // s1,2 = (1 -+ 1/sqrt 3) / 2: two-point Gauss-Legendre of d/ds Omega(s t) = A(s t) t,
+  // exact because that is a cubic polynomial in s (Omega has degree 4, Eqs. 7-8).
+  {
+    Program& O = P.omega0;
+    T4 I0 = b.t4(AR_SCR, LK_CH, v, v, o, o);  // logical (a,b,i,j) = (ai|bj)
+    chem(O, I0, P.off_Lvo, v, o, P.off_Lvo, v, o, AR_FIX, AR_FIX, 1.0, "(ai|bj)");
+    b.perm(O, yout, I0, {2, 3, 0, 1}, sNk, 0.0, "(ai|bj) -> y2");
+  }
+  // tgrad program: dE/dt for the supercell energy E = sum (2(ia|jb) - (ib|ja)) (t_ij^ab +
+  // t_i^a t_j^b) (Eq. 6; f_ia = 0), with respect to the paper-unit amplitudes (t2 = Nk s2):
+  // singles 2 sum_jb L_iajb t_jb, doubles L_iajb / Nk.  With it the Lambda equations
+  // (Eqs. 10-11) read A^T lam = -dE/dt in the plain pairing.
+  {
+    Program& E = P.tgrad;
+    b.nonlinear = true;
+    int64_t tmp = b.alloc(AR_SCR, nk * ov);
+    Gemm& g = b.g_new((int)(nk * ov), 1, (int)(nk * ov), 0, 0, nk * ov, 1, 1, AR_FIX, AR_IN, AR_SCR, 2.0, 0.0,
+                      "tgrad 1");
+    B::batch(g, tmp);
+    B::seg(g, MLph.off, P.off_x1);
+    b.g_push(E);
+    b.btr(E, nk, v, o, AR_OUT, Y1(0), AR_SCR, tmp, 1.0, "tgrad 1 -> y1");
+    b.perm(E, yout, Vk3, {0, 1, 2, 3}, 2.0 / sNk, 0.0, "tgrad 2 a");
+    b.perm(E, yout, Vk3, {0, 1, 3, 2}, -1.0 / sNk, 0.0, "tgrad 2 b");
+    b.nonlinear = false;
+  }
+
+  pack_scratch(P, {&P.jac, &P.xi, &P.egrad, &P.omega0, &P.tgrad});
 
   double tot = 0;
   for (const Op& op : J.ops)

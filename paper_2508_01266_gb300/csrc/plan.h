@@ -111,6 +111,8 @@ struct Plan {
   Program jac;       // linear in IN -> OUT (uses SCR, WS)
   Program xi;        // perturbation right-hand side xi^X(t', mu): IN = t' (paper units) -> OUT
   Program egrad;     // IN x1 -> OUT y1 += 2 L x1 (energy second derivative, singles)
+  Program omega0;    // OUT = Omega(t = 0) (paper units): doubles (ai|bj), singles f_ai = 0 (canonical)
+  Program tgrad;     // IN = t (paper units) -> OUT = dE/dt (paper units, plain pairing)
   // named offsets of the FIX inputs
   int64_t off_Loo = 0, off_Lov = 0, off_Lvo = 0, off_Lvv = 0, off_f0 = 0,
           off_t1 = 0, off_t2 = 0, off_idv = 0, off_derived = 0;

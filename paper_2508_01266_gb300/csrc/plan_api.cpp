@@ -22,7 +22,9 @@ static const Program& prog_of(const lrcc_plan* h, int which) {
     case 1: return h->P.jac;
     case 2: return h->jacT;
     case 3: return h->P.xi;
-    default: return h->P.egrad;
+    case 4: return h->P.egrad;
+    case 5: return h->P.omega0;
+    default: return h->P.tgrad;
   }
 }
 
@@ -67,21 +69,21 @@ lrcc_status lrcc_plan_info(const lrcc_plan* h, int64_t* arena_sizes, int64_t* of
 }
 
 int32_t lrcc_plan_num_ops(const lrcc_plan* h, int32_t which) {
-  if (!h || which < 0 || which > 4) return -1;
+  if (!h || which < 0 || which > 6) return -1;
   return (int32_t)prog_of(h, which).ops.size();
 }
 
 lrcc_status lrcc_plan_validate(const lrcc_plan* h, char* msg, int32_t len) {
   if (!h || !msg || len < 1) return LRCC_EINVAL;
   std::string e;
-  for (int w = 0; w < 5 && e.empty(); ++w) e = validate_plan(h->P, prog_of(h, w));
+  for (int w = 0; w < 7 && e.empty(); ++w) e = validate_plan(h->P, prog_of(h, w));
   std::strncpy(msg, e.c_str(), (size_t)len - 1);
   msg[len - 1] = 0;
   return e.empty() ? LRCC_OK : LRCC_EINVAL;
 }
 
 lrcc_status lrcc_plan_op(const lrcc_plan* h, int32_t which, int32_t i, int32_t* kind_idx_fixed) {
-  if (!h || which < 0 || which > 4 || !kind_idx_fixed) return LRCC_EINVAL;
+  if (!h || which < 0 || which > 6 || !kind_idx_fixed) return LRCC_EINVAL;
   const Program& pr = prog_of(h, which);
   if (i < 0 || i >= (int32_t)pr.ops.size()) return LRCC_EINVAL;
   kind_idx_fixed[0] = pr.ops[i].kind;

@@ -7,6 +7,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -59,6 +60,7 @@ void Runtime::release() {
   if (packscr) cudaFree(packscr);
   packscr = nullptr;
   packscr_bytes = 0;
+  drop_graphs();
   if (part) cudaFree(part);
   part = nullptr;
   part_bytes = 0;
@@ -308,6 +310,123 @@ lrcc_status Runtime::ensure_rhs(int nrhs) {
   return LRCC_OK;
 }
 
+GemmChoice Runtime::default_choice(const Gemm& g, const GemmDesc& d, int prec) const {
+  GemmChoice c;
+  c.tc = prec > 0 && tc_tile_useful(g);
+  c.tile = d.tile;
+  c.nsplit = pick_split(g, d, 1, c.tc);
+  return c;
+}
+
+// One unpacked GEMM op with an explicit kernel choice (tile of the FP64 kernel or the
+// tensor-core kernel, split-K factor); grows the split-K partials buffer if needed.
+lrcc_status Runtime::launch_gemm(GemmArgs a, const Gemm& g, const GemmChoice& c, int nr, cudaStream_t st, int prec) {
+  a.nsplit = no_split ? 1 : std::max(1, c.nsplit);
+  a.part = nullptr;
+  if (a.nsplit > 1) {
+    const size_t need = (size_t)nr * g.nbatch() * a.nsplit * g.M * g.N * sizeof(double2);
+    if (need > part_bytes) {
+      if (part) {
+        if (!ck(cudaStreamSynchronize(st), "split-K sync")) return LRCC_ECUDA;
+        cudaFree(part);
+        part = nullptr;
+        part_bytes = 0;
+      }
+      if (!ck(cudaMalloc(&part, need), "cudaMalloc(split-K partials)")) return LRCC_ENOMEM;
+      part_bytes = need;
+    }
+    a.part = part;
+  }
+  cudaError_t e = (c.tc && prec > 0) ? launch_gemm_tc(a, prec, nr, dflag, st) : launch_gemm_f64(a, c.tile, nr, st);
+  ++launches;
+  if (e == cudaSuccess && a.nsplit > 1) {
+    e = launch_split_reduce(a, nr, st);
+    ++launches;
+  }
+  return ck(e, "gemm launch") ? LRCC_OK : LRCC_ECUDA;
+}
+
+// Autotuner: for every unpacked GEMM op of the program, time the candidate kernel
+// choices on the problem's own operands (two launches each after one warm-up, CUDA
+// events) and keep the fastest.  Ops whose default already takes over 50 ms are
+// compute-saturated large GEMMs and keep their default.  The timing launches
+// accumulate into the op's destination, so the caller reruns the product afterwards.
+lrcc_status Runtime::autotune(const Program& pr, double2* const ar[AR_COUNT], int nrhs, cudaStream_t st, int prec,
+                              std::map<int, GemmChoice>& out) {
+  long long stride[AR_COUNT] = {0, plan.arena_size[AR_IN], plan.arena_size[AR_OUT], plan.arena_size[AR_SCR], 0};
+  cudaEvent_t e0, e1;
+  if (!ck(cudaEventCreate(&e0), "autotune event") || !ck(cudaEventCreate(&e1), "autotune event")) return LRCC_ECUDA;
+  lrcc_status rs = LRCC_OK;
+  for (const Op& op : pr.ops) {
+    if (op.kind != OP_GEMM) continue;
+    const Gemm& g = plan.gemms[op.idx];
+    if (g.arC == AR_FIX) continue;  // never disturb fixed data
+    if (prec > 0 && use_packed(g)) continue;
+    const GemmDesc& d = gdesc[op.idx];
+    const int nr = op.fixed_only ? 1 : nrhs;
+    GemmArgs a;
+    a.M = g.M; a.N = g.N; a.K = g.K; a.ta = g.ta; a.tb = g.tb;
+    a.epi = g.epi; a.ep1 = g.ep[1]; a.ep2 = g.ep[2]; a.ep3 = g.ep[3];
+    a.lda = g.lda; a.ldb = g.ldb; a.ldc = g.ldc;
+    a.ar = g.ar; a.ai = g.ai;
+    a.coff = d.coff; a.sbeg = d.sbeg; a.aoff = d.aoff; a.boff = d.boff;
+    a.nbatch = g.nbatch();
+    a.tiles_m = a.tiles_n = 1;
+    a.A = ar[g.arA]; a.B = ar[g.arB]; a.C = ar[g.arC];
+    a.sA = op.fixed_only ? 0 : stride[g.arA];
+    a.sB = op.fixed_only ? 0 : stride[g.arB];
+    a.sC = op.fixed_only ? 0 : stride[g.arC];
+    auto time_it = [&](const GemmChoice& c, float& ms) -> lrcc_status {
+      lrcc_status s2 = launch_gemm(a, g, c, nr, st, prec);
+      if (s2 != LRCC_OK) return s2;
+      if (!ck(cudaEventRecord(e0, st), "autotune record")) return LRCC_ECUDA;
+      for (int r = 0; r < 2; ++r)
+        if ((s2 = launch_gemm(a, g, c, nr, st, prec)) != LRCC_OK) return s2;
+      if (!ck(cudaEventRecord(e1, st), "autotune record") || !ck(cudaEventSynchronize(e1), "autotune sync") ||
+          !ck(cudaEventElapsedTime(&ms, e0, e1), "autotune elapsed"))
+        return LRCC_ECUDA;
+      return LRCC_OK;
+    };
+    const GemmChoice def = default_choice(g, d, prec);
+    float best_ms = 0.f;
+    if ((rs = time_it(def, best_ms)) != LRCC_OK) break;
+    GemmChoice best = def;
+    if (best_ms < 100.f) {
+      std::vector<GemmChoice> cand;
+      const bool tc_ok = prec > 0;
+      for (int tc = 0; tc <= (tc_ok ? 1 : 0); ++tc)
+        for (int t = 0; t < (tc ? 1 : GT_COUNT); ++t) {
+          GemmChoice c;
+          c.tc = tc != 0;
+          c.tile = tc ? d.tile : t;
+          GemmDesc dd = d;
+          dd.tile = c.tile;
+          const int s0 = pick_split(g, dd, 1, c.tc);
+          for (int sp : {1, s0, std::max(1, s0 / 2), s0 * 2}) {
+            c.nsplit = sp;
+            bool dup = false;
+            for (const auto& x : cand) dup = dup || (x.tc == c.tc && x.tile == c.tile && x.nsplit == c.nsplit);
+            if (!dup && !(c.tc == def.tc && c.tile == def.tile && c.nsplit == def.nsplit)) cand.push_back(c);
+          }
+        }
+      for (const auto& c : cand) {
+        float ms = 0.f;
+        if ((rs = time_it(c, ms)) != LRCC_OK) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = c;
+        }
+      }
+      if (rs != LRCC_OK) break;
+    }
+    out[op.idx] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rs == LRCC_OK && prec > 0) rs = read_flag(st);
+  return rs;
+}
+
 lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrhs, cudaStream_t st, int prec) {
   if (&pr == &plan.ground) ++fix_version;  // cached tensor-core packs of fixed operands are stale
   long long stride[AR_COUNT] = {0, plan.arena_size[AR_IN], plan.arena_size[AR_OUT], plan.arena_size[AR_SCR], 0};
@@ -355,28 +474,13 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
         lrcc_status ps = run_packed(op.idx, g, ar, nr, op.fixed_only != 0, stride, st, prec);
         if (ps != LRCC_OK) return ps;
       } else {
-        const bool tc = prec > 0 && tc_tile_useful(g);
-        a.nsplit = pick_split(g, d, nr, tc);
-        if (a.nsplit > 1) {
-          const size_t need = (size_t)nr * g.nbatch() * a.nsplit * g.M * g.N * sizeof(double2);
-          if (need > part_bytes) {
-            if (part) {
-              if (!ck(cudaStreamSynchronize(st), "split-K sync")) return LRCC_ECUDA;
-              cudaFree(part);
-              part = nullptr;
-              part_bytes = 0;
-            }
-            if (!ck(cudaMalloc(&part, need), "cudaMalloc(split-K partials)")) return LRCC_ENOMEM;
-            part_bytes = need;
-          }
-          a.part = part;
+        GemmChoice c = default_choice(g, d, prec);
+        if (tuned) {
+          auto t = tuned->find(op.idx);
+          if (t != tuned->end()) c = t->second;
         }
-        e = tc ? launch_gemm_tc(a, prec, nr, dflag, st) : launch_gemm_f64(a, d.tile, nr, st);
-        ++launches;
-        if (e == cudaSuccess && a.nsplit > 1) {
-          e = launch_split_reduce(a, nr, st);
-          ++launches;
-        }
+        lrcc_status gs = launch_gemm(a, g, c, nr, st, prec);
+        if (gs != LRCC_OK) return gs;
       }
     } else if (op.kind == OP_PERM) {
       const Perm& p = plan.perms[op.idx];
@@ -420,28 +524,121 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
     nvtxRangePop();
     if (!ck(e, "kernel launch")) return LRCC_ECUDA;
   }
-  if (prec > 0) {
-    int h = 0;
-    if (!ck(cudaMemcpyAsync(&h, dflag, sizeof(int), cudaMemcpyDeviceToHost, st), "flag read") ||
-        !ck(cudaStreamSynchronize(st), "flag sync"))
-      return LRCC_ECUDA;
-    if (h) {
-      cudaMemsetAsync(dflag, 0, sizeof(int), st);
-      err = "tensor-core GEMM: a bounded wait on an mbarrier gave up";
-      return LRCC_ETIMEOUT;
-    }
+  if (prec > 0 && !capturing) return read_flag(st);
+  return LRCC_OK;
+}
+
+lrcc_status Runtime::read_flag(cudaStream_t st) {
+  int h = 0;
+  if (!ck(cudaMemcpyAsync(&h, dflag, sizeof(int), cudaMemcpyDeviceToHost, st), "flag read") ||
+      !ck(cudaStreamSynchronize(st), "flag sync"))
+    return LRCC_ECUDA;
+  if (h) {
+    cudaMemsetAsync(dflag, 0, sizeof(int), st);
+    err = "tensor-core GEMM: a bounded wait on an mbarrier gave up";
+    return LRCC_ETIMEOUT;
   }
   return LRCC_OK;
 }
 
-lrcc_status Runtime::apply(int transpose, int nrhs, cudaStream_t st, int prec) {
+void Runtime::drop_graphs() {
+  for (auto& kv : graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  graphs.clear();
+}
+
+lrcc_status Runtime::apply(int transpose, int nrhs, cudaStream_t st, int prec, bool use_graphs, bool tune) {
+  const lrcc_status s = apply_impl(transpose, nrhs, st, prec, use_graphs, tune);
+  tuned = nullptr;
+  return s;
+}
+
+lrcc_status Runtime::apply_impl(int transpose, int nrhs, cudaStream_t st, int prec, bool use_graphs, bool tune) {
   double2* ar[AR_COUNT] = {fix, in, out, scr, ws};
+  tuned = nullptr;
+  if (tune) {
+    const auto tkey = std::make_tuple(transpose, nrhs, prec);
+    auto it = tunings.find(tkey);
+    if (it == tunings.end()) {
+      // the tuning launches need the product's intermediates in place: one eager
+      // product first, then the timing pass (its accumulations are discarded by the
+      // product that follows)
+      const Program& tp = transpose ? jacT : plan.jac;
+      double2* r0 = transpose ? in : out;
+      if (!ck(cudaMemsetAsync(r0, 0, plan.arena_size[AR_IN] * nrhs * sizeof(double2), st), "cudaMemsetAsync"))
+        return LRCC_ECUDA;
+      lrcc_status s0 = run(tp, ar, nrhs, st, prec);
+      if (s0 != LRCC_OK) return s0;
+      std::map<int, GemmChoice> m;
+      if ((s0 = autotune(tp, ar, nrhs, st, prec, m)) != LRCC_OK) return s0;
+      it = tunings.emplace(tkey, std::move(m)).first;
+      drop_graphs();  // captured with the default choices
+    }
+    tuned = &it->second;
+  }
   const int64_t vin = plan.arena_size[AR_IN];
   // zero the result side (every op accumulates); scratch buffers are zeroed by the
   // program's own zero ops at the start of their lifetimes
   double2* res = transpose ? in : out;
-  if (!ck(cudaMemsetAsync(res, 0, vin * nrhs * sizeof(double2), st), "cudaMemsetAsync")) return LRCC_ECUDA;
-  return run(transpose ? jacT : plan.jac, ar, nrhs, st, prec);
+  const Program& pr = transpose ? jacT : plan.jac;
+  if (!use_graphs || prof) {
+    if (!ck(cudaMemsetAsync(res, 0, vin * nrhs * sizeof(double2), st), "cudaMemsetAsync")) return LRCC_ECUDA;
+    return run(pr, ar, nrhs, st, prec);
+  }
+  const auto key = std::make_tuple(transpose, nrhs, prec);
+  const void* bufs[5] = {in, out, scr, part, packscr};
+  auto it = graphs.find(key);
+  bool valid = it != graphs.end() && it->second.version == fix_version;
+  if (valid)
+    for (int i = 0; i < 5; ++i) valid = valid && it->second.bufs[i] == bufs[i];
+  if (!valid) {
+    if (it != graphs.end()) {
+      if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+      graphs.erase(it);
+    }
+    // an eager product first: it allocates whatever the product needs (split-K
+    // partials, packed operands) and repacks fixed operands, so the capture that
+    // follows records kernels only
+    if (!ck(cudaMemsetAsync(res, 0, vin * nrhs * sizeof(double2), st), "cudaMemsetAsync")) return LRCC_ECUDA;
+    lrcc_status s = run(pr, ar, nrhs, st, prec);
+    if (s != LRCC_OK) return s;
+    if (!ck(cudaStreamSynchronize(st), "graph: sync before capture")) return LRCC_ECUDA;
+    const void* after[5] = {in, out, scr, part, packscr};
+    GraphRec rec;
+    rec.version = fix_version;
+    for (int i = 0; i < 5; ++i) rec.bufs[i] = after[i];
+    cudaStream_t cs = nullptr;
+    if (!ck(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "graph: capture stream")) return LRCC_ECUDA;
+    cudaGraph_t g = nullptr;
+    capturing = true;
+    const long long l0 = launches;
+    bool ok = ck(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "graph: begin capture");
+    if (ok) {
+      ok = ck(cudaMemsetAsync(res, 0, vin * nrhs * sizeof(double2), cs), "graph: memset");
+      lrcc_status rs = ok ? run(pr, ar, nrhs, cs, prec) : LRCC_ECUDA;
+      const bool ended = ck(cudaStreamEndCapture(cs, &g), "graph: end capture");
+      ok = ok && rs == LRCC_OK && ended;
+    }
+    capturing = false;
+    rec.nlaunch = launches - l0;
+    launches = l0;  // the captured kernels run when the graph is launched
+    const void* post[5] = {in, out, scr, part, packscr};
+    for (int i = 0; i < 5; ++i) ok = ok && post[i] == after[i];
+    if (ok) ok = ck(cudaGraphInstantiate(&rec.exec, g, 0), "graph: instantiate");
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (!ok) {
+      if (rec.exec) cudaGraphExecDestroy(rec.exec);
+      if (err.empty()) err = "graph capture of the product failed";
+      return LRCC_ECUDA;
+    }
+    graphs[key] = rec;
+    return prec > 0 ? read_flag(st) : LRCC_OK;  // this call's result is the eager product's
+  }
+  if (!ck(cudaGraphLaunch(it->second.exec, st), "cudaGraphLaunch")) return LRCC_ECUDA;
+  ++graph_launches;
+  launches += it->second.nlaunch;
+  return prec > 0 ? read_flag(st) : LRCC_OK;
 }
 
 }  // namespace lrcc
@@ -592,7 +789,9 @@ lrcc_status lrcc_jacobian_apply(lrcc_problem* p, int32_t transpose, int32_t nrhs
   Runtime& rt = p->rt;
   lrcc_status s = rt.ensure_rhs(nrhs);
   if (s != LRCC_OK) return s;
-  cudaStream_t st = (cudaStream_t)stream;
+  // a null handle is the caller's legacy default stream (this library is built with
+  // per-thread default streams, under which 0 would name the calling thread's stream)
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamLegacy;
   const Plan& P = rt.plan;
   const int nk = rt.dims.nk, o = rt.dims.nocc, v = rt.dims.nvir;
   const size_t b1 = (size_t)nk * o * v * sizeof(double2), b2 = (size_t)nk * nk * nk * o * o * v * v * sizeof(double2);
@@ -602,7 +801,7 @@ lrcc_status lrcc_jacobian_apply(lrcc_problem* p, int32_t transpose, int32_t nrhs
   if (!rt.ck(cudaMemcpy2DAsync(src + P.off_x1, pitch, x1, b1, b1, nrhs, cudaMemcpyDeviceToDevice, st), "copy x1") ||
       !rt.ck(cudaMemcpy2DAsync(src + P.off_x2, pitch, x2, b2, b2, nrhs, cudaMemcpyDeviceToDevice, st), "copy x2"))
     return LRCC_ECUDA;
-  s = rt.apply(transpose, nrhs, st, prec);
+  s = rt.apply(transpose, nrhs, st, prec, opt && opt->use_graphs, opt && opt->autotune);
   if (s != LRCC_OK) return s;
   if (!rt.ck(cudaMemcpy2DAsync(y1, b1, dst + P.off_x1, pitch, b1, nrhs, cudaMemcpyDeviceToDevice, st), "copy y1") ||
       !rt.ck(cudaMemcpy2DAsync(y2, b2, dst + P.off_x2, pitch, b2, nrhs, cudaMemcpyDeviceToDevice, st), "copy y2"))
@@ -614,6 +813,48 @@ lrcc_status lrcc_polarizability(lrcc_problem* p, const int32_t* comps, int32_t n
                                 int32_t nomega, const lrcc_options* opt, void* alpha, int32_t* info) {
   if (!p) return LRCC_EINVAL;
   return lrcc_polarize_impl(p->rt, p->have_t, p->have_l, comps, ncomp, omegas, nomega, opt, alpha, info);
+}
+
+lrcc_status lrcc_batch_polarizability(lrcc_problem* const* probs, int32_t nprob, const int32_t* comps,
+                                      int32_t ncomp, const double* omegas, int32_t nomega,
+                                      const lrcc_options* opt, void* const* alphas, int32_t* const* infos) {
+  if (!probs || nprob < 1 || !alphas) return LRCC_EINVAL;
+  for (int i = 0; i < nprob; ++i)
+    for (int j = 0; j < i; ++j)
+      if (probs[i] == probs[j]) return LRCC_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LRCC_ECUDA;
+  std::vector<lrcc_status> st(nprob, LRCC_OK);
+  std::vector<std::thread> th;
+  for (int i = 0; i < nprob; ++i) {
+    if (!probs[i] || !alphas[i]) {
+      st[i] = LRCC_EINVAL;
+      continue;
+    }
+    th.emplace_back([&, i]() {
+      lrcc::Runtime& rt = probs[i]->rt;
+      try {
+        if (!rt.ck(cudaSetDevice(dev), "batch: cudaSetDevice")) {
+          st[i] = LRCC_ECUDA;
+          return;
+        }
+        st[i] = lrcc_polarize_impl(rt, probs[i]->have_t, probs[i]->have_l, comps, ncomp, omegas, nomega, opt,
+                                   alphas[i], infos ? infos[i] : nullptr);
+        if (!rt.ck(cudaStreamSynchronize(cudaStreamPerThread), "batch: stream sync") && st[i] == LRCC_OK)
+          st[i] = LRCC_ECUDA;
+      } catch (const std::bad_alloc&) {
+        rt.err = "batch: host allocation failed";
+        st[i] = LRCC_ENOMEM;
+      } catch (...) {
+        rt.err = "batch: unexpected host exception";
+        st[i] = LRCC_EINVAL;
+      }
+    });
+  }
+  for (auto& t : th) t.join();
+  for (int i = 0; i < nprob; ++i)
+    if (st[i] != LRCC_OK) return st[i];
+  return LRCC_OK;
 }
 
 int64_t lrcc_kernel_launches(const lrcc_problem* p) { return p ? p->rt.launches : -1; }

@@ -2,13 +2,22 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/lrcc.h"
+#include "kernels.cuh"
 #include "plan.h"
 
 namespace lrcc {
+
+struct GemmChoice {
+  bool tc = false;  // tensor-core kernel (mixed precision) instead of the FP64 kernel
+  int tile = 0;     // FP64 kernel tile (gemm_tile_dims)
+  int nsplit = 1;   // split-K factor
+};
 
 struct GemmDesc {
   const long long* coff = nullptr;
@@ -69,7 +78,29 @@ struct Runtime {
                          const long long* stride, cudaStream_t st, int prec);
   // prec: 0 FP64 kernels; 1 TF32 and 2 BF16x3 tensor-core GEMMs (FP32 accumulation)
   lrcc_status run(const Program& pr, double2* const ar[AR_COUNT], int nrhs, cudaStream_t st, int prec = 0);
-  lrcc_status apply(int transpose, int nrhs, cudaStream_t st, int prec = 0);
+  lrcc_status apply(int transpose, int nrhs, cudaStream_t st, int prec = 0, bool graphs = false, bool tune = false);
+  lrcc_status apply_impl(int transpose, int nrhs, cudaStream_t st, int prec, bool graphs, bool tune);
+  // kernel choices of the unpacked GEMMs: default heuristics, or the autotuner's
+  // measurements per (transpose, nrhs, prec) when tuning is requested
+  GemmChoice default_choice(const Gemm& g, const GemmDesc& d, int prec) const;
+  lrcc_status launch_gemm(GemmArgs a, const Gemm& g, const GemmChoice& c, int nr, cudaStream_t st, int prec);
+  lrcc_status autotune(const Program& pr, double2* const ar[AR_COUNT], int nrhs, cudaStream_t st, int prec,
+                       std::map<int, GemmChoice>& out);
+  std::map<std::tuple<int, int, int>, std::map<int, GemmChoice>> tunings;
+  const std::map<int, GemmChoice>* tuned = nullptr;  // active during one apply
+  // CUDA graphs of whole products, keyed by (transpose, nrhs, prec); a graph is valid
+  // while the buffers it was captured with and the fixed-arena version are unchanged
+  struct GraphRec {
+    cudaGraphExec_t exec = nullptr;
+    long long version = -1;
+    long long nlaunch = 0;  // kernels in the graph
+    const void* bufs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  };
+  std::map<std::tuple<int, int, int>, GraphRec> graphs;
+  bool capturing = false;  // inside stream capture: run() skips its host-side flag read
+  long long graph_launches = 0;
+  void drop_graphs();
+  lrcc_status read_flag(cudaStream_t st);
   void release();
   void prof_reset();
 };

@@ -22,30 +22,13 @@
 
 #include "kernels.cuh"
 #include "runtime.h"
+#include "solver_core.h"
 #include "solver_kernels.cuh"
 
 using namespace lrcc;
 using cd = std::complex<double>;
 
 namespace {
-
-struct Dev {
-  std::vector<void*> ptrs;
-  ~Dev() {
-    for (void* p : ptrs) cudaFree(p);
-  }
-  template <class T>
-  T* get(Runtime& rt, size_t n, bool& ok) {
-    void* p = nullptr;
-    if (!ok) return nullptr;
-    if (!rt.ck(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)), "cudaMalloc(solver)")) {
-      ok = false;
-      return nullptr;
-    }
-    ptrs.push_back(p);
-    return (T*)p;
-  }
-};
 
 // Gaussian elimination with partial pivoting on a small dense complex system.
 bool solve_small(std::vector<cd> A, std::vector<cd> b, int n, std::vector<cd>& x) {
@@ -75,13 +58,245 @@ bool solve_small(std::vector<cd> A, std::vector<cd> b, int n, std::vector<cd>& x
   return true;
 }
 
+}  // namespace
+
+namespace lrcc {
+
 double u64_to_double(unsigned long long u) {
   double d;
   std::memcpy(&d, &u, sizeof(d));
   return d;
 }
 
-}  // namespace
+BatchSolver::BatchSolver(Runtime& r, const lrcc_options& o, int nsys, int min_pairs) : rt(r), opt(o), ns(nsys) {
+  depth = std::max(1, std::min(opt.diis_depth, 16));
+  maxit = std::max(1, opt.max_iter);
+  maxpairs = std::max(min_pairs, depth * ns) + 8;
+  vec = rt.plan.arena_size[AR_IN];
+  rel.assign(ns, 1.0);
+}
+
+lrcc_status BatchSolver::init() {
+  bool ok = true;
+  HX = dev.get<double2>(rt, (size_t)depth * ns * vec, ok);
+  HE = dev.get<double2>(rt, (size_t)depth * ns * vec, ok);
+  RES = dev.get<double2>(rt, (size_t)ns * vec, ok);
+  DEN = dev.get<double>(rt, (size_t)vec, ok);
+  RMAX = dev.get<unsigned long long>(rt, (size_t)ns, ok);
+  PA = dev.get<const double2*>(rt, (size_t)maxpairs, ok);
+  PB = dev.get<const double2*>(rt, (size_t)maxpairs, ok);
+  PART = dev.get<double2>(rt, dot_partial_elems(maxpairs), ok);
+  DOT = dev.get<double2>(rt, (size_t)maxpairs, ok);
+  COEF = dev.get<double2>(rt, (size_t)depth * ns, ok);
+  PV = dev.get<const double2*>(rt, (size_t)depth, ok);
+  if (!ok) return LRCC_ENOMEM;
+  const Plan& P = rt.plan;
+  const int nk = rt.dims.nk, o = rt.dims.nocc, v = rt.dims.nvir, n = o + v;
+  std::vector<double> den(vec, 1.0);
+  const std::vector<double>& e = rt.eps;
+  for (int k = 0; k < nk; ++k)
+    for (int i = 0; i < o; ++i)
+      for (int a = 0; a < v; ++a) den[P.off_x1 + ((size_t)k * o + i) * v + a] = e[k * n + o + a] - e[k * n + i];
+  size_t q = P.off_x2;
+  for (int ki = 0; ki < nk; ++ki)
+    for (int kj = 0; kj < nk; ++kj)
+      for (int ka = 0; ka < nk; ++ka) {
+        const int kb = ((ki + kj - ka) % nk + nk) % nk;
+        for (int i = 0; i < o; ++i)
+          for (int j = 0; j < o; ++j)
+            for (int a = 0; a < v; ++a)
+              for (int b = 0; b < v; ++b)
+                den[q++] = e[ka * n + o + a] + e[kb * n + o + b] - e[ki * n + i] - e[kj * n + j];
+      }
+  if (!rt.ck(cudaMemcpy(DEN, den.data(), vec * sizeof(double), cudaMemcpyHostToDevice), "den")) return LRCC_ECUDA;
+  return LRCC_OK;
+}
+
+lrcc_status BatchSolver::dots(const std::vector<const double2*>& a, const std::vector<const double2*>& b, int conj,
+                              long long len, std::vector<cd>& out) {
+  const int np = (int)a.size();
+  out.assign(np, 0.0);
+  for (int c0 = 0; c0 < np; c0 += maxpairs) {
+    const int m = std::min(maxpairs, np - c0);
+    if (!rt.ck(cudaMemcpy(PA, a.data() + c0, m * sizeof(void*), cudaMemcpyHostToDevice), "dots") ||
+        !rt.ck(cudaMemcpy(PB, b.data() + c0, m * sizeof(void*), cudaMemcpyHostToDevice), "dots") ||
+        !rt.ck(launch_dots(PA, PB, conj, len, m, PART, DOT, st), "dots kernel"))
+      return LRCC_ECUDA;
+    rt.launches += 2;
+    std::vector<double2> h(m);
+    if (!rt.ck(cudaMemcpy(h.data(), DOT, m * sizeof(double2), cudaMemcpyDeviceToHost), "dots")) return LRCC_ECUDA;
+    for (int i = 0; i < m; ++i) out[c0 + i] = cd(h[i].x, h[i].y);
+  }
+  return LRCC_OK;
+}
+
+lrcc_status BatchSolver::maxabs(const double2* x, int nrhs, std::vector<double>& out) {
+  if (!rt.ck(cudaMemsetAsync(RMAX, 0, nrhs * sizeof(unsigned long long), st), "memset") ||
+      !rt.ck(launch_maxabs(x, RMAX, vec, vec, nrhs, st), "maxabs"))
+    return LRCC_ECUDA;
+  rt.launches++;
+  std::vector<unsigned long long> h(nrhs);
+  if (!rt.ck(cudaMemcpy(h.data(), RMAX, nrhs * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "maxabs"))
+    return LRCC_ECUDA;
+  out.resize(nrhs);
+  for (int i = 0; i < nrhs; ++i) out[i] = u64_to_double(h[i]);
+  return LRCC_OK;
+}
+
+lrcc_status BatchSolver::diis(int it, int& nhist, std::vector<std::vector<cd>>& Bm, double2* X) {
+  lrcc_status s2;
+  const int slot = it % depth;
+  nhist = std::min(nhist + 1, depth);
+  std::vector<const double2*> pa, pb;
+  std::vector<int> slots;
+  for (int j = 0; j < nhist; ++j) {
+    const int sj = ((it - j) % depth + depth) % depth;
+    slots.push_back(sj);
+    for (int i = 0; i < ns; ++i) {
+      pa.push_back(HE + ((size_t)slot * ns + i) * vec);
+      pb.push_back(HE + ((size_t)sj * ns + i) * vec);
+    }
+  }
+  std::vector<cd> row;
+  if ((s2 = dots(pa, pb, 1, vec, row)) != LRCC_OK) return s2;
+  for (int j = 0; j < nhist; ++j)
+    for (int i = 0; i < ns; ++i) {
+      const int sj = slots[j];
+      Bm[i][slot * depth + sj] = row[j * ns + i];
+      Bm[i][sj * depth + slot] = std::conj(row[j * ns + i]);
+    }
+  std::vector<double2> coef((size_t)nhist * ns, make_double2(0.0, 0.0));
+  for (int i = 0; i < ns; ++i) {
+    std::vector<cd> x;
+    bool good = false;
+    if (nhist >= 2 && (opt.diis_period <= 1 || (it + 1) % opt.diis_period == 0)) {
+      const int m = nhist + 1;
+      std::vector<cd> A(m * m, 0.0), b(m, 0.0);
+      double sc = 0.0;
+      for (int a = 0; a < nhist; ++a) sc = std::max(sc, std::abs(Bm[i][slots[a] * depth + slots[a]]));
+      sc = sc > 0 ? 1.0 / sc : 1.0;
+      for (int a = 0; a < nhist; ++a) {
+        for (int c = 0; c < nhist; ++c) A[a * m + c] = sc * Bm[i][slots[a] * depth + slots[c]];
+        A[a * m + nhist] = -1.0;
+        A[nhist * m + a] = -1.0;
+      }
+      b[nhist] = -1.0;
+      good = solve_small(A, b, m, x);
+    }
+    for (int j = 0; j < nhist; ++j) {
+      cd cj = good ? x[j] : (j == 0 ? cd(1.0) : cd(0.0));
+      coef[(size_t)j * ns + i] = make_double2(cj.real(), cj.imag());
+    }
+  }
+  std::vector<const double2*> pv(nhist);
+  for (int j = 0; j < nhist; ++j) pv[j] = HX + (size_t)slots[j] * ns * vec;
+  if (!rt.ck(cudaMemcpy(PV, pv.data(), nhist * sizeof(void*), cudaMemcpyHostToDevice), "pv") ||
+      !rt.ck(cudaMemcpy(COEF, coef.data(), coef.size() * sizeof(double2), cudaMemcpyHostToDevice), "coef") ||
+      !rt.ck(launch_lincomb(PV, COEF, nhist, X, vec, vec, ns, st), "lincomb"))
+    return LRCC_ECUDA;
+  rt.launches++;
+  return LRCC_OK;
+}
+
+// Jacobi + DIIS on (A - w) x = -rhs (tr = 0, iterate in rt.in) or (A^T - w) x = -rhs
+// (tr = 1, transposed products, iterate in rt.out) for every system; prec selects the
+// GEMM arithmetic of the products.  rel receives the relative residual reached.
+lrcc_status BatchSolver::jacobi_diis(int tr, const double2* rhs, const std::vector<double>& rhsmax, const double* om,
+                                     int prec, double tol, int maxiter, bool& conv) {
+  lrcc_status s2;
+  double2* X = tr ? rt.out : rt.in;
+  double2* Y = tr ? rt.in : rt.out;
+  if (!rt.ck(launch_guess(rhs, DEN, om, X, vec, vec, ns, st), "guess")) return LRCC_ECUDA;
+  rt.launches++;
+  std::vector<std::vector<cd>> Bm(ns, std::vector<cd>(depth * depth, 0.0));
+  int nhist = 0;
+  conv = false;
+  for (int it = 0; it < maxiter; ++it) {
+    ++total_it;
+    if ((s2 = rt.apply(tr, ns, st, prec, opt.use_graphs != 0, opt.autotune != 0)) != LRCC_OK) return s2;
+    const int slot = it % depth;
+    if (!rt.ck(cudaMemsetAsync(RMAX, 0, ns * sizeof(unsigned long long), st), "memset") ||
+        !rt.ck(launch_update(X, Y, rhs, DEN, om, HE + (size_t)slot * ns * vec, HX + (size_t)slot * ns * vec, RMAX,
+                             vec, vec, ns, st),
+               "update"))
+      return LRCC_ECUDA;
+    rt.launches++;
+    std::vector<unsigned long long> hr(ns);
+    if (!rt.ck(cudaMemcpy(hr.data(), RMAX, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "rmax"))
+      return LRCC_ECUDA;
+    double worst = 0.0;
+    for (int i = 0; i < ns; ++i) {
+      rel[i] = u64_to_double(hr[i]) / std::max(rhsmax[i], 1e-300);
+      worst = std::max(worst, rel[i]);
+    }
+    if (worst <= tol) {
+      conv = true;
+      return LRCC_OK;
+    }
+    if ((s2 = diis(it, nhist, Bm, X)) != LRCC_OK) return s2;
+  }
+  return LRCC_OK;
+}
+
+// Solve every system into sol: FP64 Jacobi + DIIS, or (mixed precision) iterative
+// refinement: FP64 residual r = -rhs - (A - w) x, tensor-core inner solve of
+// (A - w) d = r to a loose tolerance, x += d, until max|r| / max|rhs| <= refine_tol.
+lrcc_status BatchSolver::solve(int tr, const double2* rhs, const double* om, double2* sol, bool& converged) {
+  lrcc_status s2;
+  const int prec = opt.precision;
+  double2* X = tr ? rt.out : rt.in;
+  double2* Y = tr ? rt.in : rt.out;
+  std::vector<double> rhsmax;
+  if ((s2 = maxabs(rhs, ns, rhsmax)) != LRCC_OK) return s2;
+  converged = false;
+  if (prec == 0) {
+    if ((s2 = jacobi_diis(tr, rhs, rhsmax, om, 0, opt.conv_tol, maxit, converged)) != LRCC_OK) return s2;
+    if (!rt.ck(cudaMemcpy(sol, X, (size_t)ns * vec * sizeof(double2), cudaMemcpyDeviceToDevice), "sol"))
+      return LRCC_ECUDA;
+    return LRCC_OK;
+  }
+  if (!rt.ck(launch_guess(rhs, DEN, om, sol, vec, vec, ns, st), "guess")) return LRCC_ECUDA;
+  rt.launches++;
+  const double tol64 = std::min(opt.refine_tol, 1e-3);
+  const double inner_tol = prec == 1 ? 3e-3 : 1e-4;
+  for (int outer = 0; outer < 40 && !converged; ++outer) {
+    if (!rt.ck(cudaMemcpy(X, sol, (size_t)ns * vec * sizeof(double2), cudaMemcpyDeviceToDevice), "x -> in"))
+      return LRCC_ECUDA;
+    if ((s2 = rt.apply(tr, ns, st, 0, opt.use_graphs != 0, opt.autotune != 0)) != LRCC_OK) return s2;
+    ++total_it;
+    // R = rhs + A x - w x = -r ; its max is the FP64 residual
+    if (!rt.ck(cudaMemsetAsync(RMAX, 0, ns * sizeof(unsigned long long), st), "memset") ||
+        !rt.ck(launch_residual(X, Y, rhs, om, RES, RMAX, vec, vec, ns, st), "residual"))
+      return LRCC_ECUDA;
+    rt.launches++;
+    std::vector<unsigned long long> hr(ns);
+    if (!rt.ck(cudaMemcpy(hr.data(), RMAX, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "rmax"))
+      return LRCC_ECUDA;
+    double worst = 0.0;
+    std::vector<double> rmx(ns);
+    for (int i = 0; i < ns; ++i) {
+      rmx[i] = u64_to_double(hr[i]);
+      rel[i] = rmx[i] / std::max(rhsmax[i], 1e-300);
+      worst = std::max(worst, rel[i]);
+    }
+    if (worst <= tol64) {
+      converged = true;
+      break;
+    }
+    bool inner_conv = false;
+    if ((s2 = jacobi_diis(tr, RES, rmx, om, prec, inner_tol, maxit, inner_conv)) != LRCC_OK) return s2;
+    for (int i = 0; i < ns; ++i) {
+      if (!rt.ck(launch_axpby(make_double2(1.0, 0.0), X + (size_t)i * vec, make_double2(1.0, 0.0),
+                              sol + (size_t)i * vec, vec, st),
+                 "x += d"))
+        return LRCC_ECUDA;
+      rt.launches++;
+    }
+  }
+  return LRCC_OK;
+}
+
+}  // namespace lrcc
 
 lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int32_t* comps, int32_t ncomp,
                                const double* omegas, int32_t nomega, const lrcc_options* optp, void* alpha_out,
@@ -120,8 +335,6 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
       rt.err = "polarizability: non-finite frequency";
       return LRCC_EINVAL;
     }
-  const int depth = std::max(1, std::min(opt.diis_depth, 16));
-  const int maxit = std::max(1, opt.max_iter);
   const int nk = rt.dims.nk, o = rt.dims.nocc, v = rt.dims.nvir, n = o + v;
   const Plan& P = rt.plan;
   const long long vec = P.arena_size[AR_IN];
@@ -163,25 +376,16 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
 
   lrcc_status s = rt.ensure_rhs(ns);
   if (s != LRCC_OK) return s;
+  BatchSolver bs(rt, opt, ns, ns * std::max(ns, ncomp));
+  if ((s = bs.init()) != LRCC_OK) return s;
   Dev dev;
   bool ok = true;
   double2* XI = dev.get<double2>(rt, (size_t)ns * vec, ok);
   double2* SOL = dev.get<double2>(rt, (size_t)ns * vec, ok);
   double2* FU = dev.get<double2>(rt, (size_t)ns * vec, ok);
-  double2* HX = dev.get<double2>(rt, (size_t)depth * ns * vec, ok);
-  double2* HE = dev.get<double2>(rt, (size_t)depth * ns * vec, ok);
   double2* TV = dev.get<double2>(rt, (size_t)vec, ok);
   double2* LAM = dev.get<double2>(rt, (size_t)vec, ok);
-  double* DEN = dev.get<double>(rt, (size_t)vec, ok);
   double* OM = dev.get<double>(rt, (size_t)ns, ok);
-  unsigned long long* RMAX = dev.get<unsigned long long>(rt, (size_t)ns, ok);
-  const int maxpairs = std::max(ns * ns, depth * ns) + 8;
-  const double2** PA = dev.get<const double2*>(rt, (size_t)maxpairs, ok);
-  const double2** PB = dev.get<const double2*>(rt, (size_t)maxpairs, ok);
-  double2* PART = dev.get<double2>(rt, dot_partial_elems(maxpairs), ok);
-  double2* DOT = dev.get<double2>(rt, (size_t)maxpairs, ok);
-  double2* COEF = dev.get<double2>(rt, (size_t)depth * ns, ok);
-  const double2** PV = dev.get<const double2*>(rt, (size_t)depth, ok);
   // left-response form: eta vectors, left right-hand sides and solutions, shifts -w
   double2* ETA = form ? dev.get<double2>(rt, (size_t)ncomp * vec, ok) : nullptr;
   double2* RHSL = form ? dev.get<double2>(rt, (size_t)ns * vec, ok) : nullptr;
@@ -195,23 +399,7 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
 
   // host helpers ------------------------------------------------------------
   auto dots = [&](const std::vector<const double2*>& a, const std::vector<const double2*>& b, int conj, long long len,
-                  std::vector<cd>& out) -> lrcc_status {
-    const int np = (int)a.size();
-    out.assign(np, 0.0);
-    for (int c0 = 0; c0 < np; c0 += maxpairs) {
-      const int m = std::min(maxpairs, np - c0);
-      if (!rt.ck(cudaMemcpy(PA, a.data() + c0, m * sizeof(void*), cudaMemcpyHostToDevice), "dots") ||
-          !rt.ck(cudaMemcpy(PB, b.data() + c0, m * sizeof(void*), cudaMemcpyHostToDevice), "dots") ||
-          !rt.ck(launch_dots(PA, PB, conj, len, m, PART, DOT, st), "dots kernel"))
-        return LRCC_ECUDA;
-      rt.launches += 2;
-      std::vector<double2> h(m);
-      if (!rt.ck(cudaMemcpy(h.data(), DOT, m * sizeof(double2), cudaMemcpyDeviceToHost), "dots"))
-        return LRCC_ECUDA;
-      for (int i = 0; i < m; ++i) out[c0 + i] = cd(h[i].x, h[i].y);
-    }
-    return LRCC_OK;
-  };
+                  std::vector<cd>& out) { return bs.dots(a, b, conj, len, out); };
   auto run_prog = [&](const Program& pr, int nrhs) -> lrcc_status {
     double2* ar[AR_COUNT] = {rt.fix, rt.in, rt.out, rt.scr, rt.ws};
     if (!rt.ck(cudaMemsetAsync(rt.out, 0, (size_t)vec * nrhs * sizeof(double2), st), "memset")) return LRCC_ECUDA;
@@ -246,36 +434,10 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
     double2* ar[AR_COUNT] = {rt.fix, nullptr, nullptr, nullptr, rt.ws};
     return rt.run(P.ground, ar, 1, st, gprec);
   };
-  auto maxabs = [&](const double2* x, int nrhs, std::vector<double>& out) -> lrcc_status {
-    CK(cudaMemsetAsync(RMAX, 0, nrhs * sizeof(unsigned long long), st), "memset");
-    CK(launch_maxabs(x, RMAX, vec, vec, nrhs, st), "maxabs");
-    rt.launches++;
-    std::vector<unsigned long long> h(nrhs);
-    CK(cudaMemcpy(h.data(), RMAX, nrhs * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "maxabs");
-    out.resize(nrhs);
-    for (int i = 0; i < nrhs; ++i) out[i] = u64_to_double(h[i]);
-    return LRCC_OK;
-  };
+  auto maxabs = [&](const double2* x, int nrhs, std::vector<double>& out) { return bs.maxabs(x, nrhs, out); };
 
-  // denominators, t vector, Lambda in the plain pairing of the paper-unit residual ----
+  // frequencies, t vector, Lambda in the plain pairing of the paper-unit residual ----
   {
-    std::vector<double> den(vec, 1.0);
-    const std::vector<double>& e = rt.eps;
-    for (int k = 0; k < nk; ++k)
-      for (int i = 0; i < o; ++i)
-        for (int a = 0; a < v; ++a) den[P.off_x1 + ((size_t)k * o + i) * v + a] = e[k * n + o + a] - e[k * n + i];
-    size_t q = P.off_x2;
-    for (int ki = 0; ki < nk; ++ki)
-      for (int kj = 0; kj < nk; ++kj)
-        for (int ka = 0; ka < nk; ++ka) {
-          const int kb = ((ki + kj - ka) % nk + nk) % nk;
-          for (int i = 0; i < o; ++i)
-            for (int j = 0; j < o; ++j)
-              for (int a = 0; a < v; ++a)
-                for (int b = 0; b < v; ++b)
-                  den[q++] = e[ka * n + o + a] + e[kb * n + o + b] - e[ki * n + i] - e[kj * n + j];
-        }
-    CK(cudaMemcpy(DEN, den.data(), vec * sizeof(double), cudaMemcpyHostToDevice), "den");
     std::vector<double> om(ns);
     for (int i = 0; i < ns; ++i) om[i] = sys[i].w;
     CK(cudaMemcpy(OM, om.data(), ns * sizeof(double), cudaMemcpyHostToDevice), "omega");
@@ -318,152 +480,14 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
       if (sys[i].c == c)
         CK(cudaMemcpy(XI + (size_t)i * vec, rt.out, vec * sizeof(double2), cudaMemcpyDeviceToDevice), "xi");
   }
-  // 2. batched solves ------------------------------------------------------------------
-  // Jacobi + DIIS on (A - w) x = -rhs (tr = 0, iterate in rt.in) or (A^T - w) x = -rhs
-  // (tr = 1, transposed products, iterate in rt.out) for every system; prec selects the
-  // GEMM arithmetic of the products.  rel receives the relative residual reached.
-  std::vector<double> rel(ns, 1.0);
-  int total_it = 0;
-  auto jacobi_diis = [&](int tr, const double2* rhs, const std::vector<double>& rhsmax, const double* om, int prec,
-                         double tol, int maxiter, bool& conv) -> lrcc_status {
-    lrcc_status s2;
-    double2* X = tr ? rt.out : rt.in;
-    double2* Y = tr ? rt.in : rt.out;
-    CK(launch_guess(rhs, DEN, om, X, vec, vec, ns, st), "guess");
-    rt.launches++;
-    std::vector<std::vector<cd>> Bm(ns, std::vector<cd>(depth * depth, 0.0));
-    int nhist = 0;
-    conv = false;
-    for (int it = 0; it < maxiter; ++it) {
-      ++total_it;
-      if ((s2 = rt.apply(tr, ns, st, prec)) != LRCC_OK) return s2;
-      const int slot = it % depth;
-      CK(cudaMemsetAsync(RMAX, 0, ns * sizeof(unsigned long long), st), "memset");
-      CK(launch_update(X, Y, rhs, DEN, om, HE + (size_t)slot * ns * vec, HX + (size_t)slot * ns * vec, RMAX, vec, vec,
-                       ns, st),
-         "update");
-      rt.launches++;
-      std::vector<unsigned long long> hr(ns);
-      CK(cudaMemcpy(hr.data(), RMAX, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "rmax");
-      double worst = 0.0;
-      for (int i = 0; i < ns; ++i) {
-        rel[i] = u64_to_double(hr[i]) / std::max(rhsmax[i], 1e-300);
-        worst = std::max(worst, rel[i]);
-      }
-      if (worst <= tol) {
-        conv = true;
-        return LRCC_OK;
-      }
-      nhist = std::min(nhist + 1, depth);
-      std::vector<const double2*> pa, pb;
-      std::vector<int> slots;
-      for (int j = 0; j < nhist; ++j) {
-        const int sj = ((it - j) % depth + depth) % depth;
-        slots.push_back(sj);
-        for (int i = 0; i < ns; ++i) {
-          pa.push_back(HE + ((size_t)slot * ns + i) * vec);
-          pb.push_back(HE + ((size_t)sj * ns + i) * vec);
-        }
-      }
-      std::vector<cd> row;
-      if ((s2 = dots(pa, pb, 1, vec, row)) != LRCC_OK) return s2;
-      for (int j = 0; j < nhist; ++j)
-        for (int i = 0; i < ns; ++i) {
-          const int sj = slots[j];
-          Bm[i][slot * depth + sj] = row[j * ns + i];
-          Bm[i][sj * depth + slot] = std::conj(row[j * ns + i]);
-        }
-      std::vector<double2> coef((size_t)nhist * ns, make_double2(0.0, 0.0));
-      for (int i = 0; i < ns; ++i) {
-        std::vector<cd> x;
-        bool good = false;
-        if (nhist >= 2 && (opt.diis_period <= 1 || (it + 1) % opt.diis_period == 0)) {
-          const int m = nhist + 1;
-          std::vector<cd> A(m * m, 0.0), b(m, 0.0);
-          double sc = 0.0;
-          for (int a = 0; a < nhist; ++a) sc = std::max(sc, std::abs(Bm[i][slots[a] * depth + slots[a]]));
-          sc = sc > 0 ? 1.0 / sc : 1.0;
-          for (int a = 0; a < nhist; ++a) {
-            for (int c = 0; c < nhist; ++c) A[a * m + c] = sc * Bm[i][slots[a] * depth + slots[c]];
-            A[a * m + nhist] = -1.0;
-            A[nhist * m + a] = -1.0;
-          }
-          b[nhist] = -1.0;
-          good = solve_small(A, b, m, x);
-        }
-        for (int j = 0; j < nhist; ++j) {
-          cd cj = good ? x[j] : (j == 0 ? cd(1.0) : cd(0.0));
-          coef[(size_t)j * ns + i] = make_double2(cj.real(), cj.imag());
-        }
-      }
-      std::vector<const double2*> pv(nhist);
-      for (int j = 0; j < nhist; ++j) pv[j] = HX + (size_t)slots[j] * ns * vec;
-      CK(cudaMemcpy(PV, pv.data(), nhist * sizeof(void*), cudaMemcpyHostToDevice), "pv");
-      CK(cudaMemcpy(COEF, coef.data(), coef.size() * sizeof(double2), cudaMemcpyHostToDevice), "coef");
-      CK(launch_lincomb(PV, COEF, nhist, X, vec, vec, ns, st), "lincomb");
-      rt.launches++;
-    }
-    return LRCC_OK;
+  // 2. batched solves (BatchSolver: FP64 Jacobi + DIIS, or mixed-precision refinement) ----
+  auto solve = [&](int tr, const double2* rhs, const double* om, double2* sol, bool& conv) {
+    return bs.solve(tr, rhs, om, sol, conv);
   };
-
-  // Solve every system into sol: FP64 Jacobi + DIIS, or (mixed precision) iterative
-  // refinement: FP64 residual r = -rhs - (A - w) x, tensor-core inner solve of
-  // (A - w) d = r to a loose tolerance, x += d, until max|r| / max|rhs| <= refine_tol.
-  // FU serves as the residual buffer.
-  const int prec = opt.precision;
-  auto solve = [&](int tr, const double2* rhs, const double* om, double2* sol, bool& converged) -> lrcc_status {
-    lrcc_status s2;
-    double2* X = tr ? rt.out : rt.in;
-    double2* Y = tr ? rt.in : rt.out;
-    std::vector<double> rhsmax;
-    if ((s2 = maxabs(rhs, ns, rhsmax)) != LRCC_OK) return s2;
-    converged = false;
-    if (prec == 0) {
-      if ((s2 = jacobi_diis(tr, rhs, rhsmax, om, 0, opt.conv_tol, maxit, converged)) != LRCC_OK) return s2;
-      CK(cudaMemcpy(sol, X, (size_t)ns * vec * sizeof(double2), cudaMemcpyDeviceToDevice), "sol");
-      return LRCC_OK;
-    }
-    CK(launch_guess(rhs, DEN, om, sol, vec, vec, ns, st), "guess");
-    rt.launches++;
-    const double tol64 = std::min(opt.refine_tol, 1e-3);
-    const double inner_tol = prec == 1 ? 3e-3 : 1e-4;
-    for (int outer = 0; outer < 40 && !converged; ++outer) {
-      CK(cudaMemcpy(X, sol, (size_t)ns * vec * sizeof(double2), cudaMemcpyDeviceToDevice), "x -> in");
-      if ((s2 = rt.apply(tr, ns, st, 0)) != LRCC_OK) return s2;
-      ++total_it;
-      // R = rhs + A x - w x = -r ; its max is the FP64 residual
-      CK(cudaMemsetAsync(RMAX, 0, ns * sizeof(unsigned long long), st), "memset");
-      CK(launch_residual(X, Y, rhs, om, FU, RMAX, vec, vec, ns, st), "residual");
-      rt.launches++;
-      std::vector<unsigned long long> hr(ns);
-      CK(cudaMemcpy(hr.data(), RMAX, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "rmax");
-      double worst = 0.0;
-      std::vector<double> rmx(ns);
-      for (int i = 0; i < ns; ++i) {
-        rmx[i] = u64_to_double(hr[i]);
-        rel[i] = rmx[i] / std::max(rhsmax[i], 1e-300);
-        worst = std::max(worst, rel[i]);
-      }
-      if (worst <= tol64) {
-        converged = true;
-        break;
-      }
-      bool inner_conv = false;
-      if ((s2 = jacobi_diis(tr, FU, rmx, om, prec, inner_tol, maxit, inner_conv)) != LRCC_OK) return s2;
-      for (int i = 0; i < ns; ++i) {
-        CK(launch_axpby(make_double2(1.0, 0.0), X + (size_t)i * vec, make_double2(1.0, 0.0), sol + (size_t)i * vec,
-                        vec, st),
-           "x += d");
-        rt.launches++;
-      }
-    }
-    return LRCC_OK;
-  };
-
   bool converged = false;
   if ((s = solve(0, XI, OM, SOL, converged)) != LRCC_OK) return s;
   if (info) {
-    info[0] = total_it;
+    info[0] = bs.total_it;
     info[1] = converged ? 0 : LRCC_ENOCONV;
   }
   if (!converged) {
@@ -616,7 +640,7 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
     bool lconv = false;
     if ((s = solve(1, RHSL, OMN, TBAR, lconv)) != LRCC_OK) return s;
     if (info) {
-      info[0] = total_it;
+      info[0] = bs.total_it;
       info[1] = lconv ? 0 : LRCC_ENOCONV;
     }
     if (!lconv) {

@@ -46,7 +46,7 @@ class PlanView:
         fl = np.zeros(3, np.float64)
         lib.lrcc_plan_info(h, _p(ar, I64P), _p(off, I64P), _p(fl, F64P))
         self.arena_sizes, self.offsets, self.flops = ar, off, fl
-        self.programs = [self._read(w) for w in range(5)]
+        self.programs = [self._read(w) for w in range(7)]
 
     def _read(self, which):
         lib, h = self.lib, self.h

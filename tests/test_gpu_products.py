@@ -103,3 +103,45 @@ def test_c2_sampled_blocks(lr):
     y2 = y2[0].cpu().numpy()
     for bk in blocks:
         assert _rel(y2[bk], nk * a2[bk].numpy()) < TOL, bk
+
+
+def test_graph_replay_bitwise_and_invalidation(lr):
+    """use_graphs: the first call runs eagerly and captures, later calls replay the graph;
+    results are bitwise those of the eager path, also after the ground state changes."""
+    nk, o, v, Q = 3, 2, 5, 8
+    p, prob, t1, t2 = _setup(lr, nk, o, v, Q)
+    x1, x2 = random_probe(nk, o, v, seed=17, nrhs=2)
+    dev = torch.device("cuda")
+    X1 = torch.as_tensor(x1, device=dev).contiguous()
+    X2 = torch.as_tensor(x2 * nk, device=dev).contiguous()
+    g = lr.default_options(use_graphs=1)
+    for tr in (False, True):
+        ref = prob.jacobian_apply(X1, X2, transpose=tr)
+        for _ in range(3):
+            got = prob.jacobian_apply(X1, X2, transpose=tr, options=g)
+            assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
+    t1b, t2b = random_amplitudes(nk, o, v, seed=18, scale1=0.03, scale2=0.03)
+    prob.set_ground_state(t1b, t2b * nk)
+    ref = prob.jacobian_apply(X1, X2)
+    got = prob.jacobian_apply(X1, X2, options=g)
+    assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_autotuned_products(lr, prec):
+    """autotune: the measured kernel choices give the same product (FP64: to rounding;
+    BF16x3: within its error bound against FP64)."""
+    nk, o, v, Q = 3, 4, 16, 48
+    p, prob, t1, t2 = _setup(lr, nk, o, v, Q)
+    x1, x2 = random_probe(nk, o, v, seed=19, nrhs=2)
+    dev = torch.device("cuda")
+    X1 = torch.as_tensor(x1, device=dev).contiguous()
+    X2 = torch.as_tensor(x2 * nk, device=dev).contiguous()
+    for tr in (False, True):
+        r1, r2 = prob.jacobian_apply(X1, X2, transpose=tr)
+        a1, a2 = prob.jacobian_apply(X1, X2, transpose=tr, options=lr.default_options(precision=prec, autotune=1))
+        b1, b2 = prob.jacobian_apply(X1, X2, transpose=tr, options=lr.default_options(precision=prec, autotune=1))
+        assert torch.equal(a1, b1) and torch.equal(a2, b2)  # tuned choices are kept
+        tol = 1e-12 if prec == 0 else 5e-5
+        assert float((a1 - r1).abs().max() / r1.abs().max()) < tol
+        assert float((a2 - r2).abs().max() / r2.abs().max()) < tol

@@ -144,3 +144,45 @@ def test_xi_and_egrad_programs(lib, nk, o, v, Q):
     h = 1e-2
     ref = (E((h, h)) - E((h, -h)) - E((-h, h)) + E((-h, -h))) / (4 * h * h)  # exact: E quadratic in t1
     assert abs(lhs - ref) < 1e-11 * abs(ref)
+
+
+@pytest.mark.parametrize("nk,o,v,Q", [(2, 2, 3, 3), (3, 1, 2, 4)])
+def test_omega0_and_tgrad_programs(lib, nk, o, v, Q):
+    """Residual at zero amplitudes and the energy gradient, simulated, against the oracle
+    (paper units: doubles of the residual times Nk, doubles of the gradient over Nk)."""
+    p = make_problem(nk, o, v, Q, seed=12, sigma_l=0.2)
+    R = rcc.RCC(p)
+    t1, t2 = random_amplitudes(nk, o, v, seed=13, scale1=0.05, scale2=0.05)
+    pv, ar = _sim_setup(lib, p, t1, t2, 1 << 20)
+    z1 = np.zeros((nk, o, v), complex)
+    z2 = np.zeros((nk,) * 3 + (o, o, v, v), complex)
+    y1, y2 = _sim_apply(pv, ar, z1, z2, 5)
+    T = torch.as_tensor
+    r1, r2 = R.residual(T(z1), T(z2))
+    assert np.abs(y1 - r1.numpy()).max() <= 1e-15
+    assert np.abs(y2 - nk * r2.numpy()).max() < 1e-13 * np.abs(nk * r2.numpy()).max()
+    g1, g2 = _sim_apply(pv, ar, t1, t2 * nk, 6)
+    e1, e2 = R.energy_grad(T(t1), T(t2))
+    assert np.abs(g1 - e1.numpy()).max() < 1e-13 * np.abs(e1.numpy()).max()
+    assert np.abs(g2 - e2.numpy() / nk).max() < 1e-13 * np.abs(e2.numpy() / nk).max()
+
+
+def test_residual_by_gauss_legendre_identity(lib):
+    """Omega(t) = Omega(0) + 1/2 [A(s1 t) t + A(s2 t) t], s1,2 = (1 -+ 1/sqrt 3)/2: exact
+    (A(s t) t is cubic in s); the GPU ground-state solver evaluates the residual this way."""
+    nk, o, v, Q = 2, 2, 3, 3
+    p = make_problem(nk, o, v, Q, seed=14, sigma_l=0.2)
+    R = rcc.RCC(p)
+    t1, t2 = random_amplitudes(nk, o, v, seed=15, scale1=0.1, scale2=0.1)
+    z1 = np.zeros((nk, o, v), complex)
+    z2 = np.zeros((nk,) * 3 + (o, o, v, v), complex)
+    pv, ar = _sim_setup(lib, p, 0 * t1, 0 * t2, 1 << 20)
+    w1, w2 = _sim_apply(pv, ar, z1, z2, 5)
+    for s in (0.5 - 0.5 / np.sqrt(3.0), 0.5 + 0.5 / np.sqrt(3.0)):
+        pv, ar = _sim_setup(lib, p, s * t1, s * t2, 1 << 20)
+        a1, a2 = _sim_apply(pv, ar, t1, t2 * nk, 1)
+        w1, w2 = w1 + 0.5 * a1, w2 + 0.5 * a2
+    T = torch.as_tensor
+    r1, r2 = R.residual(T(t1), T(t2))
+    assert np.abs(w1 - r1.numpy()).max() < 1e-12 * np.abs(r1.numpy()).max()
+    assert np.abs(w2 - nk * r2.numpy()).max() < 1e-12 * np.abs(nk * r2.numpy()).max()
