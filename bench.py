@@ -108,11 +108,21 @@ def _measured_peak(key, fallback):
         return fallback
 
 
+# dipole components and frequencies (Ha) of each workload; a product step covers one vector
+# per (component, +-omega) system (omega = 0 counted once)
+WORKLOADS = {
+    "c1": ([2], [0.0, 0.1]),
+    "c2": ([0, 1, 2], [0.0, 0.05, 0.1]),
+    "c3": ([0, 1, 2], [0.0, 0.03, 0.06, 0.09, 0.12, 0.15]),
+    "c4": ([0, 2], [0.0, 0.05, 0.1, 0.15]),
+    "c5": ([0, 1, 2], [0.0, 0.05, 0.1]),
+}
+
+
 def workload(cfg_name):
     from synth import CONFIGS
     c = dict(CONFIGS[cfg_name])
-    comps = [0, 1, 2]
-    omegas = [0.0, 0.05, 0.1]
+    comps, omegas = WORKLOADS[cfg_name]
     nsys = sum(len(comps) * (1 if w == 0 else 2) for w in omegas)
     return c, comps, omegas, nsys
 
@@ -167,6 +177,22 @@ def run_reference(args):
                              "unit": "products/s"},
             "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _fixed_elems(lr, nk, o, v, Q):
+    """Fixed-arena size (complex elements) from the plan introspection call."""
+    import ctypes as C
+    from paper_2508_01266_gb300._lib import lib, lrcc_dims
+    d = lrcc_dims(nk, o, v, Q, 0)
+    h = C.c_void_p()
+    if lib.lrcc_plan_create(C.byref(d), 1 << 26, C.byref(h)) != 0:
+        return 0
+    ar = (C.c_int64 * 5)()
+    off = (C.c_int64 * 11)()
+    fl = (C.c_double * 3)()
+    lib.lrcc_plan_info(h, ar, off, fl)
+    lib.lrcc_plan_destroy(h)
+    return int(ar[0])
 
 
 def time_mixed(lr, prob, X1, X2, Y1, Y2, args, st, dist, products):
@@ -253,6 +279,7 @@ def main():
     prob = lr.Problem(nk, o, v, Q)
     prob.set_integrals(p.L, p.eps, p.dip)
     prob.set_ground_state(t1, t2 * nk)
+    prob_fixed_gb = 16.0 * _fixed_elems(lr, nk, o, v, Q) / 1e9
     x1, x2 = random_probe(nk, o, v, seed=2000 + 97 * rank, nrhs=nrhs)
     dev = torch.device("cuda", local)
     X1 = torch.as_tensor(x1, device=dev).contiguous()
@@ -349,9 +376,10 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
                 "data": "synthetic",
                 "config": {"workload": (f"{args.config}: Nk={nk} nocc={o} nvir={v} naux={Q}, {nrhs} vectors per "
-                                        f"step (3 dipole components x omega in {{0,0.05,0.1}} Ha, +-omega)"),
+                                        f"step ({len(comps)} dipole components x omega in {omegas} Ha, +-omega)"),
                            "precision": "fp64", "rhs_per_step": nrhs, "parallelism": f"replicas x{ws}",
-                           "l2": "working set larger than L2 (vector 205 MB, intermediates > 1 GB)"},
+                           "l2": (f"working set larger than L2 (vector {16 * nk**3 * o * o * v * v / 1e6:.0f} MB, "
+                                  f"fixed intermediates {prob_fixed_gb:.1f} GB); no flush")},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "mixed_precision": mixed,
                 "clocks": clk}

@@ -41,12 +41,19 @@ def default_options(**kw) -> lrcc_options:
 def _ptr(t: torch.Tensor):
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
+    if t.is_conj() or t.is_neg():
+        raise ValueError("tensor has a lazy conjugate/negation bit: resolve it first")
     return C.c_void_p(t.data_ptr())
+
+
+def _dense(t: torch.Tensor) -> torch.Tensor:
+    """Contiguous tensor whose memory holds its values (lazy conj/neg views resolved)."""
+    return t.resolve_conj().resolve_neg().contiguous()
 
 
 def _c128(x, device):
     t = torch.as_tensor(x) if not isinstance(x, torch.Tensor) else x
-    return t.to(device=device, dtype=torch.complex128).contiguous()
+    return _dense(t.to(device=device, dtype=torch.complex128))
 
 
 def create(nk, nocc, nvir, naux, kmesh=0):
@@ -116,8 +123,8 @@ def jacobian_apply(h, x1: torch.Tensor, x2: torch.Tensor, transpose=False, y1=No
     """y = A x (or P_sym A^T x) for a batch of vectors x1[nrhs,...], x2[nrhs,...] (CUDA complex128)."""
     if x1.device.type != "cuda" or x2.device.type != "cuda":
         raise ValueError("jacobian_apply takes CUDA tensors")
-    x1 = x1.contiguous()
-    x2 = x2.contiguous()
+    x1 = _dense(x1)
+    x2 = _dense(x2)
     nrhs = x1.shape[0]
     y1 = torch.empty_like(x1) if y1 is None else y1
     y2 = torch.empty_like(x2) if y2 is None else y2
@@ -142,8 +149,8 @@ def polarizability(h, comps, omegas, options=None):
 
 def residual(h, t1: torch.Tensor, t2: torch.Tensor):
     """CCSD residual Omega(t) (paper units) of CUDA complex128 amplitudes t1, t2."""
-    t1 = t1.contiguous()
-    t2 = t2.contiguous()
+    t1 = _dense(t1)
+    t2 = _dense(t2)
     r1, r2 = torch.empty_like(t1), torch.empty_like(t2)
     _check(lib.lrcc_residual(h, _ptr(t1), _ptr(t2), _ptr(r1), _ptr(r2)), h)
     return r1, r2

@@ -25,9 +25,10 @@ class LRCCJacobian(torch.autograd.Function):
     @staticmethod
     @once_differentiable
     def backward(ctx, g1, g2):
-        b1, b2 = ctx.problem.jacobian_apply(g1.conj().contiguous(), g2.conj().contiguous(), transpose=True,
+        # conj() is a lazy view in torch: materialise it before the library reads the memory
+        b1, b2 = ctx.problem.jacobian_apply(g1.conj().resolve_conj(), g2.conj().resolve_conj(), transpose=True,
                                             options=ctx.options)
-        return b1.conj(), b2.conj(), None, None
+        return b1.conj().resolve_conj(), b2.conj().resolve_conj(), None, None
 
 
 def jacobian(problem, x1: torch.Tensor, x2: torch.Tensor, options=None):

@@ -25,6 +25,9 @@ struct GemmArgs {
   // order, applies alpha and the epilogue (bitwise reproducible).
   int nsplit = 1;
   double2* part = nullptr;
+  // tensor-core kernel only: the launch computes C^T = B^T A^T (operands and M, N swapped
+  // by the caller) and the epilogue writes element (m, n) of the launch to C[n][m]
+  int swap = 0;
 };
 
 struct PermArgs {

@@ -239,20 +239,21 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(GemmArgs g, int* er
     if (step > 0) mbar_wait(smem_u32(&mbar[(step - 1) & 1]), ((step - 1) >> 1) & 1);
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
+  // destination row length of the partials: the original N (= M of a swapped launch)
+  const int Nrow = g.swap ? M : N;
   if (ok && g.nsplit > 1 && total == 0) {  // an empty split still owns its partial tile
     const int m = m0 + tid;
     if (m < M) {
-      double2* Pp = g.part + ((rhs * g.nbatch + batch) * g.nsplit + sp) * (long long)M * N + (long long)m * N;
-      for (int n = n0; n < n0 + TC_BNC && n < N; ++n) Pp[n] = make_double2(0.0, 0.0);
+      double2* Pp = g.part + ((rhs * g.nbatch + batch) * g.nsplit + sp) * (long long)M * N;
+      for (int n = n0; n < n0 + TC_BNC && n < N; ++n)
+        Pp[g.swap ? (long long)n * Nrow + m : (long long)m * Nrow + n] = make_double2(0.0, 0.0);
     }
   }
   if (ok && total > 0) {
     const int warp = tid >> 5, lane = tid & 31;
     const int m = m0 + warp * 32 + lane;
     double2* Cp = Cb + g.coff[batch];
-    double2* Pp = g.nsplit > 1
-                      ? g.part + ((rhs * g.nbatch + batch) * g.nsplit + sp) * (long long)M * N + (long long)m * N
-                      : nullptr;
+    double2* Pp = g.nsplit > 1 ? g.part + ((rhs * g.nbatch + batch) * g.nsplit + sp) * (long long)M * N : nullptr;
 #pragma unroll 1
     for (int c0 = 0; c0 < TC_NR; c0 += 16) {
       uint32_t r[16];
@@ -269,20 +270,21 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(GemmArgs g, int* er
           const int n = n0 + c0 / 2 + j;
           if (n >= N) break;
           const double ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
+          const int mo = g.swap ? n : m, no = g.swap ? m : n;  // element of the original C
           if (Pp) {  // raw partial; alpha and the epilogue come in the reduction
-            Pp[n] = make_double2(ar, ai);
+            Pp[(long long)mo * Nrow + no] = make_double2(ar, ai);
             continue;
           }
           const double vr = g.ar * ar - g.ai * ai, vi = g.ar * ai + g.ai * ar;
           if (g.epi == 0) {
-            double2* cp = Cp + (long long)m * g.ldc + n;
+            double2* cp = Cp + (long long)mo * g.ldc + no;
             double2 cv = *cp;
             cv.x += vr;
             cv.y += vi;
             *cp = cv;
           } else {
-            const int a = m / g.ep2, c = m - a * g.ep2;
-            const int b = n / g.ep3, d = n - b * g.ep3;
+            const int a = mo / g.ep2, c = mo - a * g.ep2;
+            const int b = no / g.ep3, d = no - b * g.ep3;
             Cp[(((long long)a * g.ep1 + b) * g.ep2 + c) * g.ep3 + d] = make_double2(vr, vi);
           }
         }

@@ -744,18 +744,14 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
   // [A] ladder
   ladder(J, rpp, tLvv, v, xpp, 0.5, "ladder", &P.ladder_flops, &P.wbuild_flops);
   // [B] hole-hole: rpp += 1/2 Whh^T xpp ; Yhh = V xpp^T ; rpp += 1/2 Yhh^T Tpp.  The last
-  //     product shares its right factor with B' below: Yhh collects both left factors
-  //     and one GEMM ("hh quad") applies Tpp after (13).
+  //     product shares its right factor with B': Yhh is formed in (13), collects both
+  //     left factors, and one GEMM ("hh quad") applies Tpp.
   b.pair_gemm(J, rpp, Whh, 1, xpp, 0, 0.5, 0.0, "hh");
-  T4 Yhh = b.t4(AR_SCR, LK_PP, o, o, o, o);
-  b.pair_gemm(J, Yhh, Vpp, 0, xpp, 1, 1.0, 0.0, "Yhh");
-  // [C] ring: Zc = WC xc - 1/2 (xc M) Tc ; YC = -1/2 xc M collects C' too (one Tc product)
-  T4 YC = b.t4(AR_SCR, LK_PH, o, v, v, o);
-  b.pair_gemm(J, YC, xc, 0, Mph, 0, -0.5, 0.0, "YC");
+  // [C] ring: Zc = WC xc - 1/2 (xc M) Tc ; the second product is formed in (14) together
+  //     with C' (YC = -1/2 xc M + WCx, one Tc product)
   b.pair_gemm(J, Zc, WC, 0, xc, 0, 1.0, 0.0, "ring C");
-  // [D] ring: Zd = 1/2 WD Ud + 1/4 (Ud ML) ud ; YD = 1/2 Ud ML collects D' too (one ud product)
-  T4 YD = b.t4(AR_SCR, LK_PH, o, v, v, o);
-  b.pair_gemm(J, YD, Ud, 0, MLph, 0, 0.5, 0.0, "YD");
+  // [D] ring: Zd = 1/2 WD Ud + 1/4 (Ud ML) ud ; the second product is formed in (15)
+  //     together with D' (YD = 1/2 Ud ML + WDx, one ud product)
   b.pair_gemm(J, Zd, WD, 0, Ud, 0, 0.5, 0.0, "ring D");
   // [E] Fock-like terms in K3 blocks
   auto e_vv = [&](Program& pr, const T4& r, const T4& A, int64_t Bvv, int arB, double alpha, const char* tag) {
@@ -908,6 +904,8 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
     T4 Ioox = b.t4(AR_SCR, LK_CH, o, o, o, o);
     chem(J, Ioox, dLoo, o, o, tLoo, o, o, AR_SCR, AR_FIX, 1.0, "(ki|lj)' a");
     chem(J, Ioox, tLoo, o, o, dLoo, o, o, AR_FIX, AR_SCR, 1.0, "(ki|lj)' b");
+    T4 Yhh = b.t4(AR_SCR, LK_PP, o, o, o, o);
+    b.pair_gemm(J, Yhh, Vpp, 0, xpp, 1, 1.0, 0.0, "Yhh");
     b.perm(J, Yhh, Ioox, {0, 1, 2, 3}, 1.0, 0.0, "(ki|lj)' pp");
     b.pair_gemm(J, rpp, Yhh, 1, Tpp, 0, 0.5, 0.0, "hh quad");  // hh quad + B'
   }
@@ -916,6 +914,8 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
     T4 Ix = b.t4(AR_SCR, LK_CH, o, v, o, v);
     chem(J, Ix, dLoo, o, o, tLvv, v, v, AR_SCR, AR_FIX, 1.0, "(ki|ac)' a");
     chem(J, Ix, tLoo, o, o, dLvv, v, v, AR_FIX, AR_SCR, 1.0, "(ki|ac)' b");
+    T4 YC = b.t4(AR_SCR, LK_PH, o, v, v, o);
+    b.pair_gemm(J, YC, xc, 0, Mph, 0, -0.5, 0.0, "YC");
     b.perm(J, YC, Ix, {3, 2, 0, 1}, 1.0, 0.0, "WCx");
     b.pair_gemm(J, Zc, YC, 0, Tc, 0, 1.0, 0.0, "ring C quad");  // ring C quad + C'
   }
@@ -926,6 +926,8 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
     T4 Ib = b.t4(AR_SCR, LK_CH, v, o, v, o);  // (a,k,c,i)
     chem(J, Ib, dLvv, v, v, tLoo, o, o, AR_SCR, AR_FIX, 1.0, "(ac|ki)' a");
     chem(J, Ib, tLvv, v, v, dLoo, o, o, AR_FIX, AR_SCR, 1.0, "(ac|ki)' b");
+    T4 YD = b.t4(AR_SCR, LK_PH, o, v, v, o);
+    b.pair_gemm(J, YD, Ud, 0, MLph, 0, 0.5, 0.0, "YD");
     b.perm(J, YD, Ia, {2, 3, 0, 1}, 2.0, 0.0, "WDx a");
     b.perm(J, YD, Ib, {2, 3, 1, 0}, -1.0, 0.0, "WDx b");
     b.pair_gemm(J, Zd, YD, 0, ud, 0, 0.5, 0.0, "ring D quad");  // ring D quad + D'

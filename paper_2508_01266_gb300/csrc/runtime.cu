@@ -144,12 +144,19 @@ lrcc_status Runtime::init(const lrcc_dims& d, int64_t ws_budget) {
 
 bool Runtime::use_packed(const Gemm& g) const { return g.M >= 96 && g.N >= 96 && g.K >= 16; }
 
-// The unpacked tensor-core tile is 128 x 64 complex with K in steps of 16: below 15%
-// useful work per tile the FP64 kernel (small tiles) is used instead.
+// Useful fraction of the unpacked tensor-core tiles (128 x 64 complex, K in steps of 16)
+// for an M x N x K GEMM.
+static double tc_eff(long long M, long long N, long long K) {
+  const double tm = (double)((M + 127) / 128) * 128, tn = (double)((N + 63) / 64) * 64;
+  const double tk = (double)((K + 15) / 16) * 16;
+  return (double)M * N * K / (tm * tn * tk);
+}
+// Launch the tensor-core GEMM as C^T = B^T A^T when that fills its tiles better (small M).
+static bool tc_swap(const Gemm& g) { return tc_eff(g.N, g.M, g.K) > tc_eff(g.M, g.N, g.K); }
+// Mixed precision uses the tensor cores unless even the better orientation leaves under
+// 0.4 % of the tile useful (a few sub-tile GEMMs, cheap on the FP64 kernel).
 static bool tc_tile_useful(const Gemm& g) {
-  const double tm = (double)((g.M + 127) / 128) * 128, tn = (double)((g.N + 63) / 64) * 64;
-  const double tk = (double)((g.K + 15) / 16) * 16;
-  return (double)g.M * g.N * g.K / (tm * tn * tk) >= 0.15;
+  return std::max(tc_eff(g.M, g.N, g.K), tc_eff(g.N, g.M, g.K)) >= 0.004;
 }
 
 // Split-K factor: enough CTAs to fill the 152 SMs a few times over when the output
@@ -161,7 +168,9 @@ int Runtime::pick_split(const Gemm& g, const GemmDesc& d, int nr, bool tc) const
   if (no_split) return 1;
   int bm = 128, bn = 64;
   if (!tc) gemm_tile_dims(d.tile, &bm, &bn);
-  const long long tiles = (long long)((g.M + bm - 1) / bm) * ((g.N + bn - 1) / bn) * g.nbatch();
+  const bool sw = tc && tc_swap(g);
+  const long long LM = sw ? g.N : g.M, LN = sw ? g.M : g.N;
+  const long long tiles = ((LM + bm - 1) / bm) * ((LN + bn - 1) / bn) * g.nbatch();
   const long long target = tc ? 152LL * 3 : 152LL * 6;
   if (tiles >= target) return 1;
   const int bk = tc ? TC_BK : F64_BK;
@@ -337,7 +346,28 @@ lrcc_status Runtime::launch_gemm(GemmArgs a, const Gemm& g, const GemmChoice& c,
     }
     a.part = part;
   }
-  cudaError_t e = (c.tc && prec > 0) ? launch_gemm_tc(a, prec, nr, dflag, st) : launch_gemm_f64(a, c.tile, nr, st);
+  cudaError_t e;
+  if (c.tc && prec > 0) {
+    GemmArgs b = a;
+    if (tc_swap(g)) {  // C^T = B^T A^T: operands, transposes, leading dimensions and M, N swap
+      b.swap = 1;
+      b.M = a.N;
+      b.N = a.M;
+      b.A = a.B;
+      b.B = a.A;
+      b.sA = a.sB;
+      b.sB = a.sA;
+      b.aoff = a.boff;
+      b.boff = a.aoff;
+      b.lda = a.ldb;
+      b.ldb = a.lda;
+      b.ta = !a.tb;
+      b.tb = !a.ta;
+    }
+    e = launch_gemm_tc(b, prec, nr, dflag, st);
+  } else {
+    e = launch_gemm_f64(a, c.tile, nr, st);
+  }
   ++launches;
   if (e == cudaSuccess && a.nsplit > 1) {
     e = launch_split_reduce(a, nr, st);
