@@ -195,6 +195,34 @@ def _fixed_elems(lr, nk, o, v, Q):
     return int(ar[0])
 
 
+def alpha_wall_time(lr):
+    """alpha(w) wall time on the C1 workload (Nk=3, nocc=4, nvir=16, naux=48; alpha_zz at
+    w = 0 and 0.1 Ha), everything on the GPU: integrals in, CCSD T and Lambda solved
+    (lrcc_solve_ground_state), alpha to host (lrcc_polarizability); FP64 and BF16x3 with
+    FP64 refinement.  Times are host wall clock from the first ABI call to alpha on host."""
+    from synth import make_problem, CONFIGS
+    c = CONFIGS["c1"]
+    nk, o, v, Q = c["nk"], c["nocc"], c["nvir"], c["naux"]
+    p = make_problem(nk, o, v, Q, seed=1266)
+    out = {"workload": f"c1: Nk={nk} nocc={o} nvir={v} naux={Q}, alpha_zz at omega in {{0, 0.1}} Ha"}
+    for name, prec in (("fp64", 0), ("bf16x3", 2)):
+        t0 = time.perf_counter()
+        prob = lr.Problem(nk, o, v, Q)
+        prob.set_integrals(p.L, p.eps, p.dip)
+        *_, e, ginfo = prob.solve_ground_state(lr.default_options(conv_tol=1e-10, max_iter=300))
+        t1 = time.perf_counter()
+        a, info = prob.polarizability([2], [0.0, 0.1], lr.default_options(precision=prec, conv_tol=1e-10,
+                                                                         refine_tol=1e-8, max_iter=300))
+        t2 = time.perf_counter()
+        prob.close()
+        out[name] = {"seconds": t2 - t0, "ground_state_seconds": t1 - t0, "response_seconds": t2 - t1,
+                     "alpha_zz": [float(x.real) for x in a[:, 0, 0]], "ccsd_energy_per_cell": e,
+                     "iterations": {"ccsd": int(ginfo[0]), "lambda": int(ginfo[2]), "response": int(info[0])}}
+    out["max_abs_diff_bf16x3_vs_fp64"] = max(abs(x - y) for x, y in zip(out["fp64"]["alpha_zz"],
+                                                                           out["bf16x3"]["alpha_zz"]))
+    return out
+
+
 def time_mixed(lr, prob, X1, X2, Y1, Y2, args, st, dist, products):
     """Time the tensor-core products (BF16x3 and TF32) on the same vectors; Y1/Y2 are the
     FP64 results (None: no error column)."""
@@ -247,6 +275,7 @@ def main():
     ap.add_argument("--ref-blocks", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-alpha", action="store_true", help="skip the alpha wall-time measurement")
     ap.add_argument("--mixed-only", action="store_true",
                     help="time only the tensor-core (mixed precision) products (profiling runs)")
     ap.add_argument("--shape", default="",
@@ -365,6 +394,10 @@ def main():
     # mixed precision: the same product with the GEMMs on tcgen05 (BF16x3 and TF32, FP32 accumulate)
     mixed = {} if args.no_mixed else time_mixed(lr, prob, X1, X2, Y1, Y2, args, st, dist, products)
 
+    alpha = None
+    if rank == 0 and not args.no_alpha:
+        alpha = alpha_wall_time(lr)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         r, dt, threads, sample = cpu_oracle_rate(cfg, args.ref_blocks)
@@ -381,7 +414,7 @@ def main():
                            "l2": (f"working set larger than L2 (vector {16 * nk**3 * o * o * v * v / 1e6:.0f} MB, "
                                   f"fixed intermediates {prob_fixed_gb:.1f} GB); no flush")},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "mixed_precision": mixed,
+                "mixed_precision": mixed, "alpha_wall_time": alpha,
                 "clocks": clk}
         print(json.dumps(line), flush=True)
     prob.close()

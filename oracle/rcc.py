@@ -555,6 +555,69 @@ def polarizability_left(R: RCC, t1, t2, l1, l2, mus, omegas, tol=1e-11):
     return 0.5 * (out + out.transpose(0, 2, 1)), out
 
 
+def symmetric_basis(R: RCC):
+    """Orthonormal basis of the amplitude space with pair-symmetric doubles: singles unit
+    vectors, then one vector per orbit of the pair swap (ki,kj,ka,i,j,a,b) -> (kj,ki,kb,j,i,b,a):
+    e_p for fixed points, (e_p + e_Sp)/sqrt 2 otherwise.  Returned as index lists."""
+    nk, o, v = R.nk, R.o, R.v
+    n1 = nk * o * v
+    shape2 = (nk, nk, nk, o, o, v, v)
+    seen = np.zeros(shape2, dtype=bool)
+    pairs = []
+    for idx in np.ndindex(*shape2):
+        if seen[idx]:
+            continue
+        ki, kj, ka, i, j, a, b = idx
+        sw = (kj, ki, R.kb(ki, kj, ka), j, i, b, a)
+        seen[idx] = True
+        seen[sw] = True
+        pairs.append((idx, sw if sw != idx else None))
+    return n1, shape2, pairs
+
+
+def jacobian_matrix(R: RCC, t1, t2):
+    """Dense Jacobian on the pair-symmetric subspace in the orthonormal basis of
+    symmetric_basis (supercell units; columns are A applied to the basis vectors).
+    Its eigenvalues are the linear-response excitation energies (poles of Eq. 15)."""
+    n1, shape2, pairs = symmetric_basis(R)
+    dim = n1 + len(pairs)
+    s1 = (R.nk, R.o, R.v)
+    A = np.zeros((dim, dim), dtype=np.complex128)
+
+    def vec(c):
+        x1 = np.zeros(s1, dtype=np.complex128)
+        x2 = np.zeros(shape2, dtype=np.complex128)
+        if c < n1:
+            x1.reshape(-1)[c] = 1.0
+        else:
+            p, q = pairs[c - n1]
+            if q is None:
+                x2[p] = 1.0
+            else:
+                x2[p] = x2[q] = 1.0 / np.sqrt(2.0)
+        return x1, x2
+
+    def coords(y1, y2):
+        out = np.zeros(dim, dtype=np.complex128)
+        out[:n1] = y1.reshape(-1)
+        for r, (p, q) in enumerate(pairs):
+            out[n1 + r] = y2[p] if q is None else (y2[p] + y2[q]) / np.sqrt(2.0)
+        return out
+
+    for c in range(dim):
+        x1, x2 = vec(c)
+        y1, y2 = R.jacobian(t1, t2, torch.as_tensor(x1), torch.as_tensor(x2))
+        A[:, c] = coords(y1.numpy(), y2.numpy())
+    return A
+
+
+def excitation_energies(R: RCC, t1, t2, nroots=None):
+    """Eigenvalues of the Jacobian (LR-CCSD excitation energies), sorted by real part."""
+    w = np.linalg.eigvals(jacobian_matrix(R, t1, t2))
+    w = w[np.argsort(w.real)]
+    return w if nroots is None else w[:nroots]
+
+
 def dipole_ops(prob, comps=(0, 1, 2)):
     """k-diagonal dipole matrices mu[k,p,q] for the chosen components."""
     return [_t(prob.dip[c]) for c in comps]

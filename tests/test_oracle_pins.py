@@ -219,6 +219,37 @@ def test_eta_and_F_vectors_match_scalar_stencils():
     assert abs(complex((f1 * w1).sum() + (f2 * w2).sum()) - ref) < 1e-9 * abs(ref)
 
 
+# excitation energies (Jacobian eigenvalues) -------------------------------------
+@pytest.mark.parametrize("tr", [True, False])
+def test_excitation_energies_are_fci_two_electrons(tr):
+    """Two electrons: CCSD is exact, so every eigenvalue of its Jacobian on the
+    closed-shell space is an FCI excitation energy."""
+    p = make_problem(1, 1, 3, 4, seed=61, sigma_l=0.15, tr=tr)
+    R = rcc.RCC(p)
+    S = spinorb.SpinOrbitalSystem(p)
+    t1, t2, _ = rcc.solve_ccsd(R, tol=1e-12)
+    w = rcc.excitation_energies(R, t1, t2)
+    _, e, _ = fci.fci_states(S)
+    ex = e[1:] - e[0]
+    assert np.abs(w.imag).max() < 1e-9
+    for x in w.real:
+        assert np.abs(ex - x).min() < 1e-9
+
+
+def test_excitation_energies_replicas():
+    """Decoupled replicas: every excitation energy of one cell is also one of the
+    two-cell chain (the replicated excitation at zero crystal momentum)."""
+    p1 = make_problem(1, 1, 2, 3, seed=62, sigma_l=0.2, kind="replica")
+    p2 = make_problem(2, 1, 2, 3, seed=62, sigma_l=0.2, kind="replica")
+    w = []
+    for p in (p1, p2):
+        R = rcc.RCC(p)
+        t1, t2, _ = rcc.solve_ccsd(R, tol=1e-12)
+        w.append(rcc.excitation_energies(R, t1, t2))
+    for x in w[0]:
+        assert np.abs(w[1] - x).min() < 1e-9
+
+
 # P5 ---------------------------------------------------------------------------
 def test_decoupled_replicas_independent_of_nk():
     vals = []
