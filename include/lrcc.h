@@ -156,6 +156,17 @@ lrcc_status lrcc_residual(lrcc_problem* p, const void* t1, const void* t2, void*
 lrcc_status lrcc_solve_ground_state(lrcc_problem* p, const lrcc_options* opt, void* t1, void* t2, void* l1,
                                     void* l2, int32_t on_device, double* energy, int32_t* info);
 
+/* Linear-response excitation energies (the poles of the response function, Eq. 15):
+ * the nroots eigenvalues of the Jacobian with the smallest real parts, by a non-Hermitian
+ * Davidson iteration on batched Jacobian products (orbital-energy denominator
+ * preconditioner; converged when every wanted residual norm <= opt->conv_tol; products
+ * in opt->precision).  omegas: host c128 [nroots].  x1, x2 (each may be NULL): device
+ * c128 [nroots][Nk][o][v] and [nroots][Nk][Nk][Nk][o][o][v][v] right eigenvectors in
+ * paper units, unit Hermitian norm.  info (may be NULL): int32 [2] = iterations,
+ * status.  Requires set_ground_state; 1 <= nroots <= Nk o v.  Synchronous. */
+lrcc_status lrcc_excitation_energies(lrcc_problem* p, int32_t nroots, const lrcc_options* opt, void* omegas,
+                                     void* x1, void* x2, int32_t* info);
+
 /* Polarizabilities of several independent problems (for example chains of different
  * Nk, o, v) in one call, all with the same components, frequencies and options.  Each
  * problem's solve runs on its own host thread and that thread's default stream, so
@@ -229,6 +240,13 @@ lrcc_status lrcc_plan_btrans(const lrcc_plan* h, int32_t idx, int32_t* ints, int
  * right-hand side's copy of the arena.  Scratch buffers whose lifetimes do not overlap
  * share memory; each starts its lifetime with such an op. */
 lrcc_status lrcc_plan_zero(const lrcc_plan* h, int32_t idx, int32_t* arena, int64_t* off_n);
+
+/* Host-only utility: eigenvalues w (c128 [n]) and unit right eigenvectors v (c128
+ * [n][n], row-major, columns are the vectors; may be NULL) of the row-major complex
+ * n x n matrix a (Hessenberg reduction and shifted QR).  It solves the Davidson subspace
+ * problem of lrcc_excitation_energies and is exported for tests.  LRCC_ENOCONV if the
+ * iteration fails. */
+lrcc_status lrcc_small_eig(int32_t n, const void* a, void* w, void* v);
 
 #ifdef __cplusplus
 }

@@ -15,7 +15,7 @@ from ._lib import lib, lrcc_dims, lrcc_options, STATUS, LIB_PATH
 
 __all__ = ["LrccError", "Problem", "default_options", "create", "set_integrals", "set_ground_state",
            "jacobian_apply", "polarizability", "last_error", "destroy", "kernel_launches", "profile",
-           "profile_query", "profile_report", "batch_polarizability", "residual", "solve_ground_state", "LRCCJacobian", "jacobian", "LIB_PATH"]
+           "profile_query", "profile_report", "batch_polarizability", "residual", "solve_ground_state", "excitation_energies", "LRCCJacobian", "jacobian", "LIB_PATH"]
 
 
 class LrccError(RuntimeError):
@@ -171,6 +171,23 @@ def solve_ground_state(h, nk, nocc, nvir, options=None):
     return t1, t2, l1, l2, e.value, info
 
 
+def excitation_energies(h, nroots, nk, nocc, nvir, options=None, vectors=False):
+    """Lowest nroots LR excitation energies (complex; Jacobian eigenvalues) and, if
+    vectors, the right eigenvectors (CUDA tensors, paper units).  Returns (omegas, x1, x2, info)."""
+    om = np.zeros(nroots, dtype=np.complex128)
+    info = np.zeros(2, dtype=np.int32)
+    x1 = x2 = None
+    if vectors:
+        dev = torch.device("cuda")
+        x1 = torch.empty((nroots, nk, nocc, nvir), dtype=torch.complex128, device=dev)
+        x2 = torch.empty((nroots, nk, nk, nk, nocc, nocc, nvir, nvir), dtype=torch.complex128, device=dev)
+    opt = options if options is not None else default_options()
+    _check(lib.lrcc_excitation_energies(h, nroots, C.byref(opt), C.c_void_p(om.ctypes.data),
+                                        _ptr(x1) if vectors else None, _ptr(x2) if vectors else None,
+                                        info.ctypes.data_as(C.POINTER(C.c_int32))), h)
+    return om, x1, x2, info
+
+
 def batch_polarizability(problems, comps, omegas, options=None):
     """alpha for several independent problems in one call (one host thread and stream
     each); returns a list of (alpha, info) in the order of `problems`."""
@@ -215,6 +232,9 @@ class Problem:
 
     def solve_ground_state(self, options=None):
         return solve_ground_state(self.h, self.nk, self.nocc, self.nvir, options)
+
+    def excitation_energies(self, nroots, options=None, vectors=False):
+        return excitation_energies(self.h, nroots, self.nk, self.nocc, self.nvir, options, vectors)
 
     def profile(self, enable=True):
         profile(self.h, enable)

@@ -49,6 +49,8 @@ _SIGS = {
     "lrcc_residual": (C.c_int, [VP, VP, VP, VP, VP]),
     "lrcc_solve_ground_state": (C.c_int, [VP, C.POINTER(lrcc_options), VP, VP, VP, VP, C.c_int32,
                                           C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "lrcc_excitation_energies": (C.c_int, [VP, C.c_int32, C.POINTER(lrcc_options), VP, VP, VP,
+                                           C.POINTER(C.c_int32)]),
     "lrcc_batch_polarizability": (C.c_int, [C.POINTER(VP), C.c_int32, C.POINTER(C.c_int32), C.c_int32,
                                             C.POINTER(C.c_double), C.c_int32, C.POINTER(lrcc_options),
                                             C.POINTER(VP), C.POINTER(VP)]),
@@ -62,6 +64,7 @@ _SIGS = {
     "lrcc_plan_perm": (C.c_int, [VP, C.c_int32, VP, VP, VP]),
     "lrcc_plan_btrans": (C.c_int, [VP, C.c_int32, VP, VP, VP]),
     "lrcc_plan_zero": (C.c_int, [VP, C.c_int32, VP, VP]),
+    "lrcc_small_eig": (C.c_int, [C.c_int32, VP, VP, VP]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)

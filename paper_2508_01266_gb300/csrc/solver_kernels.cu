@@ -221,4 +221,22 @@ cudaError_t launch_axpby(double2 a, const double2* x, double2 b, double2* y, lon
   return cudaGetLastError();
 }
 
+// Davidson correction: out = -r / (den - theta), theta complex (one vector)
+__global__ void precond_kernel(const double2* r, const double* den, double2 theta, double2* out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double dr = den[i] - theta.x, di = -theta.y;
+    double q = dr * dr + di * di;
+    if (q < 1e-24) q = 1e-24;  // the shift sits on a denominator: keep the correction finite
+    const double2 v = r[i];
+    // -(v / (dr + i di)) = -(v (dr - i di)) / q
+    out[i] = make_double2(-(v.x * dr + v.y * di) / q, -(v.y * dr - v.x * di) / q);
+  }
+}
+
+cudaError_t launch_precond(const double2* r, const double* den, double2 theta, double2* out, long long n,
+                           cudaStream_t st) {
+  precond_kernel<<<grid_for(n, 256 * 4), 256, 0, st>>>(r, den, theta, out, n);
+  return cudaGetLastError();
+}
+
 }  // namespace lrcc

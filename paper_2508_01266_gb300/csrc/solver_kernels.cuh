@@ -21,5 +21,7 @@ cudaError_t launch_dots(const double2* const* a, const double2* const* b, int co
 cudaError_t launch_lincomb(const double2* const* v, const double2* c, int m, double2* out, long long n,
                            long long stride, int nrhs, cudaStream_t st);
 cudaError_t launch_axpby(double2 a, const double2* x, double2 b, double2* y, long long n, cudaStream_t st);
+cudaError_t launch_precond(const double2* r, const double* den, double2 theta, double2* out, long long n,
+                           cudaStream_t st);
 
 }  // namespace lrcc
