@@ -667,44 +667,61 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
   P.ws_limit = per_chunk;
   P.arena_size[AR_WS] = per_chunk * wblk_max;
   // ladder over chunks: build (fixed-only) then contract.  Rows: all (ki,i,j) of the PP matrix.
+  // half: the caller symmetrises the result over the pair swap (i,j,a,b) -> (j,i,b,a)
+  // (momenta swapped too) and the product is pair-symmetric (X and W are), so only the
+  // output column blocks ka with ka <= kb = P - ka are computed: ka < kb at twice the
+  // weight (the swap supplies block kb), the self-paired block ka = kb at the weight
+  // itself.  W blocks are built for those ka only.
   auto ladder = [&](Program& pr, const T4& Cpp, int64_t Afac, int na, const T4& Xpp, double alpha,
-                    const char* tag, double* flop_acc, double* build_acc) {
+                    const char* tag, double* flop_acc, double* build_acc, bool half) {
     // Cpp: logical (i,j,a,b) with a in [0,na); Xpp: logical (i,j,c,d)
     const int64_t rowsX = (int64_t)nk * o2, colsX = (int64_t)nk * v2;
     const int64_t colsC = (int64_t)nk * na * v;
     const int64_t wsz = (int64_t)na * v * v2;
-    for (size_t c0 = 0; c0 < tris.size(); c0 += per_chunk) {
-      size_t c1 = std::min(tris.size(), c0 + (size_t)per_chunk);
+    std::vector<Tri> work;
+    for (const Tri& t : tris) {
+      const int kbb = md(t.P - t.ka, nk);
+      if (!half || t.ka <= kbb) work.push_back(t);
+    }
+    for (size_t c0 = 0; c0 < work.size(); c0 += per_chunk) {
+      size_t c1 = std::min(work.size(), c0 + (size_t)per_chunk);
       Gemm& g = b.g_new(na * v, (int)v2, Q, 1, 0, (int64_t)na * v, v2, 0, AR_FIX, AR_FIX, AR_WS, 1.0, 0.0,
                         "W build");
       g.epi = 1;
       g.ep[0] = na; g.ep[1] = v; g.ep[2] = v; g.ep[3] = v;
       for (size_t t = c0; t < c1; ++t) {
-        const Tri& tr = tris[t];
+        const Tri& tr = work[t];
         int kbb = md(tr.P - tr.ka, nk), kd = md(tr.P - tr.kc, nk);
         B::batch(g, (int64_t)(t - c0) * wsz);
         B::seg(g, DF(Afac, na, v, tr.ka, tr.kc), DF(tLvv, v, v, kbb, kd));
       }
       if (build_acc) *build_acc += (double)g.flops();
       b.g_push(pr);
-      // contraction: C_P[:, ka] += alpha X_P[:, kc] W^T, grouped by (P, ka)
-      Gemm& h = b.g_new((int)rowsX, na * v, (int)v2, 0, 1, colsX, v2, colsC, Xpp.ar, AR_WS, Cpp.ar, alpha,
-                        0.0, tag);
+      // contraction: C_P[:, ka] += alpha X_P[:, kc] W^T, grouped by (P, ka); with half, the
+      // self-paired blocks and the others go to separate ops (different weights)
       std::map<std::pair<int, int>, std::vector<size_t>> grp;
-      for (size_t t = c0; t < c1; ++t) grp[{tris[t].P, tris[t].ka}].push_back(t);
-      for (auto& kv : grp) {
-        int Pm = kv.first.first, ka = kv.first.second;
-        B::batch(h, Cpp.off + (int64_t)Pm * rowsX * colsC + (int64_t)ka * na * v);
-        for (size_t t : kv.second)
-          B::seg(h, Xpp.off + (int64_t)Pm * rowsX * colsX + (int64_t)tris[t].kc * v2, (int64_t)(t - c0) * wsz);
+      for (size_t t = c0; t < c1; ++t) grp[{work[t].P, work[t].ka}].push_back(t);
+      for (int self = 0; self < (half ? 2 : 1); ++self) {
+        bool any = false;
+        for (auto& kv : grp) any = any || !half || ((md(kv.first.first - kv.first.second, nk) == kv.first.second) == (self == 1));
+        if (!any) continue;
+        const double a = half && self == 0 ? 2.0 * alpha : alpha;
+        Gemm& h = b.g_new((int)rowsX, na * v, (int)v2, 0, 1, colsX, v2, colsC, Xpp.ar, AR_WS, Cpp.ar, a, 0.0, tag);
+        for (auto& kv : grp) {
+          int Pm = kv.first.first, ka = kv.first.second;
+          if (half && ((md(Pm - ka, nk) == ka) != (self == 1))) continue;
+          B::batch(h, Cpp.off + (int64_t)Pm * rowsX * colsC + (int64_t)ka * na * v);
+          for (size_t t : kv.second)
+            B::seg(h, Xpp.off + (int64_t)Pm * rowsX * colsX + (int64_t)work[t].kc * v2, (int64_t)(t - c0) * wsz);
+        }
+        if (flop_acc) *flop_acc += (double)h.flops();
+        b.g_push(pr);
       }
-      if (flop_acc) *flop_acc += (double)h.flops();
-      b.g_push(pr);
     }
   };
   // Z(i,j,m,b) = sum_cd t_ij^cd (mc|bd)~   (PP), then K3
   T4 Zpp = b.t4(AR_FIX, LK_PP, o, o, o, v);
-  ladder(G, Zpp, Lov, o, Tpp, 1.0, "Z ladder", nullptr, nullptr);
+  ladder(G, Zpp, Lov, o, Tpp, 1.0, "Z ladder", nullptr, nullptr, false);
   T4 Zk3 = b.relayout(Zpp, AR_FIX, LK_K3);
   b.perm(G, Zk3, Zpp, {0, 1, 2, 3}, 1.0, 0.0, "Zk3");
 
@@ -742,7 +759,7 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
   T4 Zd = b.t4(AR_SCR, LK_PH, o, o, v, v);    // ring D product
 
   // [A] ladder
-  ladder(J, rpp, tLvv, v, xpp, 0.5, "ladder", &P.ladder_flops, &P.wbuild_flops);
+  ladder(J, rpp, tLvv, v, xpp, 0.5, "ladder", &P.ladder_flops, &P.wbuild_flops, true);
   // [B] hole-hole: rpp += 1/2 Whh^T xpp ; Yhh = V xpp^T ; rpp += 1/2 Yhh^T Tpp.  The last
   //     product shares its right factor with B': Yhh is formed in (13), collects both
   //     left factors, and one GEMM ("hh quad") applies Tpp.
