@@ -68,6 +68,8 @@ typedef struct {
   int32_t response_form; /* lrcc_polarizability: 0 symmetric form (default); 1 asymmetric
                             (left-response) form, symmetrised (alpha_XY + alpha_YX) / 2;
                             2 asymmetric form as computed */
+  const char* log_path;  /* NULL (default) or a file the iterative solvers append one JSON line
+                            per iteration to: solver, iteration, residuals per system */
 } lrcc_options;
 
 /* ---------------------------------------------------------------------------
@@ -240,6 +242,13 @@ lrcc_status lrcc_plan_btrans(const lrcc_plan* h, int32_t idx, int32_t* ints, int
  * right-hand side's copy of the arena.  Scratch buffers whose lifetimes do not overlap
  * share memory; each starts its lifetime with such an op. */
 lrcc_status lrcc_plan_zero(const lrcc_plan* h, int32_t idx, int32_t* arena, int64_t* off_n);
+
+/* Self test of the bounded device waits: launches one thread that waits on an mbarrier
+ * nothing arrives at, for at most `polls` polls, then records the timeout in the
+ * problem's device error flag (the mechanism every tensor-core kernel uses when a copy
+ * or an MMA never completes).  Returns LRCC_ETIMEOUT after reading and clearing the flag;
+ * the context stays usable.  Synchronous. */
+lrcc_status lrcc_wait_selftest(lrcc_problem* p, int64_t polls);
 
 /* Host-only utility: eigenvalues w (c128 [n]) and unit right eigenvectors v (c128
  * [n][n], row-major, columns are the vectors; may be NULL) of the row-major complex

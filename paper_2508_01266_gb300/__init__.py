@@ -34,7 +34,7 @@ def default_options(**kw) -> lrcc_options:
     o = lrcc_options()
     lib.lrcc_default_options(C.byref(o))
     for k, v in kw.items():
-        setattr(o, k, v)
+        setattr(o, k, v.encode() if k == "log_path" and isinstance(v, str) else v)
     return o
 
 

@@ -27,7 +27,7 @@ class lrcc_options(C.Structure):
     _fields_ = [("conv_tol", C.c_double), ("refine_tol", C.c_double), ("max_iter", C.c_int32),
                 ("diis_depth", C.c_int32), ("diis_period", C.c_int32), ("precision", C.c_int32),
                 ("autotune", C.c_int32), ("use_graphs", C.c_int32), ("spin_timeout_cycles", C.c_uint64),
-                ("response_form", C.c_int32)]
+                ("response_form", C.c_int32), ("log_path", C.c_char_p)]
 
 
 VP = C.c_void_p
@@ -65,6 +65,7 @@ _SIGS = {
     "lrcc_plan_btrans": (C.c_int, [VP, C.c_int32, VP, VP, VP]),
     "lrcc_plan_zero": (C.c_int, [VP, C.c_int32, VP, VP]),
     "lrcc_small_eig": (C.c_int, [C.c_int32, VP, VP, VP]),
+    "lrcc_wait_selftest": (C.c_int, [VP, C.c_int64]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)

@@ -33,6 +33,7 @@ extern "C" lrcc_status lrcc_excitation_energies(lrcc_problem* p, int32_t nroots,
   }
   const int nk = rt.dims.nk, o = rt.dims.nocc, v = rt.dims.nvir, n = o + v;
   const long long n1 = (long long)nk * o * v;
+  const long long n2 = (long long)nk * nk * nk * o * o * v * v;
   if (nroots < 1 || nroots > n1 || !omegas) {
     rt.err = "excitation_energies: nroots must be in [1, Nk o v] and omegas non-null";
     return LRCC_EINVAL;
@@ -188,6 +189,7 @@ extern "C" lrcc_status lrcc_excitation_energies(lrcc_problem* p, int32_t nroots,
       if ((s = norm(R + (size_t)r * vec, rnorm[r])) != LRCC_OK) return s;
       worst = std::max(worst, rnorm[r]);
     }
+    log_iteration(opt, "davidson", it, rnorm);
     if (m >= nroots && worst <= tol) {
       conv = true;
       break;
@@ -240,9 +242,31 @@ extern "C" lrcc_status lrcc_excitation_energies(lrcc_problem* p, int32_t nroots,
     for (int r = 0; r < nroots && m + knew < mmax; ++r) {
       if (rnorm[r] <= tol) continue;
       double2* t = Vp(m + knew);
-      CK(launch_precond(R + (size_t)r * vec, bs.DEN, make_double2(theta[r].real(), theta[r].imag()), t, vec, st),
+      CK(launch_precond(R + (size_t)r * vec, bs.DEN, make_double2(theta[r].real(), theta[r].imag()), TMP, vec, st),
          "precond");
       rt.launches++;
+      // keep the search space pair-symmetric: t2 <- (t2 + S t2) / 2.  The Jacobian
+      // symmetrises its input, so rounding residue in the antisymmetric part would
+      // otherwise surface as spurious zero eigenvalues.
+      CK(cudaMemcpyAsync(t, TMP, vec * sizeof(double2), cudaMemcpyDeviceToDevice, st), "copy");
+      CK(cudaMemsetAsync(t + P.off_x2, 0, n2 * sizeof(double2), st), "memset");
+      for (int sw = 0; sw < 2; ++sw) {
+        PermArgs pa;
+        pa.skind = pa.dkind = LK_K3;
+        pa.snk = pa.dnk = nk;
+        const int dn[4] = {o, o, v, v};
+        for (int i = 0; i < 4; ++i) pa.sn[i] = pa.dn[i] = dn[i];
+        const int id[4] = {0, 1, 2, 3}, swp[4] = {1, 0, 3, 2};
+        for (int i = 0; i < 4; ++i) pa.pi[i] = sw ? swp[i] : id[i];
+        pa.total = (long long)n2;
+        pa.S = TMP + P.off_x2;
+        pa.D = t + P.off_x2;
+        pa.sS = pa.sD = 0;
+        pa.ar = 0.5;
+        pa.ai = 0.0;
+        CK(launch_perm_f64(pa, 1, st), "symmetrise");
+        rt.launches++;
+      }
       double kept = 0.0;
       if ((s = orthonormalize(t, TMP, m + knew, kept)) != LRCC_OK) return s;
       if (kept > 1e-6) ++knew;
@@ -261,7 +285,7 @@ extern "C" lrcc_status lrcc_excitation_energies(lrcc_problem* p, int32_t nroots,
   // right eigenvectors (paper units), unit Hermitian norm
   if ((x1 || x2) && conv) {
     const size_t b1 = (size_t)n1 * sizeof(double2);
-    const size_t b2 = (size_t)nk * nk * nk * o * o * v * v * sizeof(double2);
+    const size_t b2 = (size_t)n2 * sizeof(double2);
     for (int r = 0; r < nroots; ++r) {
       std::vector<const double2*> xs;
       std::vector<cd> co;

@@ -200,6 +200,7 @@ lrcc_status lrcc_solve_ground_state(lrcc_problem* p, const lrcc_options* optp, v
     unsigned long long hr = 0;
     CK(cudaMemcpy(&hr, bs.RMAX, sizeof(hr), cudaMemcpyDeviceToHost), "rmax");
     err = u64_to_double(hr);
+    log_iteration(opt, "ccsd", it, {err});
     if (err <= opt.conv_tol) {
       conv = true;
       break;

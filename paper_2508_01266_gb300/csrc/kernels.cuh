@@ -68,6 +68,7 @@ cudaError_t launch_btrans_f64(const BTransArgs& t, int nrhs, cudaStream_t st);
 // FP64 kernel, FP32 accumulation.  *errflag is set when a bounded wait gives up.
 cudaError_t launch_gemm_tc(const GemmArgs& g, int prec, int nrhs, int* errflag, cudaStream_t st);
 size_t tc_smem_bytes(int prec);
+cudaError_t launch_wait_selftest(long long polls, int* errflag, cudaStream_t st);
 
 // Packed-operand tensor-core GEMM (kernels_tcp.cu).
 struct PackArgs {

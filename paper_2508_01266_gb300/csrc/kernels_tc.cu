@@ -296,6 +296,30 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(GemmArgs g, int* er
   if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_NR));
 }
 
+// Bounded-wait self test: one thread waits on an mbarrier that nothing arrives at, gives
+// up after `polls` polls and records the timeout in the error flag, exactly as the GEMM
+// kernels do when a copy or an MMA never completes (no copies, MMAs or tensor memory
+// are involved, so giving up leaves nothing in flight).
+__global__ void wait_selftest_kernel(long long polls, int* errflag) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+  asm volatile("fence.mbarrier_init.release.cluster;");
+  uint32_t done = 0;
+  for (long long it = 0; it < polls && !done; ++it)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(&bar)), "r"(0u)
+        : "memory");
+  if (!done) atomicExch(errflag, 1);
+}
+
+cudaError_t launch_wait_selftest(long long polls, int* errflag, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(polls, errflag);
+  return cudaGetLastError();
+}
+
 size_t tc_smem_bytes(int prec) {
   const int EB = prec == 1 ? 4 : 2;
   const int NPL = prec == 1 ? 1 : 2;

@@ -695,6 +695,7 @@ void lrcc_default_options(lrcc_options* o) {
   o->use_graphs = 0;
   o->spin_timeout_cycles = 0;
   o->response_form = 0;
+  o->log_path = nullptr;
 }
 
 lrcc_status lrcc_create(const lrcc_dims* dims, lrcc_problem** out) {
@@ -735,6 +736,75 @@ lrcc_status lrcc_set_integrals(lrcc_problem* p, const void* L, const double* eps
   const Plan& P = rt.plan;
   const size_t Lbytes = (size_t)nk * nk * Q * n * n * sizeof(double2);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  // validation before anything is uploaded (a rejected call leaves the problem unchanged):
+  // finite values; DF factors Hermitian in (p,k1) <-> (q,k2), which the method's exchange
+  // symmetry of the integrals relies on (Sec. II.C); dipoles Hermitian per k; a gapped
+  // reference (every virtual above every occupied level), which the denominators of
+  // Eq. 9 need.
+  {
+    std::vector<double2> hl, hd;
+    const double2* Lh = (const double2*)L;
+    const double2* Dh = (const double2*)dip;
+    const double* Eh = eps;
+    std::vector<double> he;
+    const size_t nL = (size_t)nk * nk * Q * n * n, nD = (size_t)3 * nk * n * n;
+    if (on_device) {
+      hl.resize(nL);
+      hd.resize(nD);
+      he.resize((size_t)nk * n);
+      if (!rt.ck(cudaMemcpy(hl.data(), L, Lbytes, cudaMemcpyDeviceToHost), "cudaMemcpy(L to host)") ||
+          !rt.ck(cudaMemcpy(hd.data(), dip, nD * sizeof(double2), cudaMemcpyDeviceToHost), "cudaMemcpy(dip)") ||
+          !rt.ck(cudaMemcpy(he.data(), eps, he.size() * sizeof(double), cudaMemcpyDeviceToHost), "cudaMemcpy(eps)"))
+        return LRCC_ECUDA;
+      Lh = hl.data();
+      Dh = hd.data();
+      Eh = he.data();
+    }
+    double lmax = 0.0, lerr = 0.0;
+    for (size_t i = 0; i < nL; ++i) {
+      if (!std::isfinite(Lh[i].x) || !std::isfinite(Lh[i].y))
+        return fail(p, LRCC_EINVAL, "set_integrals: non-finite DF factor");
+      lmax = std::max(lmax, std::hypot(Lh[i].x, Lh[i].y));
+    }
+    auto li = [&](int k1, int k2, int q, int a, int b) { return (((size_t)k1 * nk + k2) * Q + q) * n * n + (size_t)a * n + b; };
+    for (int k1 = 0; k1 < nk; ++k1)
+      for (int k2 = 0; k2 < nk; ++k2)
+        for (int q = 0; q < Q; ++q)
+          for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) {
+              const double2 x = Lh[li(k1, k2, q, a, b)], y = Lh[li(k2, k1, q, b, a)];
+              lerr = std::max(lerr, std::hypot(x.x - y.x, x.y + y.y));
+            }
+    if (lerr > 1e-10 * std::max(lmax, 1e-300))
+      return fail(p, LRCC_EINVAL, "set_integrals: DF factors are not Hermitian (max |L(k2,k1)^H - L(k1,k2)| = " +
+                                      std::to_string(lerr) + ")");
+    double dmax = 0.0, derr = 0.0;
+    for (size_t i = 0; i < nD; ++i) {
+      if (!std::isfinite(Dh[i].x) || !std::isfinite(Dh[i].y))
+        return fail(p, LRCC_EINVAL, "set_integrals: non-finite dipole integral");
+      dmax = std::max(dmax, std::hypot(Dh[i].x, Dh[i].y));
+    }
+    for (int c = 0; c < 3; ++c)
+      for (int k = 0; k < nk; ++k)
+        for (int a = 0; a < n; ++a)
+          for (int b = 0; b < n; ++b) {
+            const double2 x = Dh[(((size_t)c * nk + k) * n + a) * n + b], y = Dh[(((size_t)c * nk + k) * n + b) * n + a];
+            derr = std::max(derr, std::hypot(x.x - y.x, x.y + y.y));
+          }
+    if (derr > 1e-10 * std::max(dmax, 1e-300))
+      return fail(p, LRCC_EINVAL, "set_integrals: dipole integrals are not Hermitian");
+    double occ_max = -1e300, vir_min = 1e300;
+    for (int k = 0; k < nk; ++k)
+      for (int q = 0; q < n; ++q) {
+        const double x = Eh[(size_t)k * n + q];
+        if (!std::isfinite(x)) return fail(p, LRCC_EINVAL, "set_integrals: non-finite orbital energy");
+        if (q < o) occ_max = std::max(occ_max, x);
+        else vir_min = std::min(vir_min, x);
+      }
+    if (!(vir_min > occ_max))
+      return fail(p, LRCC_EINVAL, "set_integrals: the reference is not gapped (lowest virtual energy not above "
+                                  "the highest occupied one)");
+  }
   double2* tmp = nullptr;
   if (!rt.ck(cudaMalloc(&tmp, Lbytes), "cudaMalloc(L staging)")) return LRCC_ENOMEM;
   lrcc_status st = LRCC_OK;
@@ -786,6 +856,24 @@ lrcc_status lrcc_set_ground_state(lrcc_problem* p, const void* t1, const void* t
   const Plan& P = rt.plan;
   const int nk = rt.dims.nk, o = rt.dims.nocc, v = rt.dims.nvir;
   const size_t n1 = (size_t)nk * o * v, n2 = (size_t)nk * nk * nk * o * o * v * v;
+  {  // finite amplitudes and multipliers (host data checked in place, device data copied)
+    const void* arrs[4] = {t1, t2, l1, l2};
+    const size_t cnt[4] = {n1, n2, n1, n2};
+    for (int a = 0; a < 4; ++a) {
+      if (!arrs[a]) continue;
+      std::vector<double2> h;
+      const double2* x = (const double2*)arrs[a];
+      if (on_device) {
+        h.resize(cnt[a]);
+        if (!rt.ck(cudaMemcpy(h.data(), arrs[a], cnt[a] * sizeof(double2), cudaMemcpyDeviceToHost), "validate"))
+          return LRCC_ECUDA;
+        x = h.data();
+      }
+      for (size_t i = 0; i < cnt[a]; ++i)
+        if (!std::isfinite(x[i].x) || !std::isfinite(x[i].y))
+          return fail(p, LRCC_EINVAL, "set_ground_state: non-finite amplitude or multiplier");
+    }
+  }
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (!rt.ck(cudaMemset(rt.fix + P.off_derived, 0, (P.arena_size[AR_FIX] - P.off_derived) * sizeof(double2)),
              "cudaMemset(derived)") ||
@@ -885,6 +973,16 @@ lrcc_status lrcc_batch_polarizability(lrcc_problem* const* probs, int32_t nprob,
   for (int i = 0; i < nprob; ++i)
     if (st[i] != LRCC_OK) return st[i];
   return LRCC_OK;
+}
+
+lrcc_status lrcc_wait_selftest(lrcc_problem* p, int64_t polls) {
+  if (!p || polls < 1) return LRCC_EINVAL;
+  Runtime& rt = p->rt;
+  if (!rt.ck(launch_wait_selftest(polls, rt.dflag, cudaStreamLegacy), "wait self test")) return LRCC_ECUDA;
+  ++rt.launches;
+  const lrcc_status s = rt.read_flag(cudaStreamLegacy);
+  if (s == LRCC_ETIMEOUT) rt.err = "wait self test: the bounded wait gave up as intended";
+  return s;
 }
 
 int64_t lrcc_kernel_launches(const lrcc_problem* p) { return p ? p->rt.launches : -1; }

@@ -16,6 +16,7 @@
 //     alpha_XY(w) = -<<X;Y>>_w / Nk (per cell).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <complex>
 #include <cstring>
 #include <vector>
@@ -66,6 +67,16 @@ double u64_to_double(unsigned long long u) {
   double d;
   std::memcpy(&d, &u, sizeof(d));
   return d;
+}
+
+void log_iteration(const lrcc_options& opt, const char* solver, int it, const std::vector<double>& res) {
+  if (!opt.log_path) return;
+  FILE* f = std::fopen(opt.log_path, "a");
+  if (!f) return;
+  std::fprintf(f, "{\"solver\": \"%s\", \"iter\": %d, \"residual\": [", solver, it);
+  for (size_t i = 0; i < res.size(); ++i) std::fprintf(f, "%s%.6e", i ? ", " : "", res[i]);
+  std::fprintf(f, "]}\n");
+  std::fclose(f);
 }
 
 BatchSolver::BatchSolver(Runtime& r, const lrcc_options& o, int nsys, int min_pairs) : rt(r), opt(o), ns(nsys) {
@@ -229,6 +240,9 @@ lrcc_status BatchSolver::jacobi_diis(int tr, const double2* rhs, const std::vect
       rel[i] = u64_to_double(hr[i]) / std::max(rhsmax[i], 1e-300);
       worst = std::max(worst, rel[i]);
     }
+    log_iteration(opt, tr ? (prec ? "jacobi_diis_transpose_mixed" : "jacobi_diis_transpose")
+                          : (prec ? "jacobi_diis_mixed" : "jacobi_diis"),
+                  it, rel);
     if (worst <= tol) {
       conv = true;
       return LRCC_OK;
@@ -279,6 +293,7 @@ lrcc_status BatchSolver::solve(int tr, const double2* rhs, const double* om, dou
       rel[i] = rmx[i] / std::max(rhsmax[i], 1e-300);
       worst = std::max(worst, rel[i]);
     }
+    log_iteration(opt, tr ? "refinement_transpose" : "refinement", outer, rel);
     if (worst <= tol64) {
       converged = true;
       break;

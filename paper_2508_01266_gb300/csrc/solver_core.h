@@ -63,4 +63,8 @@ struct BatchSolver {
 
 double u64_to_double(unsigned long long u);
 
+// One JSON line per solver iteration into opt.log_path (no-op when it is NULL):
+// {"solver": name, "iter": it, "residual": [per system]}.
+void log_iteration(const lrcc_options& opt, const char* solver, int it, const std::vector<double>& res);
+
 }  // namespace lrcc
