@@ -375,6 +375,14 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
   const int64_t o2 = (int64_t)o * o, v2 = (int64_t)v * v, ov = (int64_t)o * v;
   auto kb3 = [&](int k1, int k2, int k3) { return md(k1 + k2 - k3, nk); };
   const double sNk = (double)nk;
+  // layout extents and GEMM dimensions are 32-bit: the largest single extent is a whole
+  // DF factor or pair matrix dimension
+  {
+    const int64_t n64 = o + (int64_t)v;
+    const int64_t big = std::max({(int64_t)nk * nk * Q * n64 * n64, (int64_t)nk * v2 * nk, (int64_t)nk * nk * ov * Q,
+                                  (int64_t)nk * o2 * nk});
+    if (big > INT32_MAX) throw std::runtime_error("problem too large: an extent exceeds 2^31 elements");
+  }
 
   // ---------------- FIX inputs ----------------
   // DF factor blocks [k1][k2][Q][n1][n2] in supercell units (L / sqrt(Nk))

@@ -59,8 +59,11 @@ def test_rejected_inputs_leave_problem_usable(lr):
 
 def test_allocation_failure_is_reported(lr):
     with pytest.raises(lr.LrccError) as e:
-        lr.Problem(3, 40, 400, 2000)  # fixed arena of more than a terabyte
+        lr.Problem(9, 16, 100, 400)  # fixed arena of about 0.5 TB
     assert e.value.status == 2
+    with pytest.raises(lr.LrccError) as e:
+        lr.Problem(3, 40, 400, 2000)  # a single extent beyond 32-bit layout dimensions
+    assert e.value.status == 1 and "too large" in str(e.value)
     p, prob, X, ref = _small(lr)  # the context is still usable
     assert _same(prob, X, ref)
     prob.close()
