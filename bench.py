@@ -27,6 +27,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 pipe, nominal (profiling recipe table)
+# DRAM bytes (read + write) of one FP64 ladder-contraction launch of this workload (15 vectors),
+# from a one-pass ncu capture of this build's kernel (profiles/ladder_c2_fp64.md)
+LADDER_TRAFFIC_BYTES = 23.36e9 + 1.00e9
 
 
 def _dist():
@@ -384,8 +387,10 @@ def main():
     lad_per_launch_fl = lad_fl / max(lad_n, 1)
     lad_avg_ms = lad_ms / max(lad_n, 1)
     achieved = lad_per_launch_fl / (lad_avg_ms * 1e-3) / 1e9 if lad_n else None
+    default_workload = args.config == "c2" and not args.shape and nrhs == 15
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-            "frac": (achieved / FP64_NOMINAL_GFLOPS) if achieved else None, "traffic": None,
+            "frac": (achieved / FP64_NOMINAL_GFLOPS) if achieved else None,
+            "traffic": LADDER_TRAFFIC_BYTES if default_workload else None,
             "kernel": "zgemm_seg_kernel (ladder contraction)",
             "peak_source": "FP64 nominal 1.25 TFLOP/s of the profiling recipe (DFMA probe measured 1.195)",
             "ladder_share_of_step": lad_ms / max(all_ms, 1e-9), "wbuild_share_of_step": wb_ms / max(all_ms, 1e-9),

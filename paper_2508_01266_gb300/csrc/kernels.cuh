@@ -96,10 +96,12 @@ struct PGemmArgs {
   const unsigned char* B;
   double2* C;
   long long abytes, bbytes, sA, sB, sC;
+  int nrhs = 1;  // persistent kernel: right-hand sides folded into its tile loop
 };
 long long packed_bytes(int mode, int R, int K);
 cudaError_t launch_pack(const PackArgs& p, int prec, int nrhs, cudaStream_t st);
 cudaError_t launch_gemm_tcp(const PGemmArgs& g, int prec, int nrhs, int* errflag, cudaStream_t st);
+cudaError_t launch_gemm_tcp_persistent(const PGemmArgs& g, int prec, int nrhs, int* errflag, cudaStream_t st);
 size_t tcp_smem_bytes();
 
 // DF factor split: L[k1][k2][Q][n][n] (paper units) -> oo/ov/vo/vv blocks * scale.

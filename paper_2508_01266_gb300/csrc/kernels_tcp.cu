@@ -21,6 +21,8 @@
 // outstanding copies (bounded), releases tensor memory and returns.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace lrcc {
@@ -367,6 +369,293 @@ cudaError_t launch_gemm_tcp(const PGemmArgs& g0, int prec, int nrhs, int* errfla
         cudaFuncSetAttribute(tcp_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (attr != cudaSuccess) return attr;
     tcp_gemm_kernel<2><<<grid, P_THREADS, sm, st>>>(g, errflag);
+  }
+  return cudaGetLastError();
+}
+
+
+// --------------------------------------------------------------------------------
+// persistent packed GEMM: one CTA per SM loops over (batch, n tile, m tile, rhs) tiles
+// (right-hand sides fastest, so CTAs running together share B tiles in L2); two TMEM
+// accumulators (2 x 256 columns) let the epilogue of one tile overlap the MMAs of the
+// next.  Barriers: full/empty per smem stage (producer <-> MMA), accf[b] (MMA -> epilogue:
+// accumulator b complete), acce[b] (epilogue -> MMA: accumulator b drained), done (all
+// MMAs of the CTA complete, before TMEM is released).  Every wait is bounded and also
+// gives up when another role has failed; a failing CTA drains its copies and MMAs first.
+// --------------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ bool wait_or_fail(uint32_t bar, uint32_t parity, volatile int* fail) {
+  for (long long it = 0; it < P_SPIN; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255) == 255 && *fail) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void decode_tile(const PGemmArgs& g, long long tile, int& rhs, int& batch, int& mt,
+                                            int& nt) {
+  rhs = (int)(tile % g.nrhs);
+  long long r = tile / g.nrhs;
+  mt = (int)(r % g.tiles_m);
+  r /= g.tiles_m;
+  nt = (int)(r % g.tiles_n);
+  batch = (int)(r / g.tiles_n);
+}
+
+}  // namespace
+
+template <int PREC>
+__global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g, int* errflag) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[P_STAGES], empty[P_STAGES], accf[2], acce[2], donebar;
+  __shared__ uint32_t tmem_sh;
+  __shared__ volatile int fail_sh;
+
+  const long long ntiles = (long long)g.tiles_m * g.tiles_n * g.nbatch * g.nrhs;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nkt = g.nkt;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P_STAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&empty[s])));
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&accf[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(su32(&acce[b])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&donebar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    fail_sh = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_sh)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_sh;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    long long it = 0;
+    bool ok = true;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      int rhs, batch, mt, nt;
+      decode_tile(g, tile, rhs, batch, mt, nt);
+      const int s0 = g.sbeg[batch], total = (g.sbeg[batch + 1] - s0) * nkt;
+      const unsigned char* Ab = g.A + rhs * g.sA;
+      const unsigned char* Bb = g.B + rhs * g.sB;
+      for (int i = 0; i < total; ++i) {
+        const int s = (int)(it % P_STAGES);
+        if (it >= P_STAGES && !wait_or_fail(su32(&empty[s]), (uint32_t)(((it / P_STAGES) - 1) & 1), &fail_sh)) {
+          ok = false;
+          break;
+        }
+        const int seg = s0 + i / nkt, kt = i % nkt;
+        const unsigned char* at = Ab + (long long)g.ia[seg] * g.abytes + ((long long)mt * nkt + kt) * P_ATILE;
+        const unsigned char* bt = Bb + (long long)g.ib[seg] * g.bbytes + ((long long)nt * nkt + kt) * P_BTILE;
+        unsigned char* sa = smem + s * (P_ATILE + P_BTILE);
+        unsigned char* sb = sa + P_ATILE;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&full[s])),
+                     "r"(P_ATILE + P_BTILE)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                su32(sa)),
+            "l"(at), "r"(P_ATILE), "r"(su32(&full[s]))
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                su32(sb)),
+            "l"(bt), "r"(P_BTILE), "r"(su32(&full[s]))
+            : "memory");
+        ++it;
+      }
+    }
+    if (!ok) {
+      fail_sh = 1;
+      // drain this CTA's copies still in flight before shared memory is released
+      for (long long j = (it > P_STAGES ? it - P_STAGES : 0); j < it; ++j)
+        wait_parity(su32(&full[j % P_STAGES]), (uint32_t)((j / P_STAGES) & 1));
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t LBO = 128;
+    constexpr uint32_t SBO_A = (P_BKR / (PREC == 1 ? 4 : 8)) * 128;
+    const uint32_t fmt = PREC == 1 ? 2u : 1u;
+    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(P_BNR >> 3) << 17) |
+                           ((uint32_t)(P_BM >> 4) << 24);
+    long long it = 0;
+    int local = 0;
+    bool ok = true;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++local) {
+      int rhs, batch, mt, nt;
+      decode_tile(g, tile, rhs, batch, mt, nt);
+      const int total = (g.sbeg[batch + 1] - g.sbeg[batch]) * nkt;
+      const int b = local & 1;
+      if (local >= 2 && !wait_or_fail(su32(&acce[b]), (uint32_t)(((local / 2) - 1) & 1), &fail_sh)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t acc = tmem + (uint32_t)(b * P_BNR);
+      for (int i = 0; i < total; ++i, ++it) {
+        const int s = (int)(it % P_STAGES);
+        if (!wait_or_fail(su32(&full[s]), (uint32_t)((it / P_STAGES) & 1), &fail_sh)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a0 = su32(smem + s * (P_ATILE + P_BTILE)), b0 = a0 + P_ATILE;
+        if (PREC == 1) {
+#pragma unroll
+          for (int ks = 0; ks < P_BKR / 8; ++ks) {
+            const uint32_t ko = ks * 2 * LBO;
+            const uint64_t ad = sdesc(a0 + ko, LBO, SBO_A), bd = sdesc(b0 + ko, LBO, SBO_A);
+            const uint32_t accum = (i > 0 || ks > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+          }
+        } else {
+#pragma unroll
+          for (int ks = 0; ks < P_BKR / 16; ++ks) {
+            const uint32_t ko = ks * 2 * LBO;
+            const uint64_t ahi = sdesc(a0 + ko, LBO, SBO_A), bhi = sdesc(b0 + ko, LBO, SBO_A);
+            const uint64_t alo = sdesc(a0 + P_BM * 64 + ko, LBO, SBO_A),
+                           blo = sdesc(b0 + P_BNR * 64 + ko, LBO, SBO_A);
+            const uint32_t accum = (i > 0 || ks > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p, q;\n setp.ne.b32 p, %6, 0;\n setp.ne.b32 q, 1, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %4, %3, q;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %2, %3, q;\n}\n" ::"r"(acc),
+                "l"(ahi), "l"(bhi), "r"(idesc), "l"(blo), "l"(alo), "r"(accum));
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         su32(&empty[s]))
+                     : "memory");
+      }
+      if (!ok) break;
+      // accumulator b complete once every MMA above is (immediately when total == 0)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       su32(&accf[b]))
+                   : "memory");
+    }
+    if (!ok) fail_sh = 1;
+    // tracks every MMA this thread issued: TMEM is released only after it completes
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     su32(&donebar))
+                 : "memory");
+  } else if (warp >= 2) {
+    // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31
+    const int q = warp & 3;
+    int local = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++local) {
+      int rhs, batch, mt, nt;
+      decode_tile(g, tile, rhs, batch, mt, nt);
+      const int total = (g.sbeg[batch + 1] - g.sbeg[batch]) * nkt;
+      const int b = local & 1;
+      bool ok = wait_or_fail(su32(&accf[b]), (uint32_t)((local / 2) & 1), &fail_sh);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) fail_sh = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int m = mt * P_BM + q * 32 + lane;
+      double2* Cp = g.C + rhs * g.sC + g.coff[batch];
+#pragma unroll 1
+      for (int c0 = 0; c0 < P_BNR; c0 += 16) {
+        uint32_t r[16];
+        if (total > 0) {
+          const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * P_BNR + c0);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                "=r"(r[15])
+              : "r"(ta));
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) r[j] = 0u;
+        }
+        if (m < g.M && (total > 0 || g.epi == 1)) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int n = nt * (P_BNR / 2) + c0 / 2 + j;
+            if (n >= g.N) break;
+            const double ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
+            const double vr = g.ar * ar - g.ai * ai, vi = g.ar * ai + g.ai * ar;
+            if (g.epi == 0) {
+              double2* cp = Cp + (long long)m * g.ldc + n;
+              double2 cv = *cp;
+              cv.x += vr;
+              cv.y += vi;
+              *cp = cv;
+            } else {
+              const int a = m / g.ep2, c = m - a * g.ep2;
+              const int bb = n / g.ep3, d = n - bb * g.ep3;
+              Cp[(((long long)a * g.ep1 + bb) * g.ep2 + c) * g.ep3 + d] = make_double2(vr, vi);
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&acce[b])) : "memory");
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !wait_parity(su32(&donebar), 0)) fail_sh = 1;
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (threadIdx.x == 0 && fail_sh) atomicExch(errflag, 1);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+cudaError_t launch_gemm_tcp_persistent(const PGemmArgs& g0, int prec, int nrhs, int* errflag, cudaStream_t st) {
+  PGemmArgs g = g0;
+  g.tiles_m = (g.M + P_BM - 1) / P_BM;
+  g.tiles_n = (g.N + P_BNR / 2 - 1) / (P_BNR / 2);
+  g.nrhs = nrhs;
+  const long long ntiles = (long long)g.tiles_m * g.tiles_n * g.nbatch * nrhs;
+  if (ntiles <= 0) return cudaSuccess;
+  static const int nsm = []() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+      return 152;
+    return n > 0 ? n : 152;
+  }();
+  const unsigned grid = (unsigned)std::min<long long>(ntiles, nsm);
+  const size_t sm = tcp_smem_bytes();
+  if (prec == 1) {
+    static const cudaError_t attr =  // thread-safe one-time setup
+        cudaFuncSetAttribute(tcp_gemm_persistent<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (attr != cudaSuccess) return attr;
+    tcp_gemm_persistent<1><<<grid, P_THREADS, sm, st>>>(g, errflag);
+  } else {
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(tcp_gemm_persistent<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (attr != cudaSuccess) return attr;
+    tcp_gemm_persistent<2><<<grid, P_THREADS, sm, st>>>(g, errflag);
   }
   return cudaGetLastError();
 }

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -24,6 +25,9 @@ static int64_t align_up(int64_t n) { return (n + 31) / 32 * 32; }
 bool Runtime::ck(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return true;
   err = std::string(what) + ": " + cudaGetErrorString(e);
+  // consume the runtime's last-error state: a recoverable error (for example an
+  // allocation that did not fit) must not resurface at the next kernel launch check
+  (void)cudaGetLastError();
   return false;
 }
 
@@ -61,6 +65,7 @@ void Runtime::release() {
   packscr = nullptr;
   packscr_bytes = 0;
   drop_graphs();
+  fixpack_bytes = 0;
   if (part) cudaFree(part);
   part = nullptr;
   part_bytes = 0;
@@ -138,6 +143,10 @@ lrcc_status Runtime::init(const lrcc_dims& d, int64_t ws_budget) {
   if (!ck(cudaMalloc(&dip, 3 * nk * n * n * sizeof(double2)), "cudaMalloc(dipoles)")) return LRCC_ENOMEM;
   if (!ck(cudaMemset(fix, 0, plan.arena_size[AR_FIX] * sizeof(double2)), "cudaMemset")) return LRCC_ECUDA;
   if (!ck(cudaMalloc(&dflag, sizeof(int)), "cudaMalloc(flag)")) return LRCC_ENOMEM;
+  {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) fixpack_budget = tot / 16;
+  }
   if (!ck(cudaMemset(dflag, 0, sizeof(int)), "cudaMemset(flag)")) return LRCC_ECUDA;
   return LRCC_OK;
 }
@@ -216,13 +225,19 @@ lrcc_status Runtime::run_packed(int gi, const Gemm& g, double2* const ar[AR_COUN
       return LRCC_ECUDA;
     pp.init = true;
   }
-  // operands that live in the fixed arena are packed once per precision; the others
-  // (vector arenas and the W workspace, rebuilt every product) are packed each time
+  // operands that live in the fixed arena are packed once per precision and cached while
+  // the cache stays within its budget (1/16 of device memory); beyond it they are packed
+  // into the shared scratch at every use (a memory-bound pass, cheap next to the GEMM).
+  // Vector and workspace operands are packed every time.
   const bool varA = g.arA != AR_FIX, varB = g.arB != AR_FIX;
   const int nrA = (!fixed_only && is_vec_arena(g.arA)) ? nr : 1;
   const int nrB = (!fixed_only && is_vec_arena(g.arB)) ? nr : 1;
-  const size_t needA = varA ? (size_t)pp.abytes * pp.alist.size() * nrA : 0;
-  const size_t needB = varB ? (size_t)pp.bbytes * pp.blist.size() * nrB : 0;
+  const size_t sizeA = (size_t)pp.abytes * pp.alist.size(), sizeB = (size_t)pp.bbytes * pp.blist.size();
+  const bool cacheA = !varA && (pp.fixA[prec] || fixpack_bytes + sizeA <= fixpack_budget);
+  const bool cacheB = !varB && (pp.fixB[prec] || fixpack_bytes + (cacheA && !pp.fixA[prec] ? sizeA : 0) + sizeB <=
+                                                     fixpack_budget);
+  const size_t needA = varA ? sizeA * nrA : (cacheA ? 0 : sizeA);
+  const size_t needB = varB ? sizeB * nrB : (cacheB ? 0 : sizeB);
   if (needA + needB + 1024 > packscr_bytes) {
     if (!ck(cudaStreamSynchronize(st), "sync")) return LRCC_ECUDA;  // earlier ops may still read it
     if (packscr) cudaFree(packscr);
@@ -253,13 +268,14 @@ lrcc_status Runtime::run_packed(int gi, const Gemm& g, double2* const ar[AR_COUN
   const unsigned char* Ap;
   const unsigned char* Bp;
   lrcc_status s;
-  if (varA) {
+  if (!cacheA) {
     if ((s = pack(0, g.arA, pp.alist, pp.d_aoffs, g.M, g.lda, g.ta, pp.abytes, packscr, nrA)) != LRCC_OK) return s;
     Ap = packscr;
   } else {
-    if (!pp.fixA[prec] &&
-        !ck(cudaMalloc(&pp.fixA[prec], (size_t)pp.abytes * pp.alist.size()), "cudaMalloc(packed fixed)"))
-      return LRCC_ENOMEM;
+    if (!pp.fixA[prec]) {
+      if (!ck(cudaMalloc(&pp.fixA[prec], sizeA), "cudaMalloc(packed fixed)")) return LRCC_ENOMEM;
+      fixpack_bytes += sizeA;
+    }
     if (pp.verA[prec] != fix_version) {
       if ((s = pack(0, g.arA, pp.alist, pp.d_aoffs, g.M, g.lda, g.ta, pp.abytes, pp.fixA[prec], 1)) != LRCC_OK)
         return s;
@@ -267,15 +283,16 @@ lrcc_status Runtime::run_packed(int gi, const Gemm& g, double2* const ar[AR_COUN
     }
     Ap = pp.fixA[prec];
   }
-  if (varB) {
+  if (!cacheB) {
     unsigned char* dst = packscr + needA;
     if ((s = pack(1, g.arB, pp.blist, pp.d_boffs, g.N, g.ldb, g.tb ? 0 : 1, pp.bbytes, dst, nrB)) != LRCC_OK)
       return s;
     Bp = dst;
   } else {
-    if (!pp.fixB[prec] &&
-        !ck(cudaMalloc(&pp.fixB[prec], (size_t)pp.bbytes * pp.blist.size()), "cudaMalloc(packed fixed)"))
-      return LRCC_ENOMEM;
+    if (!pp.fixB[prec]) {
+      if (!ck(cudaMalloc(&pp.fixB[prec], sizeB), "cudaMalloc(packed fixed)")) return LRCC_ENOMEM;
+      fixpack_bytes += sizeB;
+    }
     if (pp.verB[prec] != fix_version) {
       if ((s = pack(1, g.arB, pp.blist, pp.d_boffs, g.N, g.ldb, g.tb ? 0 : 1, pp.bbytes, pp.fixB[prec], 1)) !=
           LRCC_OK)
@@ -297,7 +314,16 @@ lrcc_status Runtime::run_packed(int gi, const Gemm& g, double2* const ar[AR_COUN
   a.sA = nrA > 1 ? (long long)pp.abytes * pp.alist.size() : 0;
   a.sB = nrB > 1 ? (long long)pp.bbytes * pp.blist.size() : 0;
   a.sC = (!fixed_only && is_vec_arena(g.arC)) ? stride[g.arC] : 0;
-  if (!ck(launch_gemm_tcp(a, prec, fixed_only ? 1 : nr, dflag, st), "packed gemm")) return LRCC_ECUDA;
+  // persistent double-buffered kernel by default; LRCC_PACKED_KERNEL=classic selects the
+  // one-tile-per-CTA kernel (same arithmetic, same results)
+  static const bool persistent = []() {
+    const char* e = std::getenv("LRCC_PACKED_KERNEL");
+    return !(e && std::string(e) == "classic");
+  }();
+  const int nrr = fixed_only ? 1 : nr;
+  const cudaError_t e = persistent ? launch_gemm_tcp_persistent(a, prec, nrr, dflag, st)
+                                   : launch_gemm_tcp(a, prec, nrr, dflag, st);
+  if (!ck(e, "packed gemm")) return LRCC_ECUDA;
   ++launches;
   return LRCC_OK;
 }

@@ -66,8 +66,10 @@ struct Runtime {
   int* dflag = nullptr;  // device error flag of the tensor-core kernels (bounded waits)
   std::vector<PackPlan> packs;            // per GEMM op (lazily built)
   long long fix_version = 0;              // bumped whenever the ground-state program rewrites FIX
-  unsigned char* packscr = nullptr;       // packed vector-dependent operands
+  unsigned char* packscr = nullptr;       // packed vector-dependent operands (and uncached fixed ones)
   size_t packscr_bytes = 0;
+  size_t fixpack_bytes = 0;               // cached packs of fixed operands
+  size_t fixpack_budget = (size_t)16 << 30;
   bool use_packed(const Gemm& g) const;
   // split-K partials (grown on demand; never during a call that must not allocate)
   double2* part = nullptr;
