@@ -55,7 +55,9 @@ typedef struct {
 } lrcc_dims;
 
 typedef struct {
-  double conv_tol;     /* relative residual of the response equations (default 1e-10) */
+  double conv_tol;     /* convergence threshold (default 1e-10): response and Lambda equations:
+                          max |residual| / max |right-hand side|; CCSD amplitudes: max |Omega|;
+                          Davidson: residual norm of every wanted root */
   double refine_tol;   /* mixed precision: FP64 residual target of iterative refinement */
   int32_t max_iter;    /* default 200 */
   int32_t diis_depth;  /* default 8 */
@@ -70,6 +72,12 @@ typedef struct {
                             2 asymmetric form as computed */
   const char* log_path;  /* NULL (default) or a file the iterative solvers append one JSON line
                             per iteration to: solver, iteration, residuals per system */
+  int32_t max_batch;     /* vectors per launch of a product: 0 (default) as many as the per-vector
+                            scratch that fits in device memory allows; larger batches run in
+                            chunks (same results) */
+  int32_t host_history;  /* DIIS history of the solvers: 0 (default) device memory unless it would
+                            take more than half of the free memory, then pinned host memory read
+                            by the kernels through the coherent CPU-GPU link; 1 host; -1 device */
 } lrcc_options;
 
 /* ---------------------------------------------------------------------------

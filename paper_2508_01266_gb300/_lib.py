@@ -27,7 +27,8 @@ class lrcc_options(C.Structure):
     _fields_ = [("conv_tol", C.c_double), ("refine_tol", C.c_double), ("max_iter", C.c_int32),
                 ("diis_depth", C.c_int32), ("diis_period", C.c_int32), ("precision", C.c_int32),
                 ("autotune", C.c_int32), ("use_graphs", C.c_int32), ("spin_timeout_cycles", C.c_uint64),
-                ("response_form", C.c_int32), ("log_path", C.c_char_p)]
+                ("response_form", C.c_int32), ("log_path", C.c_char_p), ("max_batch", C.c_int32),
+                ("host_history", C.c_int32)]
 
 
 VP = C.c_void_p

@@ -328,20 +328,54 @@ lrcc_status Runtime::run_packed(int gi, const Gemm& g, double2* const ar[AR_COUN
   return LRCC_OK;
 }
 
+// Input/output vectors for nrhs right-hand sides; per-vector scratch for as many of them
+// as fit (max_batch caps it when set): products over larger batches run in chunks of
+// scr_rhs vectors (run_chunked), with identical results.
 lrcc_status Runtime::ensure_rhs(int nrhs) {
-  if (nrhs <= cap_rhs) return LRCC_OK;
+  const int want_scr = max_batch > 0 ? std::min(nrhs, max_batch) : nrhs;
+  // keep the buffers when they hold the batch and the scratch was sized for at least this
+  // request (a smaller scratch than requested means memory ran out; asking again would not help)
+  if (nrhs <= cap_rhs && want_scr <= scr_req && (max_batch <= 0 || scr_rhs <= max_batch)) return LRCC_OK;
+  drop_graphs();
   for (double2** p : {&in, &out, &scr})
     if (*p) {
       cudaFree(*p);
       *p = nullptr;
     }
   cap_rhs = 0;
-  const int64_t vin = plan.arena_size[AR_IN], vscr = plan.arena_size[AR_SCR];
+  scr_rhs = 0;
+  scr_req = 0;
+  const int64_t vin = plan.arena_size[AR_IN], vscr = std::max<int64_t>(plan.arena_size[AR_SCR], 1);
   if (!ck(cudaMalloc(&in, vin * nrhs * sizeof(double2)), "cudaMalloc(input vectors)")) return LRCC_ENOMEM;
   if (!ck(cudaMalloc(&out, vin * nrhs * sizeof(double2)), "cudaMalloc(output vectors)")) return LRCC_ENOMEM;
-  if (!ck(cudaMalloc(&scr, std::max<int64_t>(vscr, 1) * nrhs * sizeof(double2)), "cudaMalloc(scratch)"))
+  for (int k = want_scr; k >= 1; k = k / 2) {
+    if (cudaMalloc(&scr, vscr * k * sizeof(double2)) == cudaSuccess) {
+      scr_rhs = k;
+      break;
+    }
+    (void)cudaGetLastError();
+    scr = nullptr;
+    if (k == 1) break;
+  }
+  if (!scr) {
+    err = "cudaMalloc(scratch): out of memory even for one vector";
     return LRCC_ENOMEM;
+  }
   cap_rhs = nrhs;
+  scr_req = want_scr;
+  return LRCC_OK;
+}
+
+// A vector program over nrhs vectors held in in/out, in chunks of at most scr_rhs.
+lrcc_status Runtime::run_chunked(const Program& pr, int nrhs, cudaStream_t st, int prec) {
+  const int64_t vin = plan.arena_size[AR_IN];
+  const int step = std::max(1, scr_rhs);
+  for (int c0 = 0; c0 < nrhs; c0 += step) {
+    const int cnt = std::min(step, nrhs - c0);
+    double2* ar[AR_COUNT] = {fix, in + (size_t)c0 * vin, out + (size_t)c0 * vin, scr, ws};
+    lrcc_status s = run(pr, ar, cnt, st, prec);
+    if (s != LRCC_OK) return s;
+  }
   return LRCC_OK;
 }
 
@@ -637,6 +671,10 @@ lrcc_status Runtime::apply_impl(int transpose, int nrhs, cudaStream_t st, int pr
   // program's own zero ops at the start of their lifetimes
   double2* res = transpose ? in : out;
   const Program& pr = transpose ? jacT : plan.jac;
+  if (nrhs > scr_rhs) {  // scratch holds fewer vectors than the batch: chunks, no graph
+    if (!ck(cudaMemsetAsync(res, 0, vin * nrhs * sizeof(double2), st), "cudaMemsetAsync")) return LRCC_ECUDA;
+    return run_chunked(pr, nrhs, st, prec);
+  }
   if (!use_graphs || prof) {
     if (!ck(cudaMemsetAsync(res, 0, vin * nrhs * sizeof(double2), st), "cudaMemsetAsync")) return LRCC_ECUDA;
     return run(pr, ar, nrhs, st, prec);
@@ -722,6 +760,8 @@ void lrcc_default_options(lrcc_options* o) {
   o->spin_timeout_cycles = 0;
   o->response_form = 0;
   o->log_path = nullptr;
+  o->max_batch = 0;
+  o->host_history = 0;
 }
 
 lrcc_status lrcc_create(const lrcc_dims* dims, lrcc_problem** out) {
@@ -931,6 +971,7 @@ lrcc_status lrcc_jacobian_apply(lrcc_problem* p, int32_t transpose, int32_t nrhs
   const int prec = opt ? opt->precision : 0;
   if (prec < 0 || prec > 2) return fail(p, LRCC_EINVAL, "jacobian_apply: precision must be 0, 1 or 2");
   Runtime& rt = p->rt;
+  rt.max_batch = opt ? std::max(0, opt->max_batch) : 0;
   lrcc_status s = rt.ensure_rhs(nrhs);
   if (s != LRCC_OK) return s;
   // a null handle is the caller's legacy default stream (this library is built with

@@ -50,7 +50,10 @@ struct Runtime {
   double2 *dip = nullptr, *l1 = nullptr, *l2 = nullptr;
   std::vector<double> eps;
   std::vector<double2> dip_host;  // [3][nk][n][n]
-  int cap_rhs = 0;
+  int cap_rhs = 0;  // vectors held by in/out
+  int scr_rhs = 0;  // vectors held by the per-vector scratch (<= cap_rhs)
+  int scr_req = 0;  // vectors the scratch was requested for
+  int max_batch = 0;  // 0: as many vectors per launch as memory allows
   long long launches = 0;
   std::string err;
   // optional per-op timing with CUDA events on the launching stream
@@ -63,6 +66,7 @@ struct Runtime {
   bool ck(cudaError_t e, const char* what);
   lrcc_status init(const lrcc_dims& d, int64_t ws_budget);
   lrcc_status ensure_rhs(int nrhs);
+  lrcc_status run_chunked(const Program& pr, int nrhs, cudaStream_t st, int prec);
   int* dflag = nullptr;  // device error flag of the tensor-core kernels (bounded waits)
   std::vector<PackPlan> packs;            // per GEMM op (lazily built)
   long long fix_version = 0;              // bumped whenever the ground-state program rewrites FIX

@@ -89,8 +89,22 @@ BatchSolver::BatchSolver(Runtime& r, const lrcc_options& o, int nsys, int min_pa
 
 lrcc_status BatchSolver::init() {
   bool ok = true;
-  HX = dev.get<double2>(rt, (size_t)depth * ns * vec, ok);
-  HE = dev.get<double2>(rt, (size_t)depth * ns * vec, ok);
+  const size_t hist = (size_t)depth * ns * vec * sizeof(double2);
+  bool host = opt.host_history > 0;
+  if (opt.host_history == 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) host = 2 * hist > fr / 2;
+  }
+  if (host) {
+    // pinned host memory mapped into the device address space: the update, dot and
+    // combination kernels read and write the history over the coherent CPU-GPU link
+    HX = (double2*)dev.host(rt, hist, ok);
+    HE = (double2*)dev.host(rt, hist, ok);
+  } else {
+    HX = dev.get<double2>(rt, (size_t)depth * ns * vec, ok);
+    HE = dev.get<double2>(rt, (size_t)depth * ns * vec, ok);
+  }
+  host_history = host;
   RES = dev.get<double2>(rt, (size_t)ns * vec, ok);
   DEN = dev.get<double>(rt, (size_t)vec, ok);
   RMAX = dev.get<unsigned long long>(rt, (size_t)ns, ok);
@@ -389,6 +403,7 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
   const int ns = (int)sys.size();
   if (ns == 0) return LRCC_OK;
 
+  rt.max_batch = std::max(0, opt.max_batch);
   lrcc_status s = rt.ensure_rhs(ns);
   if (s != LRCC_OK) return s;
   BatchSolver bs(rt, opt, ns, ns * std::max(ns, ncomp));
@@ -416,9 +431,8 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
   auto dots = [&](const std::vector<const double2*>& a, const std::vector<const double2*>& b, int conj, long long len,
                   std::vector<cd>& out) { return bs.dots(a, b, conj, len, out); };
   auto run_prog = [&](const Program& pr, int nrhs) -> lrcc_status {
-    double2* ar[AR_COUNT] = {rt.fix, rt.in, rt.out, rt.scr, rt.ws};
     if (!rt.ck(cudaMemsetAsync(rt.out, 0, (size_t)vec * nrhs * sizeof(double2), st), "memset")) return LRCC_ECUDA;
-    return rt.run(pr, ar, nrhs, st);
+    return rt.run_chunked(pr, nrhs, st, 0);
   };
   auto set_mu = [&](int comp) -> lrcc_status {
     const double2* d = rt.dip_host.data() + (size_t)comp * nk * n * n;

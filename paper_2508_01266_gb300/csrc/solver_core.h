@@ -15,9 +15,26 @@ using cd = std::complex<double>;
 
 // device allocations released together
 struct Dev {
-  std::vector<void*> ptrs;
+  std::vector<void*> ptrs, hptrs;
   ~Dev() {
     for (void* p : ptrs) cudaFree(p);
+    for (void* p : hptrs) cudaFreeHost(p);
+  }
+  // pinned host memory mapped into the device address space; returns the device pointer
+  void* host(Runtime& rt, size_t bytes, bool& ok) {
+    void* h = nullptr;
+    void* d = nullptr;
+    if (!ok) return nullptr;
+    if (!rt.ck(cudaHostAlloc(&h, std::max<size_t>(bytes, 1), cudaHostAllocMapped), "cudaHostAlloc(history)")) {
+      ok = false;
+      return nullptr;
+    }
+    hptrs.push_back(h);
+    if (!rt.ck(cudaHostGetDevicePointer(&d, h, 0), "cudaHostGetDevicePointer")) {
+      ok = false;
+      return nullptr;
+    }
+    return d;
   }
   template <class T>
   T* get(Runtime& rt, size_t n, bool& ok) {
@@ -44,6 +61,7 @@ struct BatchSolver {
   unsigned long long* RMAX = nullptr;
   const double2 **PA = nullptr, **PB = nullptr, **PV = nullptr;
   int total_it = 0;
+  bool host_history = false;
   std::vector<double> rel;
 
   BatchSolver(Runtime& r, const lrcc_options& o, int nsys, int min_pairs);

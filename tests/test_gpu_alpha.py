@@ -142,3 +142,23 @@ def test_left_response_alpha_mixed_c1(lr, c1_ref):
     print(f"C1 left-response alpha_zz BF16x3: {got.ravel()} oracle {ref.ravel()} |err| {err:.2e}")
     assert info[1] == 0
     assert err <= 1e-5
+
+
+def test_alpha_host_history_and_chunks_bitwise(lr):
+    """DIIS history in pinned host memory (read by the kernels over the CPU-GPU link) and
+    chunked products give bitwise the alpha of the all-device, single-launch solve."""
+    p = make_problem(2, 2, 3, 4, seed=5, sigma_l=0.15)
+    nk, o, v, Q = p.nk, p.nocc, p.nvir, p.naux
+    R = rcc.RCC(p)
+    t1, t2, _ = rcc.solve_ccsd(R, tol=1e-10)
+    l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=1e-10)
+    pl1, pl2 = paper_lambda(nk, l1, l2)
+    prob = lr.Problem(nk, o, v, Q)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    prob.set_ground_state(t1, t2 * nk, pl1, pl2)
+    base = dict(conv_tol=1e-11, max_iter=300)
+    ref, _ = prob.polarizability([0, 2], [0.0, 0.07], lr.default_options(host_history=-1, **base))
+    got, info = prob.polarizability([0, 2], [0.0, 0.07], lr.default_options(host_history=1, max_batch=2, **base))
+    prob.close()
+    assert info[1] == 0
+    assert np.array_equal(got, ref)

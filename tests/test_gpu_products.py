@@ -145,3 +145,18 @@ def test_autotuned_products(lr, prec):
         tol = 1e-12 if prec == 0 else 5e-5
         assert float((a1 - r1).abs().max() / r1.abs().max()) < tol
         assert float((a2 - r2).abs().max() / r2.abs().max()) < tol
+
+
+def test_chunked_batch_bitwise(lr):
+    """max_batch: a batch larger than the per-launch vector count runs in chunks with
+    bitwise the same results (split-K choices do not depend on the batch)."""
+    nk, o, v, Q = 3, 2, 5, 8
+    p, prob, t1, t2 = _setup(lr, nk, o, v, Q)
+    x1, x2 = random_probe(nk, o, v, seed=23, nrhs=5)
+    dev = torch.device("cuda")
+    X1 = torch.as_tensor(x1, device=dev).contiguous()
+    X2 = torch.as_tensor(x2 * nk, device=dev).contiguous()
+    for tr in (False, True):
+        ref = prob.jacobian_apply(X1, X2, transpose=tr)
+        got = prob.jacobian_apply(X1, X2, transpose=tr, options=lr.default_options(max_batch=2))
+        assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
