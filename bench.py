@@ -42,12 +42,19 @@ def _dist():
 
 
 def _max_over_ranks(dist, x):
+    """Slowest rank's time (the job's time); a CPU tensor on the gloo backend."""
     if dist is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seed(rank):
+    """Seed of a rank's right-hand sides: replicas work on disjoint synthetic vectors."""
+    return 2000 + 97 * rank
 
 
 class ClockSampler:
@@ -312,7 +319,7 @@ def main():
     prob.set_integrals(p.L, p.eps, p.dip)
     prob.set_ground_state(t1, t2 * nk)
     prob_fixed_gb = 16.0 * _fixed_elems(lr, nk, o, v, Q) / 1e9
-    x1, x2 = random_probe(nk, o, v, seed=2000 + 97 * rank, nrhs=nrhs)
+    x1, x2 = random_probe(nk, o, v, seed=replica_seed(rank), nrhs=nrhs)
     dev = torch.device("cuda", local)
     X1 = torch.as_tensor(x1, device=dev).contiguous()
     X2 = torch.as_tensor(x2 * nk, device=dev).contiguous()

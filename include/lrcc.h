@@ -16,8 +16,9 @@
  *     paper's spin-orbital amplitudes (Sec. II.A keeps all spin blocks).
  *   - Density-fitting factors L[k1][k2][Q][p][q] (paper units):
  *         <pq|rs> = (pr|qs) = sum_Q L[kp][kr][Q][p][r] * L[kq][ks][Q][q][s].
- *     Hermiticity L[k2][k1][Q] = L[k1][k2][Q]^H is assumed, which makes the paper's
- *     assumption <PQ|RS>* = <RS|PQ> (Sec. II.C) exact.
+ *     Hermiticity L[k2][k1][Q] = L[k1][k2][Q]^H is required (set_integrals rejects
+ *     factors that violate it beyond 1e-10 of their largest entry); it makes the
+ *     paper's assumption <PQ|RS>* = <RS|PQ> (Sec. II.C) exact.
  *   - Singles x1[k][i][a]; doubles x2[ki][kj][ka][i][j][a][b] with kb implied,
  *     in the paper's normalization (t2 and lambda2 carry the factor Nk relative to
  *     the supercell amplitudes, so Eqs. 6-15 hold with their printed 1/Nk factors).
@@ -91,7 +92,10 @@ lrcc_status lrcc_create(const lrcc_dims* dims, lrcc_problem** out);
 /* Integrals of Sec. II.A/II.C: DF factors (c128 [nk][nk][naux][n][n], paper units),
  * orbital energies eps ([nk][n], canonical Fock diagonal, Eq. 9) and dipole
  * integrals (c128 [3][nk][n][n], k-diagonal, <p|mu_c|q>).  Pointers are host
- * memory when on_device == 0, device memory otherwise.  Copies the data. */
+ * memory when on_device == 0, device memory otherwise.  Copies the data.
+ * LRCC_EINVAL (problem unchanged) for non-finite values, DF factors or dipoles that
+ * are not Hermitian, or a reference that is not gapped (some virtual level at or
+ * below some occupied level). */
 lrcc_status lrcc_set_integrals(lrcc_problem* p, const void* L, const double* eps, const void* dip,
                                int32_t on_device);
 
