@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "liblrcc.so")
-SOURCES = ["plan.cpp", "plan_api.cpp", "small_eig.cpp", "kernels_f64.cu", "runtime.cu", "solver.cu", "solver_kernels.cu", "kernels_tc.cu", "noalloc.cu", "kernels_tcp.cu", "ground.cu", "davidson.cu"]
+SOURCES = ["plan.cpp", "plan_api.cpp", "small_eig.cpp", "kernels_f64.cu", "runtime.cu", "solver.cu", "solver_kernels.cu", "kernels_tc.cu", "noalloc.cu", "kernels_tcp.cu", "ground.cu", "davidson.cu", "kernels_small.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

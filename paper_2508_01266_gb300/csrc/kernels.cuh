@@ -59,6 +59,11 @@ int gemm_pick_tile(int M, int N);
 
 cudaError_t launch_gemm_f64(const GemmArgs& g, int tile, int nrhs, cudaStream_t st);
 cudaError_t launch_split_reduce(const GemmArgs& g, int nrhs, cudaStream_t st);
+// short-contraction and tiny-output FP64 GEMM kernels (kernels_small.cu)
+bool skinny_k_ok(const GemmArgs& g);
+cudaError_t launch_skinny_k(const GemmArgs& g, int nrhs, cudaStream_t st);
+bool reduce_small_ok(const GemmArgs& g);
+cudaError_t launch_reduce_small(const GemmArgs& g, int nrhs, cudaStream_t st);
 constexpr int F64_BK = 8;  // complex K per iteration of the FP64 GEMM
 constexpr int TC_BK = 16;  // complex K per iteration of the unpacked tensor-core GEMM
 cudaError_t launch_perm_f64(const PermArgs& p, int nrhs, cudaStream_t st);

@@ -379,8 +379,33 @@ lrcc_status Runtime::run_chunked(const Program& pr, int nrhs, cudaStream_t st, i
   return LRCC_OK;
 }
 
+static GemmArgs shape_args(const Gemm& g) {
+  GemmArgs a;
+  a.M = g.M; a.N = g.N; a.K = g.K; a.ta = g.ta; a.tb = g.tb; a.epi = g.epi;
+  return a;
+}
+
+// Splits of the tiny-output reduction: whole segments per split, about 8 CTAs per SM.
+static int reduce_split(const Gemm& g, const GemmDesc& d) {
+  const long long want = (152LL * 8 + g.nbatch() - 1) / g.nbatch();
+  long long s = std::min<long long>(want, d.max_seg);
+  const long long per = (long long)g.nbatch() * g.M * g.N * (long long)sizeof(double2);
+  if (per > 0) s = std::min<long long>(s, (64LL << 20) / per);
+  return (int)std::max<long long>(s, 1);
+}
+
 GemmChoice Runtime::default_choice(const Gemm& g, const GemmDesc& d, int prec) const {
   GemmChoice c;
+  const GemmArgs sa = shape_args(g);
+  if (skinny_k_ok(sa)) {
+    c.special = 1;
+    return c;
+  }
+  if (reduce_small_ok(sa) && !no_split) {
+    c.special = 2;
+    c.nsplit = reduce_split(g, d);
+    return c;
+  }
   c.tc = prec > 0 && tc_tile_useful(g);
   c.tile = d.tile;
   c.nsplit = pick_split(g, d, 1, c.tc);
@@ -390,6 +415,12 @@ GemmChoice Runtime::default_choice(const Gemm& g, const GemmDesc& d, int prec) c
 // One unpacked GEMM op with an explicit kernel choice (tile of the FP64 kernel or the
 // tensor-core kernel, split-K factor); grows the split-K partials buffer if needed.
 lrcc_status Runtime::launch_gemm(GemmArgs a, const Gemm& g, const GemmChoice& c, int nr, cudaStream_t st, int prec) {
+  if (c.special == 1) {
+    a.nsplit = 1;
+    a.part = nullptr;
+    ++launches;
+    return ck(launch_skinny_k(a, nr, st), "skinny gemm launch") ? LRCC_OK : LRCC_ECUDA;
+  }
   a.nsplit = no_split ? 1 : std::max(1, c.nsplit);
   a.part = nullptr;
   if (a.nsplit > 1) {
@@ -407,6 +438,29 @@ lrcc_status Runtime::launch_gemm(GemmArgs a, const Gemm& g, const GemmChoice& c,
     a.part = part;
   }
   cudaError_t e;
+  if (c.special == 2) {
+    if (!a.part) {  // nsplit == 1: one partial buffer still needed
+      const size_t need = (size_t)nr * g.nbatch() * g.M * g.N * sizeof(double2);
+      if (need > part_bytes) {
+        if (part) {
+          if (!ck(cudaStreamSynchronize(st), "split-K sync")) return LRCC_ECUDA;
+          cudaFree(part);
+          part = nullptr;
+          part_bytes = 0;
+        }
+        if (!ck(cudaMalloc(&part, need), "cudaMalloc(split-K partials)")) return LRCC_ENOMEM;
+        part_bytes = need;
+      }
+      a.part = part;
+    }
+    e = launch_reduce_small(a, nr, st);
+    ++launches;
+    if (e == cudaSuccess) {
+      e = launch_split_reduce(a, nr, st);
+      ++launches;
+    }
+    return ck(e, "reduction gemm launch") ? LRCC_OK : LRCC_ECUDA;
+  }
   if (c.tc && prec > 0) {
     GemmArgs b = a;
     if (tc_swap(g)) {  // C^T = B^T A^T: operands, transposes, leading dimensions and M, N swap

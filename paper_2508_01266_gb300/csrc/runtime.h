@@ -17,6 +17,7 @@ struct GemmChoice {
   bool tc = false;  // tensor-core kernel (mixed precision) instead of the FP64 kernel
   int tile = 0;     // FP64 kernel tile (gemm_tile_dims)
   int nsplit = 1;   // split-K factor
+  int special = 0;  // 1: short-contraction FP64 kernel; 2: tiny-output FP64 reduction kernel
 };
 
 struct GemmDesc {
