@@ -805,11 +805,12 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
   };
   e_vv(J, r, xs, Fv, AR_FIX, 1.0, "E vv");
   e_oo(J, r, xs, Fo, AR_FIX, -1.0, "E oo");
-  int64_t YEv = b.alloc(AR_SCR, nk * v2), YEo = b.alloc(AR_SCR, nk * o2);
-  yev(J, YEv, AR_SCR, Uk3, 1.0, "YEv");
-  yeo(J, YEo, AR_SCR, Uk3, 1.0, "YEo");
-  e_vv(J, r, Tk3, YEv, AR_SCR, -1.0, "E vv quad");
-  e_oo(J, r, Tk3, YEo, AR_SCR, -1.0, "E oo quad");
+  // The quadratic Fock-like terms r -= t YEv^T, r -= YEo^T t share the left factor t with
+  // the derivative-Fock terms below (r += t f'vv^T, r -= f'oo^T t): YEv and YEo are
+  // accumulated into f'vv (weight -1) and f'oo (weight +1) and applied by those two GEMMs.
+  int64_t dfvv = b.alloc(AR_SCR, nk * v2), dfoo = b.alloc(AR_SCR, nk * o2);
+  yev(J, dfvv, AR_SCR, Uk3, -1.0, "YEv");
+  yeo(J, dfoo, AR_SCR, Uk3, 1.0, "YEo");
 
   // singles from X2: y1 += Ud_0 fovT + sum_mef U (ae|mf) - sum_mne U (ne|mi)
   {
@@ -966,8 +967,7 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
     b.g_push(J);
   }
   // derivative Fock blocks f'vv[k](b,c), f'oo[k](k,j), f'vo[k](a,i), f'ov[k](m,e)
-  int64_t dfvv = b.alloc(AR_SCR, nk * v2), dfoo = b.alloc(AR_SCR, nk * o2), dfvo = b.alloc(AR_SCR, nk * ov),
-          dfov = b.alloc(AR_SCR, nk * ov), dfovT = b.alloc(AR_SCR, nk * ov);
+  int64_t dfvo = b.alloc(AR_SCR, nk * ov), dfov = b.alloc(AR_SCR, nk * ov), dfovT = b.alloc(AR_SCR, nk * ov);
   auto coul = [&](int64_t dst, int a, int c, int64_t Lbase, int la, int lc, double alpha, const char* tag) {
     Gemm& g = b.g_new(1, a * c, Q, 0, 0, Q, (int64_t)a * c, (int64_t)a * c, AR_SCR, AR_FIX, AR_SCR, alpha, 0.0,
                       tag);
@@ -1017,8 +1017,8 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
     b.g_push(J);
   }
   // (16) E' : r += sum_c T_ij^ac f'_bc - sum_k T_ik^ab f'_kj
-  e_vv(J, r, Tk3, dfvv, AR_SCR, 1.0, "E' vv");
-  e_oo(J, r, Tk3, dfoo, AR_SCR, -1.0, "E' oo");
+  e_vv(J, r, Tk3, dfvv, AR_SCR, 1.0, "E' vv");   // + E vv quad (through YEv)
+  e_oo(J, r, Tk3, dfoo, AR_SCR, -1.0, "E' oo");  // + E oo quad (through YEo)
   // (17) singles from X1
   {
     // sum_e f~vv[k](a,e) x(i,e) -> y1[k](i,a)
