@@ -1,10 +1,9 @@
 // FP64 kernels for the two GEMM shapes that tile-based kernels handle poorly, used in
 // every precision mode (they are memory-bound, so FP64 costs nothing extra):
 //
-// skinny_k_kernel — short contraction (K <= 16) with few rows (M <= 64), e.g. the
-//   Fock-like hole terms r(i, j, ab) += sum_k F(k, j) x(i, k, ab): one CTA per (batch entry,
-//   chunk of 128 columns) stages A (M x K) and the B chunk (K x 128) of each segment in
-//   shared memory; every thread owns whole output elements and adds them to C.
+// skinny_k_kernel — short contraction (K <= 16) with few rows (M <= 16) and long rows
+//   (N >= 64), e.g. the Fock-like hole terms r(i, j, ab) += sum_k F(k, j) x(i, k, ab): one
+//   thread per output column, one CTA per (batch entry, 256 columns).
 //
 // reduce_small_kernel — tiny output (M * N <= 64) with a long contraction, both operands
 //   K-contiguous (ta = 0, tb = 1), e.g. the o x o intermediates summed over (l, c, d) and
@@ -17,9 +16,8 @@ namespace lrcc {
 
 namespace {
 
-constexpr int SK_NT = 128;       // columns per CTA
-constexpr int SK_THREADS = 256;
-constexpr int SK_MAXK = 16, SK_MAXM = 64;
+constexpr int SK_THREADS = 256;  // columns per CTA
+constexpr int SK_MAXK = 16, SK_MAXM = 16;
 
 __device__ __forceinline__ void cmac(double2& acc, double2 a, double2 b) {
   acc.x = fma(a.x, b.x, acc.x);
@@ -30,22 +28,22 @@ __device__ __forceinline__ void cmac(double2& acc, double2 a, double2 b) {
 
 }  // namespace
 
-// PER = outputs per thread = M * SK_NT / SK_THREADS rounded up (the launcher picks the
-// smallest instantiation that covers M, keeping the accumulators in registers)
-template <int PER>
+// One thread per output column n: it loads the column's K values of B into registers
+// (independent loads, all in flight together), keeps M accumulators, and adds the column
+// of C at the end; A (M x K) is staged in shared memory per segment.  Memory-bound: every
+// element of B and C is touched once.
+template <int MM, int KK>  // compile-time bounds of M and K (register arrays)
 __global__ void __launch_bounds__(SK_THREADS) skinny_k_kernel(GemmArgs g, int nchunk) {
-  __shared__ double2 As[SK_MAXM][SK_MAXK];
-  __shared__ double2 Bs[SK_MAXK][SK_NT];
+  __shared__ double2 As[MM][KK];
   const int batch = blockIdx.x / nchunk, chunk = blockIdx.x - batch * nchunk;
-  const int n0 = chunk * SK_NT;
+  const int n = chunk * SK_THREADS + threadIdx.x;
   const long long rhs = blockIdx.y;
   const double2* Ab = g.A + rhs * g.sA;
   const double2* Bb = g.B + rhs * g.sB;
   const int M = g.M, N = g.N, K = g.K, tid = threadIdx.x;
-  const int nout = M * SK_NT;
-  double2 acc[PER];
+  double2 acc[MM];
 #pragma unroll
-  for (int j = 0; j < PER; ++j) acc[j] = make_double2(0.0, 0.0);
+  for (int m = 0; m < MM; ++m) acc[m] = make_double2(0.0, 0.0);
   for (int s = g.sbeg[batch]; s < g.sbeg[batch + 1]; ++s) {
     const double2* Ap = Ab + g.aoff[s];
     const double2* Bp = Bb + g.boff[s];
@@ -54,36 +52,27 @@ __global__ void __launch_bounds__(SK_THREADS) skinny_k_kernel(GemmArgs g, int nc
       const int m = e / K, k = e - m * K;
       As[m][k] = g.ta ? Ap[(long long)k * g.lda + m] : Ap[(long long)m * g.lda + k];
     }
-    for (int e = tid; e < K * SK_NT; e += SK_THREADS) {
-      int k, c;
-      if (g.tb) {  // B[n][k]: consecutive threads walk k
-        c = e / K;
-        k = e - c * K;
-      } else {     // B[k][n]: consecutive threads walk n
-        k = e / SK_NT;
-        c = e - k * SK_NT;
-      }
-      const int n = n0 + c;
-      Bs[k][c] = n < N ? (g.tb ? Bp[(long long)n * g.ldb + k] : Bp[(long long)k * g.ldb + n])
-                       : make_double2(0.0, 0.0);
-    }
     __syncthreads();
+    if (n < N) {
+      double2 b[KK];
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      const int o = tid + j * SK_THREADS;
-      if (o >= nout) break;
-      const int m = o / SK_NT, c = o - m * SK_NT;
-      for (int k = 0; k < K; ++k) cmac(acc[j], As[m][k], Bs[k][c]);
+      for (int k = 0; k < KK; ++k)
+        if (k < K) b[k] = g.tb ? Bp[(long long)n * g.ldb + k] : Bp[(long long)k * g.ldb + n];
+#pragma unroll
+      for (int m = 0; m < MM; ++m) {
+        if (m >= M) break;
+#pragma unroll
+        for (int k = 0; k < KK; ++k)
+          if (k < K) cmac(acc[m], As[m][k], b[k]);
+      }
     }
   }
+  if (n >= N) return;
   double2* Cp = g.C + rhs * g.sC + g.coff[batch];
 #pragma unroll
-  for (int j = 0; j < PER; ++j) {
-    const int o = tid + j * SK_THREADS;
-    if (o >= nout) break;
-    const int m = o / SK_NT, n = n0 + (o - m * SK_NT);
-    if (n >= N) continue;
-    const double vr = g.ar * acc[j].x - g.ai * acc[j].y, vi = g.ar * acc[j].y + g.ai * acc[j].x;
+  for (int m = 0; m < MM; ++m) {
+    if (m >= M) break;
+    const double vr = g.ar * acc[m].x - g.ai * acc[m].y, vi = g.ar * acc[m].y + g.ai * acc[m].x;
     double2* cp = Cp + (long long)m * g.ldc + n;
     double2 cv = *cp;
     cv.x += vr;
@@ -92,20 +81,17 @@ __global__ void __launch_bounds__(SK_THREADS) skinny_k_kernel(GemmArgs g, int nc
   }
 }
 
-bool skinny_k_ok(const GemmArgs& g) { return g.K <= SK_MAXK && g.M <= SK_MAXM && g.epi == 0; }
+bool skinny_k_ok(const GemmArgs& g) { return g.K <= SK_MAXK && g.M <= SK_MAXM && g.N >= 64 && g.epi == 0; }
 
 cudaError_t launch_skinny_k(const GemmArgs& g, int nrhs, cudaStream_t st) {
   if (!skinny_k_ok(g)) return cudaErrorInvalidValue;
-  const int nchunk = (g.N + SK_NT - 1) / SK_NT;
+  const int nchunk = (g.N + SK_THREADS - 1) / SK_THREADS;
   const long long nblk = (long long)g.nbatch * nchunk;
   if (nblk <= 0) return cudaSuccess;
   if (nblk > 2147483647LL || nrhs > 65535) return cudaErrorInvalidConfiguration;
   const dim3 grid((unsigned)nblk, (unsigned)nrhs);
-  const int per = (g.M * SK_NT + SK_THREADS - 1) / SK_THREADS;
-  if (per <= 4) skinny_k_kernel<4><<<grid, SK_THREADS, 0, st>>>(g, nchunk);
-  else if (per <= 8) skinny_k_kernel<8><<<grid, SK_THREADS, 0, st>>>(g, nchunk);
-  else if (per <= 16) skinny_k_kernel<16><<<grid, SK_THREADS, 0, st>>>(g, nchunk);
-  else skinny_k_kernel<32><<<grid, SK_THREADS, 0, st>>>(g, nchunk);
+  if (g.M <= 8 && g.K <= 8) skinny_k_kernel<8, 8><<<grid, SK_THREADS, 0, st>>>(g, nchunk);
+  else skinny_k_kernel<SK_MAXM, SK_MAXK><<<grid, SK_THREADS, 0, st>>>(g, nchunk);
   return cudaGetLastError();
 }
 

@@ -151,7 +151,16 @@ lrcc_status Runtime::init(const lrcc_dims& d, int64_t ws_budget) {
   return LRCC_OK;
 }
 
-bool Runtime::use_packed(const Gemm& g) const { return g.M >= 96 && g.N >= 96 && g.K >= 16; }
+// Packed-operand tensor-core path for GEMMs with both output dimensions at least
+// LRCC_PACKED_MIN (default 96) and K >= 16; the autotuner may also choose it per op.
+bool Runtime::use_packed(const Gemm& g) const {
+  static const int pmin = []() {
+    const char* e = std::getenv("LRCC_PACKED_MIN");
+    const int v = e ? std::atoi(e) : 0;
+    return v > 0 ? v : 96;
+  }();
+  return g.M >= pmin && g.N >= pmin && g.K >= 16;
+}
 
 // Useful fraction of the unpacked tensor-core tiles (128 x 64 complex, K in steps of 16)
 // for an M x N x K GEMM.
@@ -396,6 +405,10 @@ static int reduce_split(const Gemm& g, const GemmDesc& d) {
 
 GemmChoice Runtime::default_choice(const Gemm& g, const GemmDesc& d, int prec) const {
   GemmChoice c;
+  if (prec > 0 && use_packed(g)) {
+    c.packed = true;
+    return c;
+  }
   const GemmArgs sa = shape_args(g);
   if (skinny_k_ok(sa)) {
     c.special = 1;
@@ -505,7 +518,6 @@ lrcc_status Runtime::autotune(const Program& pr, double2* const ar[AR_COUNT], in
     if (op.kind != OP_GEMM) continue;
     const Gemm& g = plan.gemms[op.idx];
     if (g.arC == AR_FIX) continue;  // never disturb fixed data
-    if (prec > 0 && use_packed(g)) continue;
     const GemmDesc& d = gdesc[op.idx];
     const int nr = op.fixed_only ? 1 : nrhs;
     GemmArgs a;
@@ -520,12 +532,16 @@ lrcc_status Runtime::autotune(const Program& pr, double2* const ar[AR_COUNT], in
     a.sA = op.fixed_only ? 0 : stride[g.arA];
     a.sB = op.fixed_only ? 0 : stride[g.arB];
     a.sC = op.fixed_only ? 0 : stride[g.arC];
+    auto one = [&](const GemmChoice& c) -> lrcc_status {
+      return c.packed ? run_packed(op.idx, g, ar, nr, op.fixed_only != 0, stride, st, prec)
+                      : launch_gemm(a, g, c, nr, st, prec);
+    };
     auto time_it = [&](const GemmChoice& c, float& ms) -> lrcc_status {
-      lrcc_status s2 = launch_gemm(a, g, c, nr, st, prec);
+      lrcc_status s2 = one(c);
       if (s2 != LRCC_OK) return s2;
       if (!ck(cudaEventRecord(e0, st), "autotune record")) return LRCC_ECUDA;
       for (int r = 0; r < 2; ++r)
-        if ((s2 = launch_gemm(a, g, c, nr, st, prec)) != LRCC_OK) return s2;
+        if ((s2 = one(c)) != LRCC_OK) return s2;
       if (!ck(cudaEventRecord(e1, st), "autotune record") || !ck(cudaEventSynchronize(e1), "autotune sync") ||
           !ck(cudaEventElapsedTime(&ms, e0, e1), "autotune elapsed"))
         return LRCC_ECUDA;
@@ -538,6 +554,11 @@ lrcc_status Runtime::autotune(const Program& pr, double2* const ar[AR_COUNT], in
     if (best_ms < 100.f) {
       std::vector<GemmChoice> cand;
       const bool tc_ok = prec > 0;
+      if (tc_ok && !def.packed && g.M >= 8 && g.N >= 8 && g.K >= 8) {
+        GemmChoice pk;
+        pk.packed = true;
+        cand.push_back(pk);
+      }
       for (int tc = 0; tc <= (tc_ok ? 1 : 0); ++tc)
         for (int t = 0; t < (tc ? 1 : GT_COUNT); ++t) {
           GemmChoice c;
@@ -550,7 +571,9 @@ lrcc_status Runtime::autotune(const Program& pr, double2* const ar[AR_COUNT], in
             c.nsplit = sp;
             bool dup = false;
             for (const auto& x : cand) dup = dup || (x.tc == c.tc && x.tile == c.tile && x.nsplit == c.nsplit);
-            if (!dup && !(c.tc == def.tc && c.tile == def.tile && c.nsplit == def.nsplit)) cand.push_back(c);
+            if (!dup && !(!def.packed && c.tc == def.tc && c.tile == def.tile && c.nsplit == def.nsplit &&
+                          def.special == 0))
+              cand.push_back(c);
           }
         }
       for (const auto& c : cand) {
@@ -614,15 +637,15 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
       a.sA = op.fixed_only ? 0 : stride[g.arA];
       a.sB = op.fixed_only ? 0 : stride[g.arB];
       a.sC = op.fixed_only ? 0 : stride[g.arC];
-      if (prec > 0 && use_packed(g)) {
+      GemmChoice c = default_choice(g, d, prec);
+      if (tuned) {
+        auto t = tuned->find(op.idx);
+        if (t != tuned->end()) c = t->second;
+      }
+      if (prec > 0 && c.packed) {
         lrcc_status ps = run_packed(op.idx, g, ar, nr, op.fixed_only != 0, stride, st, prec);
         if (ps != LRCC_OK) return ps;
       } else {
-        GemmChoice c = default_choice(g, d, prec);
-        if (tuned) {
-          auto t = tuned->find(op.idx);
-          if (t != tuned->end()) c = t->second;
-        }
         lrcc_status gs = launch_gemm(a, g, c, nr, st, prec);
         if (gs != LRCC_OK) return gs;
       }

@@ -18,6 +18,7 @@ struct GemmChoice {
   int tile = 0;     // FP64 kernel tile (gemm_tile_dims)
   int nsplit = 1;   // split-K factor
   int special = 0;  // 1: short-contraction FP64 kernel; 2: tiny-output FP64 reduction kernel
+  bool packed = false;  // packed-operand tensor-core GEMM (mixed precision)
 };
 
 struct GemmDesc {
