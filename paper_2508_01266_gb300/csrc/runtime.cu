@@ -152,12 +152,12 @@ lrcc_status Runtime::init(const lrcc_dims& d, int64_t ws_budget) {
 }
 
 // Packed-operand tensor-core path for GEMMs with both output dimensions at least
-// LRCC_PACKED_MIN (default 96) and K >= 16; the autotuner may also choose it per op.
+// LRCC_PACKED_MIN (default 32) and K >= 16; the autotuner may also choose it per op.
 bool Runtime::use_packed(const Gemm& g) const {
   static const int pmin = []() {
     const char* e = std::getenv("LRCC_PACKED_MIN");
     const int v = e ? std::atoi(e) : 0;
-    return v > 0 ? v : 96;
+    return v > 0 ? v : 32;
   }();
   return g.M >= pmin && g.N >= pmin && g.K >= 16;
 }
@@ -410,10 +410,6 @@ GemmChoice Runtime::default_choice(const Gemm& g, const GemmDesc& d, int prec) c
     return c;
   }
   const GemmArgs sa = shape_args(g);
-  if (skinny_k_ok(sa)) {
-    c.special = 1;
-    return c;
-  }
   if (reduce_small_ok(sa) && !no_split) {
     c.special = 2;
     c.nsplit = reduce_split(g, d);
@@ -536,15 +532,26 @@ lrcc_status Runtime::autotune(const Program& pr, double2* const ar[AR_COUNT], in
       return c.packed ? run_packed(op.idx, g, ar, nr, op.fixed_only != 0, stride, st, prec)
                       : launch_gemm(a, g, c, nr, st, prec);
     };
+    float best_seen = 1e30f;
     auto time_it = [&](const GemmChoice& c, float& ms) -> lrcc_status {
+      if (!ck(cudaEventRecord(e0, st), "autotune record")) return LRCC_ECUDA;
       lrcc_status s2 = one(c);
       if (s2 != LRCC_OK) return s2;
+      float first = 0.f;
+      if (!ck(cudaEventRecord(e1, st), "autotune record") || !ck(cudaEventSynchronize(e1), "autotune sync") ||
+          !ck(cudaEventElapsedTime(&first, e0, e1), "autotune elapsed"))
+        return LRCC_ECUDA;
+      if (first > 3.f * best_seen) {  // far slower than the best so far: not worth timing
+        ms = 1e30f;
+        return LRCC_OK;
+      }
       if (!ck(cudaEventRecord(e0, st), "autotune record")) return LRCC_ECUDA;
       for (int r = 0; r < 2; ++r)
         if ((s2 = one(c)) != LRCC_OK) return s2;
       if (!ck(cudaEventRecord(e1, st), "autotune record") || !ck(cudaEventSynchronize(e1), "autotune sync") ||
           !ck(cudaEventElapsedTime(&ms, e0, e1), "autotune elapsed"))
         return LRCC_ECUDA;
+      best_seen = std::min(best_seen, ms / 2.f);
       return LRCC_OK;
     };
     const GemmChoice def = default_choice(g, d, prec);
@@ -552,6 +559,10 @@ lrcc_status Runtime::autotune(const Program& pr, double2* const ar[AR_COUNT], in
     if ((rs = time_it(def, best_ms)) != LRCC_OK) break;
     GemmChoice best = def;
     if (best_ms < 100.f) {
+      // candidates: mixed precision tries the tensor-core paths (packed, unpacked with
+      // split factors) and the FP64 kernels only for ops already under a millisecond;
+      // FP64 tries every tile shape with split factors.  A candidate whose first launch
+      // takes over three times the best so far is dropped without the timed launches.
       std::vector<GemmChoice> cand;
       const bool tc_ok = prec > 0;
       if (tc_ok && !def.packed && g.M >= 8 && g.N >= 8 && g.K >= 8) {
@@ -559,7 +570,14 @@ lrcc_status Runtime::autotune(const Program& pr, double2* const ar[AR_COUNT], in
         pk.packed = true;
         cand.push_back(pk);
       }
-      for (int tc = 0; tc <= (tc_ok ? 1 : 0); ++tc)
+      if (def.special != 1 && skinny_k_ok(shape_args(g))) {
+        GemmChoice sk;
+        sk.special = 1;
+        cand.push_back(sk);
+      }
+      const bool try_f64 = !tc_ok || best_ms < 1.f;
+      for (int tc = tc_ok ? 1 : 0; tc >= 0; --tc) {
+        if (tc == 0 && !try_f64) continue;
         for (int t = 0; t < (tc ? 1 : GT_COUNT); ++t) {
           GemmChoice c;
           c.tc = tc != 0;
@@ -570,12 +588,14 @@ lrcc_status Runtime::autotune(const Program& pr, double2* const ar[AR_COUNT], in
           for (int sp : {1, s0, std::max(1, s0 / 2), s0 * 2}) {
             c.nsplit = sp;
             bool dup = false;
-            for (const auto& x : cand) dup = dup || (x.tc == c.tc && x.tile == c.tile && x.nsplit == c.nsplit);
+            for (const auto& x : cand)
+              dup = dup || (!x.packed && x.special == 0 && x.tc == c.tc && x.tile == c.tile && x.nsplit == c.nsplit);
             if (!dup && !(!def.packed && c.tc == def.tc && c.tile == def.tile && c.nsplit == def.nsplit &&
                           def.special == 0))
               cand.push_back(c);
           }
         }
+      }
       for (const auto& c : cand) {
         float ms = 0.f;
         if ((rs = time_it(c, ms)) != LRCC_OK) break;
