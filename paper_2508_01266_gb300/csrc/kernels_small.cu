@@ -69,15 +69,16 @@ __global__ void __launch_bounds__(SK_THREADS) skinny_k_kernel(GemmArgs g, int nc
   }
   if (n >= N) return;
   double2* Cp = g.C + rhs * g.sC + g.coff[batch];
+  double2 cv[MM];  // all loads first, then the stores (no load waits on a store)
+#pragma unroll
+  for (int m = 0; m < MM; ++m)
+    if (m < M) cv[m] = Cp[(long long)m * g.ldc + n];
 #pragma unroll
   for (int m = 0; m < MM; ++m) {
     if (m >= M) break;
-    const double vr = g.ar * acc[m].x - g.ai * acc[m].y, vi = g.ar * acc[m].y + g.ai * acc[m].x;
-    double2* cp = Cp + (long long)m * g.ldc + n;
-    double2 cv = *cp;
-    cv.x += vr;
-    cv.y += vi;
-    *cp = cv;
+    cv[m].x += g.ar * acc[m].x - g.ai * acc[m].y;
+    cv[m].y += g.ar * acc[m].y + g.ai * acc[m].x;
+    Cp[(long long)m * g.ldc + n] = cv[m];
   }
 }
 

@@ -264,7 +264,28 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(GemmArgs g, int* er
             "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
           : "r"(ta));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (m < M) {
+      if (m < M && !Pp && g.epi == 0) {
+        // all loads first, then the stores (no load waits on a store)
+        const int cnt = min(8, N - (n0 + c0 / 2));
+        double2 cv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (j >= cnt) break;
+          const int n = n0 + c0 / 2 + j;
+          const int mo = g.swap ? n : m, no = g.swap ? m : n;  // element of the original C
+          cv[j] = Cp[(long long)mo * g.ldc + no];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (j >= cnt) break;
+          const int n = n0 + c0 / 2 + j;
+          const int mo = g.swap ? n : m, no = g.swap ? m : n;
+          const double ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
+          cv[j].x += g.ar * ar - g.ai * ai;
+          cv[j].y += g.ar * ai + g.ai * ar;
+          Cp[(long long)mo * g.ldc + no] = cv[j];
+        }
+      } else if (m < M) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int n = n0 + c0 / 2 + j;
@@ -276,13 +297,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(GemmArgs g, int* er
             continue;
           }
           const double vr = g.ar * ar - g.ai * ai, vi = g.ar * ai + g.ai * ar;
-          if (g.epi == 0) {
-            double2* cp = Cp + (long long)mo * g.ldc + no;
-            double2 cv = *cp;
-            cv.x += vr;
-            cv.y += vi;
-            *cp = cv;
-          } else {
+          {
             const int a = mo / g.ep2, c = mo - a * g.ep2;
             const int b = no / g.ep3, d = no - b * g.ep3;
             Cp[(((long long)a * g.ep1 + b) * g.ep2 + c) * g.ep3 + d] = make_double2(vr, vi);

@@ -319,20 +319,30 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_kernel(PGemmArgs g, int
               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
             : "r"(ta));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
-        if (m < g.M) {
+        if (m < g.M && g.epi == 0) {
+          const int nb = nt * (P_BNR / 2) + c0 / 2;
+          const int cnt = min(8, g.N - nb);
+          double2* cp = Cp + (long long)m * g.ldc + nb;
+          double2 cv[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (j < cnt) cv[j] = cp[j];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            if (j >= cnt) break;
+            const double ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
+            cv[j].x += g.ar * ar - g.ai * ai;
+            cv[j].y += g.ar * ai + g.ai * ar;
+            cp[j] = cv[j];
+          }
+        } else if (m < g.M) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int n = nt * (P_BNR / 2) + c0 / 2 + j;
             if (n >= g.N) break;
             const double ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
             const double vr = g.ar * ar - g.ai * ai, vi = g.ar * ai + g.ai * ar;
-            if (g.epi == 0) {
-              double2* cp = Cp + (long long)m * g.ldc + n;
-              double2 cv = *cp;
-              cv.x += vr;
-              cv.y += vi;
-              *cp = cv;
-            } else {
+            {
               const int a = m / g.ep2, c = m - a * g.ep2;
               const int b = n / g.ep3, d = n - b * g.ep3;
               Cp[(((long long)a * g.ep1 + b) * g.ep2 + c) * g.ep3 + d] = make_double2(vr, vi);
@@ -596,19 +606,30 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
           for (int j = 0; j < 16; ++j) r[j] = 0u;
         }
         if (m < g.M && (total > 0 || g.epi == 1)) {
+          const int nb = nt * (P_BNR / 2) + c0 / 2;
+          const int cnt = min(8, g.N - nb);
+          if (g.epi == 0) {
+            // all loads of the row segment first, then the stores (no load waits on a store)
+            double2* cp = Cp + (long long)m * g.ldc + nb;
+            double2 cv[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int n = nt * (P_BNR / 2) + c0 / 2 + j;
-            if (n >= g.N) break;
-            const double ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
-            const double vr = g.ar * ar - g.ai * ai, vi = g.ar * ai + g.ai * ar;
-            if (g.epi == 0) {
-              double2* cp = Cp + (long long)m * g.ldc + n;
-              double2 cv = *cp;
-              cv.x += vr;
-              cv.y += vi;
-              *cp = cv;
-            } else {
+            for (int j = 0; j < 8; ++j)
+              if (j < cnt) cv[j] = cp[j];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              if (j >= cnt) break;
+              const double ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
+              cv[j].x += g.ar * ar - g.ai * ai;
+              cv[j].y += g.ar * ai + g.ai * ar;
+              cp[j] = cv[j];
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              if (j >= cnt) break;
+              const int n = nb + j;
+              const double ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
+              const double vr = g.ar * ar - g.ai * ai, vi = g.ar * ai + g.ai * ar;
               const int a = m / g.ep2, c = m - a * g.ep2;
               const int bb = n / g.ep3, d = n - bb * g.ep3;
               Cp[(((long long)a * g.ep1 + bb) * g.ep2 + c) * g.ep3 + d] = make_double2(vr, vi);
