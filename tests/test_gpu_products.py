@@ -160,3 +160,24 @@ def test_chunked_batch_bitwise(lr):
         ref = prob.jacobian_apply(X1, X2, transpose=tr)
         got = prob.jacobian_apply(X1, X2, transpose=tr, options=lr.default_options(max_batch=2))
         assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
+
+
+def test_c2_transpose_bilinear_identity(lr):
+    """Full C2 size: <y, A x> = <A^T y, x> (plain pairing; y pair-symmetric) for FP64 and,
+    to its precision, BF16x3 — a property that holds at any size."""
+    c = CONFIGS["c2"]
+    nk, o, v, Q = c["nk"], c["nocc"], c["nvir"], c["naux"]
+    p, prob, t1, t2 = _setup(lr, nk, o, v, Q, seed=1266, sigma=0.02, tscale=0.01)
+    dev = torch.device("cuda")
+    x1, x2 = random_probe(nk, o, v, seed=31, nrhs=1)
+    y1, y2 = random_probe(nk, o, v, seed=32, nrhs=1)
+    X = (torch.as_tensor(x1, device=dev), torch.as_tensor(x2 * nk, device=dev))
+    Y = (torch.as_tensor(y1, device=dev), torch.as_tensor(y2 * nk, device=dev))
+    for prec, tol in ((0, 1e-12), (2, 1e-4)):
+        opt = lr.default_options(precision=prec)
+        a1, a2 = prob.jacobian_apply(*X, options=opt)
+        b1, b2 = prob.jacobian_apply(*Y, transpose=True, options=opt)
+        lhs = complex((Y[0] * a1).sum() + (Y[1] * a2).sum())
+        rhs = complex((b1 * X[0]).sum() + (b2 * X[1]).sum())
+        assert abs(lhs - rhs) < tol * abs(lhs), (prec, lhs, rhs)
+    prob.close()
