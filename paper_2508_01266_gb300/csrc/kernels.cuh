@@ -58,12 +58,14 @@ void gemm_tile_dims(int tile, int* bm, int* bn);
 int gemm_pick_tile(int M, int N);
 
 cudaError_t launch_gemm_f64(const GemmArgs& g, int tile, int nrhs, cudaStream_t st);
+// the same tiled GEMM with FP32 arithmetic (FP64 operands and destination)
+cudaError_t launch_gemm_f32(const GemmArgs& g, int tile, int nrhs, cudaStream_t st);
 cudaError_t launch_split_reduce(const GemmArgs& g, int nrhs, cudaStream_t st);
-// short-contraction and tiny-output FP64 GEMM kernels (kernels_small.cu)
+// short-contraction and tiny-output GEMM kernels (kernels_small.cu); f32: FP32 arithmetic
 bool skinny_k_ok(const GemmArgs& g);
-cudaError_t launch_skinny_k(const GemmArgs& g, int nrhs, cudaStream_t st);
+cudaError_t launch_skinny_k(const GemmArgs& g, int nrhs, cudaStream_t st, bool f32);
 bool reduce_small_ok(const GemmArgs& g);
-cudaError_t launch_reduce_small(const GemmArgs& g, int nrhs, cudaStream_t st);
+cudaError_t launch_reduce_small(const GemmArgs& g, int nrhs, cudaStream_t st, bool f32);
 constexpr int F64_BK = 8;  // complex K per iteration of the FP64 GEMM
 constexpr int TC_BK = 16;  // complex K per iteration of the unpacked tensor-core GEMM
 cudaError_t launch_perm_f64(const PermArgs& p, int nrhs, cudaStream_t st);

@@ -5,6 +5,13 @@
 // FP64 contraction in this path, so the GEMM is a shared-memory tiled DFMA kernel:
 // each thread owns a TM x TN register tile of complex accumulators (4 DFMA per
 // complex MAC); tiles are picked per op to minimise padded work.
+//
+// The same GEMM with FP32 arithmetic (operands rounded to FP32 when staged in shared
+// memory, FP32 accumulators, the FP64 destination updated in FP64) serves the mixed-
+// precision products for the small-tile shapes that would leave tensor-core tiles mostly
+// padding: at 2 flops per byte they are FP64-pipe bound but HBM bound in FP32, and the
+// FP32 rounding (2^-24 per operand, chains capped by the caller) is far below the
+// BF16x3 operand split's.
 #include <cstdio>
 
 #include "kernels.cuh"
@@ -16,12 +23,28 @@ __device__ __forceinline__ int kmod(int a, int n) {
   return a < 0 ? a + n : a;
 }
 
-template <int BM, int BN, int BK, int TM, int TN>
+template <typename T> struct Cplx;
+template <> struct Cplx<double> {
+  using t = double2;
+  static __device__ __forceinline__ double2 from(double2 v) { return v; }
+  static __device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
+};
+template <> struct Cplx<float> {
+  using t = float2;
+  static __device__ __forceinline__ float2 from(double2 v) {
+    return make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+  }
+  static __device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
+};
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     zgemm_seg_kernel(GemmArgs g) {
   constexpr int NTX = BN / TN, NTY = BM / TM, NT = NTX * NTY;
-  __shared__ double2 As[BK][BM];
-  __shared__ double2 Bs[BK][BN];
+  using C2 = Cplx<T>;
+  using V2 = typename C2::t;
+  __shared__ V2 As[BK][BM];
+  __shared__ V2 Bs[BK][BN];
   const int tpb = g.tiles_m * g.tiles_n;
   const int bid = blockIdx.x;
   const int per_batch = tpb * g.nsplit;
@@ -38,13 +61,13 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   const int tid = threadIdx.x;
   const int tx = tid % NTX, ty = tid / NTX;
   const int M = g.M, N = g.N, K = g.K;
-  double accr[TM][TN], acci[TM][TN];
+  T accr[TM][TN], acci[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
-      accr[i][j] = 0.0;
-      acci[i][j] = 0.0;
+      accr[i][j] = T(0);
+      acci[i][j] = T(0);
     }
   // iteration space of this batch entry: (segment, K block), segment-major; this CTA
   // takes the split's contiguous range of it
@@ -70,7 +93,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         const int gm = m0 + m, gk = k0 + k;
         double2 val = make_double2(0.0, 0.0);
         if (gm < M && gk < K) val = g.ta ? Ap[(long long)gk * g.lda + gm] : Ap[(long long)gm * g.lda + gk];
-        As[k][m] = val;
+        As[k][m] = C2::from(val);
       }
       for (int idx = tid; idx < BK * BN; idx += NT) {
         int k, n;
@@ -84,12 +107,12 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         const int gn = n0 + n, gk = k0 + k;
         double2 val = make_double2(0.0, 0.0);
         if (gn < N && gk < K) val = g.tb ? Bp[(long long)gn * g.ldb + gk] : Bp[(long long)gk * g.ldb + gn];
-        Bs[k][n] = val;
+        Bs[k][n] = C2::from(val);
       }
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        double2 a[TM], b[TN];
+        V2 a[TM], b[TN];
 #pragma unroll
         for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * NTY];
 #pragma unroll
@@ -98,10 +121,10 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         for (int i = 0; i < TM; ++i)
 #pragma unroll
           for (int j = 0; j < TN; ++j) {
-            accr[i][j] = fma(a[i].x, b[j].x, accr[i][j]);
-            accr[i][j] = fma(-a[i].y, b[j].y, accr[i][j]);
-            acci[i][j] = fma(a[i].x, b[j].y, acci[i][j]);
-            acci[i][j] = fma(a[i].y, b[j].x, acci[i][j]);
+            accr[i][j] = C2::mad(a[i].x, b[j].x, accr[i][j]);
+            accr[i][j] = C2::mad(-a[i].y, b[j].y, accr[i][j]);
+            acci[i][j] = C2::mad(a[i].x, b[j].y, acci[i][j]);
+            acci[i][j] = C2::mad(a[i].y, b[j].x, acci[i][j]);
           }
       }
       __syncthreads();
@@ -120,7 +143,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
         const int n = n0 + tx + j * NTX;
-        if (n < N) Pp[(long long)m * N + n] = make_double2(accr[i][j], acci[i][j]);
+        if (n < N) Pp[(long long)m * N + n] = make_double2((double)accr[i][j], (double)acci[i][j]);
       }
     }
     return;
@@ -142,8 +165,9 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         const int b = n / g.ep3, d = n - b * g.ep3;
         addr = (((long long)a * g.ep1 + b) * g.ep2 + c) * g.ep3 + d;
       }
-      const double vr = g.ar * accr[i][j] - g.ai * acci[i][j];
-      const double vi = g.ar * acci[i][j] + g.ai * accr[i][j];
+      const double ur = (double)accr[i][j], ui = (double)acci[i][j];
+      const double vr = g.ar * ur - g.ai * ui;
+      const double vi = g.ar * ui + g.ai * ur;
       if (g.epi == 0) {
         double2 cv = Cp[addr];
         cv.x += vr;
@@ -224,7 +248,7 @@ int gemm_pick_tile(int M, int N) {
   return best;
 }
 
-template <int BM, int BN, int TM, int TN>
+template <typename T, int BM, int BN, int TM, int TN>
 static cudaError_t launch_t(GemmArgs g, int nrhs, cudaStream_t st) {
   g.tiles_m = (g.M + BM - 1) / BM;
   g.tiles_n = (g.N + BN - 1) / BN;
@@ -233,24 +257,33 @@ static cudaError_t launch_t(GemmArgs g, int nrhs, cudaStream_t st) {
   if (nblk <= 0) return cudaSuccess;
   if (nblk > 2147483647LL || nrhs > 65535) return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)nblk, (unsigned)nrhs);
-  zgemm_seg_kernel<BM, BN, F64_BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(g);
+  zgemm_seg_kernel<T, BM, BN, F64_BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(g);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_f64(const GemmArgs& g, int tile, int nrhs, cudaStream_t st) {
+template <typename T>
+static cudaError_t launch_tile(const GemmArgs& g, int tile, int nrhs, cudaStream_t st) {
   switch (tile) {
-    case GT_64x64: return launch_t<64, 64, 4, 4>(g, nrhs, st);
-    case GT_32x64: return launch_t<32, 64, 2, 4>(g, nrhs, st);
-    case GT_64x32: return launch_t<64, 32, 4, 2>(g, nrhs, st);
-    case GT_32x32: return launch_t<32, 32, 2, 2>(g, nrhs, st);
-    case GT_16x64: return launch_t<16, 64, 1, 4>(g, nrhs, st);
-    case GT_64x16: return launch_t<64, 16, 4, 1>(g, nrhs, st);
-    case GT_16x16: return launch_t<16, 16, 1, 1>(g, nrhs, st);
-    case GT_8x32: return launch_t<8, 32, 1, 1>(g, nrhs, st);
-    case GT_1x256: return launch_t<1, 256, 1, 1>(g, nrhs, st);
-    case GT_256x1: return launch_t<256, 1, 1, 1>(g, nrhs, st);
+    case GT_64x64: return launch_t<T, 64, 64, 4, 4>(g, nrhs, st);
+    case GT_32x64: return launch_t<T, 32, 64, 2, 4>(g, nrhs, st);
+    case GT_64x32: return launch_t<T, 64, 32, 4, 2>(g, nrhs, st);
+    case GT_32x32: return launch_t<T, 32, 32, 2, 2>(g, nrhs, st);
+    case GT_16x64: return launch_t<T, 16, 64, 1, 4>(g, nrhs, st);
+    case GT_64x16: return launch_t<T, 64, 16, 4, 1>(g, nrhs, st);
+    case GT_16x16: return launch_t<T, 16, 16, 1, 1>(g, nrhs, st);
+    case GT_8x32: return launch_t<T, 8, 32, 1, 1>(g, nrhs, st);
+    case GT_1x256: return launch_t<T, 1, 256, 1, 1>(g, nrhs, st);
+    case GT_256x1: return launch_t<T, 256, 1, 1, 1>(g, nrhs, st);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gemm_f64(const GemmArgs& g, int tile, int nrhs, cudaStream_t st) {
+  return launch_tile<double>(g, tile, nrhs, st);
+}
+
+cudaError_t launch_gemm_f32(const GemmArgs& g, int tile, int nrhs, cudaStream_t st) {
+  return launch_tile<float>(g, tile, nrhs, st);
 }
 
 // --------------------------------------------------------------------------

@@ -571,9 +571,25 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
                      su32(&donebar))
                  : "memory");
   } else if (warp >= 2) {
-    // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31
+    // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31.  The read-modify-write of the
+    // FP64 destination dominates short contractions, so the C rows of this CTA's next
+    // tile are prefetched into L2 while the current tile drains, and each step keeps 16
+    // complex loads of a row in flight.
     const int q = warp & 3;
+    auto prefetch_c = [&](long long tl) {
+      if (g.epi != 0 || tl >= ntiles) return;
+      int prhs, pbatch, pmt, pnt;
+      decode_tile(g, tl, prhs, pbatch, pmt, pnt);
+      const int pm = pmt * P_BM + q * 32 + lane;
+      const int nb0 = pnt * (P_BNR / 2);
+      if (pm >= g.M || nb0 >= g.N) return;
+      const int cnt = min(P_BNR / 2, g.N - nb0);
+      const double2* row = g.C + prhs * g.sC + g.coff[pbatch] + (long long)pm * g.ldc + nb0;
+      for (int j = 0; j < cnt; j += 8) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + j));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(row + cnt - 1));
+    };
     int local = 0;
+    if (blockIdx.x < ntiles) prefetch_c(blockIdx.x);
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++local) {
       int rhs, batch, mt, nt;
       decode_tile(g, tile, rhs, batch, mt, nt);
@@ -586,11 +602,12 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
+      prefetch_c(tile + gridDim.x);
       const int m = mt * P_BM + q * 32 + lane;
       double2* Cp = g.C + rhs * g.sC + g.coff[batch];
 #pragma unroll 1
-      for (int c0 = 0; c0 < P_BNR; c0 += 16) {
-        uint32_t r[16];
+      for (int c0 = 0; c0 < P_BNR; c0 += 32) {
+        uint32_t r[32];
         if (total > 0) {
           const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * P_BNR + c0);
           asm volatile(
@@ -600,23 +617,30 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
                 "=r"(r[15])
               : "r"(ta));
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];"
+              : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+                "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                "=r"(r[30]), "=r"(r[31])
+              : "r"(ta + 16u));
           asm volatile("tcgen05.wait::ld.sync.aligned;");
         } else {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) r[j] = 0u;
+          for (int j = 0; j < 32; ++j) r[j] = 0u;
         }
         if (m < g.M && (total > 0 || g.epi == 1)) {
           const int nb = nt * (P_BNR / 2) + c0 / 2;
-          const int cnt = min(8, g.N - nb);
+          const int cnt = min(16, g.N - nb);
           if (g.epi == 0) {
             // all loads of the row segment first, then the stores (no load waits on a store)
             double2* cp = Cp + (long long)m * g.ldc + nb;
-            double2 cv[8];
+            double2 cv[16];
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
+            for (int j = 0; j < 16; ++j)
               if (j < cnt) cv[j] = cp[j];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < 16; ++j) {
               if (j >= cnt) break;
               const double ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
               cv[j].x += g.ar * ar - g.ai * ai;
@@ -625,7 +649,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
             }
           } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < 16; ++j) {
               if (j >= cnt) break;
               const int n = nb + j;
               const double ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);

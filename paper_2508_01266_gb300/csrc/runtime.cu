@@ -9,6 +9,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -151,15 +152,50 @@ lrcc_status Runtime::init(const lrcc_dims& d, int64_t ws_budget) {
   return LRCC_OK;
 }
 
+// Longest contraction (complex terms: segments x K) that one FP32 tensor-core
+// accumulator may sum.  The FP32 rounding of a chain grows with its length (about
+// sqrt(n) u32 typically, n u32 at worst); at 8192 terms the BF16x3 products stay within
+// 1e-5 of FP64 on the workloads, while chains of 64000 (the o x o and v x v
+// intermediates summed over three momenta) reached 2e-4.  Longer contractions take the
+// unpacked kernel with enough K splits, whose partials are summed in FP64.
+constexpr long long TC_CHAIN_MAX = 8192;
+
+static long long chain_len(const Gemm& g, const GemmDesc& d) { return (long long)d.max_seg * g.K; }
+
+// Fewest K splits that keep every FP32 accumulator chain of the unpacked tensor-core
+// kernel within TC_CHAIN_MAX (its splits take equal shares of the (segment, K tile) range).
+static int tc_min_split(const Gemm& g, const GemmDesc& d) {
+  const long long iters = (long long)d.max_seg * ((g.K + TC_BK - 1) / TC_BK);
+  const long long per = TC_CHAIN_MAX / TC_BK;
+  return (int)std::max<long long>(1, (iters + per - 1) / per);
+}
+// The same bound for the tiled GEMM with FP32 arithmetic (K blocks of F64_BK).
+static int f32_min_split(const Gemm& g, const GemmDesc& d) {
+  const long long iters = (long long)d.max_seg * ((g.K + F64_BK - 1) / F64_BK);
+  const long long per = TC_CHAIN_MAX / F64_BK;
+  return (int)std::max<long long>(1, (iters + per - 1) / per);
+}
+// FP32 tiny-output reduction: a lane sums ceil(K / 32) terms per segment over its split's
+// whole segments, then 32 lanes meet in the shuffle tree; keep lanes x chain within
+// TC_CHAIN_MAX.  0: not possible (one segment alone is too long).
+static int reduce_f32_min_split(const Gemm& g, const GemmDesc& d) {
+  const long long lane = (g.K + 31) / 32;
+  const long long segs = (TC_CHAIN_MAX / 32) / std::max<long long>(lane, 1);
+  if (segs < 1) return 0;
+  return (int)std::max<long long>(1, (d.max_seg + segs - 1) / segs);
+}
+
 // Packed-operand tensor-core path for GEMMs with both output dimensions at least
-// LRCC_PACKED_MIN (default 32) and K >= 16; the autotuner may also choose it per op.
-bool Runtime::use_packed(const Gemm& g) const {
+// LRCC_PACKED_MIN (default 32), K >= 16 and a contraction within TC_CHAIN_MAX (the
+// packed kernel sums a tile's whole contraction in one FP32 accumulator); the
+// autotuner may also choose it per op, under the same chain limit.
+bool Runtime::use_packed(const Gemm& g, const GemmDesc& d) const {
   static const int pmin = []() {
     const char* e = std::getenv("LRCC_PACKED_MIN");
     const int v = e ? std::atoi(e) : 0;
     return v > 0 ? v : 32;
   }();
-  return g.M >= pmin && g.N >= pmin && g.K >= 16;
+  return g.M >= pmin && g.N >= pmin && g.K >= 16 && chain_len(g, d) <= TC_CHAIN_MAX;
 }
 
 // Useful fraction of the unpacked tensor-core tiles (128 x 64 complex, K in steps of 16)
@@ -179,11 +215,17 @@ static bool tc_tile_useful(const Gemm& g) {
 
 // Split-K factor: enough CTAs to fill the 152 SMs a few times over when the output
 // tiles of one vector cannot, keeping at least 8 K iterations per split and the
-// partials of one vector under 64 MiB.  The choice does not depend on the number of
-// vectors, so a vector's result is bitwise the same in any batch.
-int Runtime::pick_split(const Gemm& g, const GemmDesc& d, int nr, bool tc) const {
-  (void)nr;
+// partials of one vector under 64 MiB; with FP32 accumulation (tensor cores or FP32
+// arithmetic) at least the split that caps the accumulator chains.  The
+// choice does not depend on the number of vectors, so a vector's result is bitwise the
+// same in any batch.
+int Runtime::pick_split(const Gemm& g, const GemmDesc& d, int nr, bool tc, bool f32) const {
   if (no_split) return 1;
+  return std::max(pick_split_fill(g, d, nr, tc), tc ? tc_min_split(g, d) : f32 ? f32_min_split(g, d) : 1);
+}
+
+int Runtime::pick_split_fill(const Gemm& g, const GemmDesc& d, int nr, bool tc) const {
+  (void)nr;
   int bm = 128, bn = 64;
   if (!tc) gemm_tile_dims(d.tile, &bm, &bn);
   const bool sw = tc && tc_swap(g);
@@ -403,9 +445,15 @@ static int reduce_split(const Gemm& g, const GemmDesc& d) {
   return (int)std::max<long long>(s, 1);
 }
 
+// Default kernel of a GEMM op.  FP64 products: the tiny-output reduction kernel where it
+// applies, else the FP64 tile kernel.  Mixed precision: the packed tensor-core path for
+// large tiles; the reduction and short-contraction kernels in FP32 arithmetic; the FP32
+// tile kernel where even the better orientation of the unpacked tensor-core tile would
+// be under 20 % useful (small tiles, K <= 40: FP64-pipe bound, HBM bound in FP32); else
+// the unpacked tensor-core kernel.  The autotuner may replace any of these per op.
 GemmChoice Runtime::default_choice(const Gemm& g, const GemmDesc& d, int prec) const {
   GemmChoice c;
-  if (prec > 0 && use_packed(g)) {
+  if (prec > 0 && use_packed(g, d)) {
     c.packed = true;
     return c;
   }
@@ -413,10 +461,25 @@ GemmChoice Runtime::default_choice(const Gemm& g, const GemmDesc& d, int prec) c
   if (reduce_small_ok(sa) && !no_split) {
     c.special = 2;
     c.nsplit = reduce_split(g, d);
+    const int fmin = reduce_f32_min_split(g, d);
+    if (prec > 0 && fmin > 0) {
+      c.f32 = true;
+      c.nsplit = std::max(c.nsplit, fmin);
+    }
+    return c;
+  }
+  if (prec > 0 && skinny_k_ok(sa) && chain_len(g, d) <= TC_CHAIN_MAX) {
+    c.special = 1;
+    c.f32 = true;
+    return c;
+  }
+  c.tile = d.tile;
+  if (prec > 0 && std::max(tc_eff(g.M, g.N, g.K), tc_eff(g.N, g.M, g.K)) < 0.2) {
+    c.f32 = true;
+    c.nsplit = pick_split(g, d, 1, false, true);
     return c;
   }
   c.tc = prec > 0 && tc_tile_useful(g);
-  c.tile = d.tile;
   c.nsplit = pick_split(g, d, 1, c.tc);
   return c;
 }
@@ -428,7 +491,7 @@ lrcc_status Runtime::launch_gemm(GemmArgs a, const Gemm& g, const GemmChoice& c,
     a.nsplit = 1;
     a.part = nullptr;
     ++launches;
-    return ck(launch_skinny_k(a, nr, st), "skinny gemm launch") ? LRCC_OK : LRCC_ECUDA;
+    return ck(launch_skinny_k(a, nr, st, c.f32 && prec > 0), "skinny gemm launch") ? LRCC_OK : LRCC_ECUDA;
   }
   a.nsplit = no_split ? 1 : std::max(1, c.nsplit);
   a.part = nullptr;
@@ -462,7 +525,7 @@ lrcc_status Runtime::launch_gemm(GemmArgs a, const Gemm& g, const GemmChoice& c,
       }
       a.part = part;
     }
-    e = launch_reduce_small(a, nr, st);
+    e = launch_reduce_small(a, nr, st, c.f32 && prec > 0);
     ++launches;
     if (e == cudaSuccess) {
       e = launch_split_reduce(a, nr, st);
@@ -489,7 +552,7 @@ lrcc_status Runtime::launch_gemm(GemmArgs a, const Gemm& g, const GemmChoice& c,
     }
     e = launch_gemm_tc(b, prec, nr, dflag, st);
   } else {
-    e = launch_gemm_f64(a, c.tile, nr, st);
+    e = (c.f32 && prec > 0) ? launch_gemm_f32(a, c.tile, nr, st) : launch_gemm_f64(a, c.tile, nr, st);
   }
   ++launches;
   if (e == cudaSuccess && a.nsplit > 1) {
@@ -500,7 +563,8 @@ lrcc_status Runtime::launch_gemm(GemmArgs a, const Gemm& g, const GemmChoice& c,
 }
 
 // Autotuner: for every unpacked GEMM op of the program, time the candidate kernel
-// choices on the problem's own operands (two launches each after one warm-up, CUDA
+// choices on the problem's own operands (one untimed launch, one timed launch that
+// drops candidates over three times the best so far, then two timed launches; CUDA
 // events) and keep the fastest.  Ops whose default already takes over 50 ms are
 // compute-saturated large GEMMs and keep their default.  The timing launches
 // accumulate into the op's destination, so the caller reruns the product afterwards.
@@ -534,9 +598,12 @@ lrcc_status Runtime::autotune(const Program& pr, double2* const ar[AR_COUNT], in
     };
     float best_seen = 1e30f;
     auto time_it = [&](const GemmChoice& c, float& ms) -> lrcc_status {
-      if (!ck(cudaEventRecord(e0, st), "autotune record")) return LRCC_ECUDA;
+      // an untimed launch first: a kernel's first launch in the process also loads its
+      // code (lazy module loading), which must not count against it
       lrcc_status s2 = one(c);
       if (s2 != LRCC_OK) return s2;
+      if (!ck(cudaEventRecord(e0, st), "autotune record")) return LRCC_ECUDA;
+      if ((s2 = one(c)) != LRCC_OK) return s2;
       float first = 0.f;
       if (!ck(cudaEventRecord(e1, st), "autotune record") || !ck(cudaEventSynchronize(e1), "autotune sync") ||
           !ck(cudaEventElapsedTime(&first, e0, e1), "autotune elapsed"))
@@ -559,41 +626,66 @@ lrcc_status Runtime::autotune(const Program& pr, double2* const ar[AR_COUNT], in
     if ((rs = time_it(def, best_ms)) != LRCC_OK) break;
     GemmChoice best = def;
     if (best_ms < 100.f) {
-      // candidates: mixed precision tries the tensor-core paths (packed, unpacked with
-      // split factors) and the FP64 kernels only for ops already under a millisecond;
-      // FP64 tries every tile shape with split factors.  A candidate whose first launch
-      // takes over three times the best so far is dropped without the timed launches.
+      // candidates: mixed precision tries the tensor-core paths (packed; unpacked with
+      // split factors), the short-contraction kernel and the tile shapes of the tiled
+      // kernel within 25 % of the least padded one, the last two in FP32 arithmetic
+      // (accumulator chains capped by the splits); FP64 tries the short-contraction kernel
+      // and the same FP64 tile shapes with split factors.  A candidate whose first timed
+      // launch takes over three times the best so far is dropped without further launches.
       std::vector<GemmChoice> cand;
-      const bool tc_ok = prec > 0;
-      if (tc_ok && !def.packed && g.M >= 8 && g.N >= 8 && g.K >= 8) {
+      const bool mixed = prec > 0;
+      auto key = [](const GemmChoice& x) {
+        const bool tiled = !x.packed && !x.tc && x.special == 0;
+        return std::make_tuple(x.packed, x.special, x.tc, x.f32, tiled ? x.tile : -1,
+                               (x.packed || x.special == 1) ? 0 : x.nsplit);
+      };
+      auto add = [&](const GemmChoice& c) {
+        if (key(c) == key(def)) return;
+        for (const auto& x : cand)
+          if (key(x) == key(c)) return;
+        cand.push_back(c);
+      };
+      if (mixed && g.M >= 8 && g.N >= 8 && g.K >= 8 && chain_len(g, d) <= TC_CHAIN_MAX) {
         GemmChoice pk;
         pk.packed = true;
-        cand.push_back(pk);
+        add(pk);
       }
-      if (def.special != 1 && skinny_k_ok(shape_args(g))) {
+      if (skinny_k_ok(shape_args(g)) && (!mixed || chain_len(g, d) <= TC_CHAIN_MAX)) {
         GemmChoice sk;
         sk.special = 1;
-        cand.push_back(sk);
+        sk.f32 = mixed;
+        add(sk);
       }
-      const bool try_f64 = !tc_ok || best_ms < 1.f;
-      for (int tc = tc_ok ? 1 : 0; tc >= 0; --tc) {
-        if (tc == 0 && !try_f64) continue;
-        for (int t = 0; t < (tc ? 1 : GT_COUNT); ++t) {
-          GemmChoice c;
-          c.tc = tc != 0;
-          c.tile = tc ? d.tile : t;
-          GemmDesc dd = d;
-          dd.tile = c.tile;
-          const int s0 = pick_split(g, dd, 1, c.tc);
-          for (int sp : {1, s0, std::max(1, s0 / 2), s0 * 2}) {
-            c.nsplit = sp;
-            bool dup = false;
-            for (const auto& x : cand)
-              dup = dup || (!x.packed && x.special == 0 && x.tc == c.tc && x.tile == c.tile && x.nsplit == c.nsplit);
-            if (!dup && !(!def.packed && c.tc == def.tc && c.tile == def.tile && c.nsplit == def.nsplit &&
-                          def.special == 0))
-              cand.push_back(c);
-          }
+      if (mixed) {
+        GemmChoice c;
+        c.tc = true;
+        c.tile = d.tile;
+        const int s0 = pick_split(g, d, 1, true);
+        for (int sp : {1, s0, std::max(1, s0 / 2), s0 * 2}) {
+          c.nsplit = std::max(sp, tc_min_split(g, d));
+          add(c);
+        }
+      }
+      double wmin = 1e300;
+      std::vector<double> wt(GT_COUNT);
+      for (int t = 0; t < GT_COUNT; ++t) {
+        int bm = 1, bn = 1;
+        gemm_tile_dims(t, &bm, &bn);
+        wt[t] = (double)((g.M + bm - 1) / bm) * bm * (double)((g.N + bn - 1) / bn) * bn;
+        wmin = std::min(wmin, wt[t]);
+      }
+      for (int t = 0; t < GT_COUNT; ++t) {
+        if (wt[t] > 1.25 * wmin) continue;
+        GemmChoice c;
+        c.f32 = mixed;
+        c.tile = t;
+        GemmDesc dd = d;
+        dd.tile = t;
+        const int s0 = pick_split(g, dd, 1, false, mixed);
+        const int smin = mixed ? f32_min_split(g, dd) : 1;
+        for (int sp : {1, s0, std::max(1, s0 / 2), s0 * 2}) {
+          c.nsplit = std::max(sp, smin);
+          add(c);
         }
       }
       for (const auto& c : cand) {

@@ -17,8 +17,9 @@ struct GemmChoice {
   bool tc = false;  // tensor-core kernel (mixed precision) instead of the FP64 kernel
   int tile = 0;     // FP64 kernel tile (gemm_tile_dims)
   int nsplit = 1;   // split-K factor
-  int special = 0;  // 1: short-contraction FP64 kernel; 2: tiny-output FP64 reduction kernel
+  int special = 0;  // 1: short-contraction kernel; 2: tiny-output reduction kernel
   bool packed = false;  // packed-operand tensor-core GEMM (mixed precision)
+  bool f32 = false;     // mixed precision: tile / special kernel with FP32 arithmetic
 };
 
 struct GemmDesc {
@@ -76,12 +77,13 @@ struct Runtime {
   size_t packscr_bytes = 0;
   size_t fixpack_bytes = 0;               // cached packs of fixed operands
   size_t fixpack_budget = (size_t)16 << 30;
-  bool use_packed(const Gemm& g) const;
+  bool use_packed(const Gemm& g, const GemmDesc& d) const;
   // split-K partials (grown on demand; never during a call that must not allocate)
   double2* part = nullptr;
   size_t part_bytes = 0;
   bool no_split = false;
-  int pick_split(const Gemm& g, const GemmDesc& d, int nr, bool tc) const;
+  int pick_split(const Gemm& g, const GemmDesc& d, int nr, bool tc, bool f32 = false) const;
+  int pick_split_fill(const Gemm& g, const GemmDesc& d, int nr, bool tc) const;
   lrcc_status run_packed(int gi, const Gemm& g, double2* const ar[AR_COUNT], int nr, bool fixed_only,
                          const long long* stride, cudaStream_t st, int prec);
   // prec: 0 FP64 kernels; 1 TF32 and 2 BF16x3 tensor-core GEMMs (FP32 accumulation)
