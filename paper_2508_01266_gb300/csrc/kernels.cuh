@@ -52,6 +52,7 @@ struct BTransArgs {
 // Tile configurations of the FP64 GEMM kernel.
 enum GemmTile : int {
   GT_64x64 = 0, GT_32x64, GT_64x32, GT_32x32, GT_16x64, GT_64x16, GT_16x16, GT_8x32, GT_1x256, GT_256x1,
+  GT_48x48,
   GT_COUNT
 };
 void gemm_tile_dims(int tile, int* bm, int* bn);

@@ -225,8 +225,8 @@ cudaError_t launch_split_reduce(const GemmArgs& g, int nrhs, cudaStream_t st) {
 }
 
 void gemm_tile_dims(int tile, int* bm, int* bn) {
-  static const int d[GT_COUNT][2] = {{64, 64}, {32, 64}, {64, 32}, {32, 32}, {16, 64},
-                                     {64, 16}, {16, 16}, {8, 32},  {1, 256}, {256, 1}};
+  static const int d[GT_COUNT][2] = {{64, 64}, {32, 64}, {64, 32}, {32, 32}, {16, 64}, {64, 16},
+                                     {16, 16}, {8, 32},  {1, 256}, {256, 1}, {48, 48}};
   *bm = d[tile][0];
   *bn = d[tile][1];
 }
@@ -274,6 +274,7 @@ static cudaError_t launch_tile(const GemmArgs& g, int tile, int nrhs, cudaStream
     case GT_8x32: return launch_t<T, 8, 32, 1, 1>(g, nrhs, st);
     case GT_1x256: return launch_t<T, 1, 256, 1, 1>(g, nrhs, st);
     case GT_256x1: return launch_t<T, 256, 1, 1, 1>(g, nrhs, st);
+    case GT_48x48: return launch_t<T, 48, 48, 3, 3>(g, nrhs, st);  // 40 x 40 blocks (nvir = 40)
   }
   return cudaErrorInvalidValue;
 }
