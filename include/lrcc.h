@@ -246,6 +246,16 @@ lrcc_status lrcc_plan_op(const lrcc_plan* h, int32_t which, int32_t i, int32_t* 
  * alpha double[2]; coff int64[nbatch], sbeg int32[nbatch+1], aoff/boff int64[nseg]. */
 lrcc_status lrcc_plan_gemm(const lrcc_plan* h, int32_t idx, int32_t* ints, int64_t* lds, double* alpha,
                            int64_t* coff, int32_t* sbeg, int64_t* aoff, int64_t* boff);
+/* Kernel the executor launches by default for GEMM op idx at a precision (0 FP64,
+ * 1 TF32, 2 BF16x3), as decided on the host before any launch; out int32[7]: packed
+ * (tensor-core kernel on packed operands), special (1 short-contraction, 2 tiny-output
+ * reduction kernel), tc (unpacked tensor-core kernel), f32 (FP32 arithmetic on FP64
+ * operands), tile (tiled-kernel shape), nsplit (K splits; the reduction kernel splits
+ * whole segments), max_seg (most segments of a batch entry).  The mixed-precision modes are
+ * this library's (the paper computes in FP64); they keep every FP32 accumulation chain
+ * within 8192 complex terms, the partials of K splits being summed in FP64.  EINVAL for a
+ * bad handle, index or precision. */
+lrcc_status lrcc_plan_choice(const lrcc_plan* h, int32_t idx, int32_t precision, int32_t* out);
 /* ints int32[18]: src(kind nk n0..n3) dst(kind nk n0..n3) pi0..pi3 arS arD; offs int64[2]. */
 lrcc_status lrcc_plan_perm(const lrcc_plan* h, int32_t idx, int32_t* ints, int64_t* offs, double* alpha);
 /* ints int32[5]: nb R C arS arD; offs int64[2]. */

@@ -65,6 +65,7 @@ _SIGS = {
     "lrcc_plan_perm": (C.c_int, [VP, C.c_int32, VP, VP, VP]),
     "lrcc_plan_btrans": (C.c_int, [VP, C.c_int32, VP, VP, VP]),
     "lrcc_plan_zero": (C.c_int, [VP, C.c_int32, VP, VP]),
+    "lrcc_plan_choice": (C.c_int, [VP, C.c_int32, C.c_int32, VP]),
     "lrcc_small_eig": (C.c_int, [C.c_int32, VP, VP, VP]),
     "lrcc_wait_selftest": (C.c_int, [VP, C.c_int64]),
 }

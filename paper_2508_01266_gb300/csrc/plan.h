@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+struct lrcc_plan;  // introspection handle of include/lrcc.h
+
 namespace lrcc {
 
 enum Arena : int { AR_FIX = 0, AR_IN = 1, AR_OUT = 2, AR_SCR = 3, AR_WS = 4, AR_COUNT = 5 };
@@ -124,6 +126,9 @@ struct Plan {
 
 // Build both programs.  ws_budget: complex elements for the W-block workspace.
 Plan build_plan(const Dims& d, int64_t ws_budget);
+
+// The plan of an introspection handle (plan_api.cpp), for host-only queries elsewhere.
+const Plan* plan_of(const ::lrcc_plan* h);
 
 // Host-side bounds check of every op against the arena sizes (per-vector sizes for
 // the vector arenas).  Returns an empty string when every access is in bounds.

@@ -16,6 +16,8 @@ struct lrcc_plan {
   std::string err;
 };
 
+const Plan* lrcc::plan_of(const lrcc_plan* h) { return h ? &h->P : nullptr; }
+
 static const Program& prog_of(const lrcc_plan* h, int which) {
   switch (which) {
     case 0: return h->P.ground;

@@ -189,7 +189,7 @@ static int reduce_f32_min_split(const Gemm& g, const GemmDesc& d) {
 // LRCC_PACKED_MIN (default 32), K >= 16 and a contraction within TC_CHAIN_MAX (the
 // packed kernel sums a tile's whole contraction in one FP32 accumulator); the
 // autotuner may also choose it per op, under the same chain limit.
-bool Runtime::use_packed(const Gemm& g, const GemmDesc& d) const {
+static bool packed_ok(const Gemm& g, const GemmDesc& d) {
   static const int pmin = []() {
     const char* e = std::getenv("LRCC_PACKED_MIN");
     const int v = e ? std::atoi(e) : 0;
@@ -197,6 +197,7 @@ bool Runtime::use_packed(const Gemm& g, const GemmDesc& d) const {
   }();
   return g.M >= pmin && g.N >= pmin && g.K >= 16 && chain_len(g, d) <= TC_CHAIN_MAX;
 }
+bool Runtime::use_packed(const Gemm& g, const GemmDesc& d) const { return packed_ok(g, d); }
 
 // Useful fraction of the unpacked tensor-core tiles (128 x 64 complex, K in steps of 16)
 // for an M x N x K GEMM.
@@ -219,13 +220,22 @@ static bool tc_tile_useful(const Gemm& g) {
 // arithmetic) at least the split that caps the accumulator chains.  The
 // choice does not depend on the number of vectors, so a vector's result is bitwise the
 // same in any batch.
-int Runtime::pick_split(const Gemm& g, const GemmDesc& d, int nr, bool tc, bool f32) const {
-  if (no_split) return 1;
-  return std::max(pick_split_fill(g, d, nr, tc), tc ? tc_min_split(g, d) : f32 ? f32_min_split(g, d) : 1);
-}
+static int split_fill(const Gemm& g, const GemmDesc& d, bool tc);
 
+static int split_for(const Gemm& g, const GemmDesc& d, bool tc, bool f32, bool no_split) {
+  if (no_split) return 1;
+  return std::max(split_fill(g, d, tc), tc ? tc_min_split(g, d) : f32 ? f32_min_split(g, d) : 1);
+}
+int Runtime::pick_split(const Gemm& g, const GemmDesc& d, int nr, bool tc, bool f32) const {
+  (void)nr;
+  return split_for(g, d, tc, f32, no_split);
+}
 int Runtime::pick_split_fill(const Gemm& g, const GemmDesc& d, int nr, bool tc) const {
   (void)nr;
+  return split_fill(g, d, tc);
+}
+
+static int split_fill(const Gemm& g, const GemmDesc& d, bool tc) {
   int bm = 128, bn = 64;
   if (!tc) gemm_tile_dims(d.tile, &bm, &bn);
   const bool sw = tc && tc_swap(g);
@@ -451,9 +461,9 @@ static int reduce_split(const Gemm& g, const GemmDesc& d) {
 // tile kernel where even the better orientation of the unpacked tensor-core tile would
 // be under 20 % useful (small tiles, K <= 40: FP64-pipe bound, HBM bound in FP32); else
 // the unpacked tensor-core kernel.  The autotuner may replace any of these per op.
-GemmChoice Runtime::default_choice(const Gemm& g, const GemmDesc& d, int prec) const {
+GemmChoice gemm_default_choice(const Gemm& g, const GemmDesc& d, int prec, bool no_split) {
   GemmChoice c;
-  if (prec > 0 && use_packed(g, d)) {
+  if (prec > 0 && packed_ok(g, d)) {
     c.packed = true;
     return c;
   }
@@ -476,13 +486,43 @@ GemmChoice Runtime::default_choice(const Gemm& g, const GemmDesc& d, int prec) c
   c.tile = d.tile;
   if (prec > 0 && std::max(tc_eff(g.M, g.N, g.K), tc_eff(g.N, g.M, g.K)) < 0.2) {
     c.f32 = true;
-    c.nsplit = pick_split(g, d, 1, false, true);
+    c.nsplit = split_for(g, d, false, true, no_split);
     return c;
   }
   c.tc = prec > 0 && tc_tile_useful(g);
-  c.nsplit = pick_split(g, d, 1, c.tc);
+  c.nsplit = split_for(g, d, c.tc, false, no_split);
   return c;
 }
+
+GemmChoice Runtime::default_choice(const Gemm& g, const GemmDesc& d, int prec) const {
+  return gemm_default_choice(g, d, prec, no_split);
+}
+
+}  // namespace lrcc
+
+extern "C" lrcc_status lrcc_plan_choice(const lrcc_plan* h, int32_t idx, int32_t precision, int32_t* out) {
+  using namespace lrcc;
+  const Plan* P = plan_of(h);
+  if (!P || !out || idx < 0 || idx >= (int32_t)P->gemms.size() || precision < 0 || precision > 2)
+    return LRCC_EINVAL;
+  const Gemm& g = P->gemms[idx];
+  GemmDesc d;
+  d.tile = gemm_pick_tile(g.M, g.N);
+  int ms = 1;
+  for (size_t b = 0; b + 1 < g.sbeg.size(); ++b) ms = std::max(ms, g.sbeg[b + 1] - g.sbeg[b]);
+  d.max_seg = ms;
+  const GemmChoice c = gemm_default_choice(g, d, precision, false);
+  out[0] = c.packed;
+  out[1] = c.special;
+  out[2] = c.tc;
+  out[3] = c.f32;
+  out[4] = c.tile;
+  out[5] = c.nsplit;
+  out[6] = d.max_seg;
+  return LRCC_OK;
+}
+
+namespace lrcc {
 
 // One unpacked GEMM op with an explicit kernel choice (tile of the FP64 kernel or the
 // tensor-core kernel, split-K factor); grows the split-K partials buffer if needed.

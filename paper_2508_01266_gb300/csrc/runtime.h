@@ -31,6 +31,10 @@ struct GemmDesc {
   int max_seg = 1;  // most segments of any batch entry
 };
 
+// Default kernel of a GEMM op for a precision (0 FP64, 1 TF32, 2 BF16x3); host-only, used
+// by the executor and by the plan introspection call lrcc_plan_choice.
+GemmChoice gemm_default_choice(const Gemm& g, const GemmDesc& d, int prec, bool no_split);
+
 // Packed-operand execution of one GEMM op on the tensor cores (mixed precision).
 struct PackPlan {
   bool init = false;

@@ -1,0 +1,138 @@
+"""Host-side tests (no GPU) of the executor's default kernel choices, read through the plan
+introspection call lrcc_plan_choice: in the mixed-precision modes every FP32 accumulation
+chain stays within 8192 complex terms (longer contractions go through K splits whose
+partials are summed in FP64), and FP64 products use FP64 arithmetic only.
+
+The chain lengths are recomputed here from each kernel's split rule and the plan's own
+segment lists, not from the library's split formulas."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from synth import CONFIGS
+
+CHAIN_MAX = 8192  # complex terms summed in one FP32 accumulator
+TC_BK = 16        # complex K per iteration of the unpacked tensor-core kernel
+TILE_BK = 8       # complex K per iteration of the tiled kernel
+LANES = 32        # lanes of the reduction kernel's warp sums
+
+SHAPES = dict(CONFIGS)
+SHAPES.update({"chain_a": dict(nk=3, nocc=4, nvir=24, naux=60),
+               "chain_b": dict(nk=5, nocc=6, nvir=32, naux=100),
+               "tiny": dict(nk=2, nocc=1, nvir=3, naux=5)})
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2508_01266_gb300 import _lib
+    return _lib.lib
+
+
+def _plan(lib, s):
+    from paper_2508_01266_gb300._lib import lrcc_dims
+    d = lrcc_dims(s["nk"], s["nocc"], s["nvir"], s["naux"], 0)
+    h = C.c_void_p()
+    assert lib.lrcc_plan_create(C.byref(d), 1 << 26, C.byref(h)) == 0
+    return h
+
+
+def _gemm_ops(lib, h):
+    """(gemm index, M, N, K, most segments of a batch entry) of every GEMM op of every program."""
+    seen = {}
+    kif = (C.c_int32 * 3)()
+    for which in range(7):
+        for i in range(lib.lrcc_plan_num_ops(h, which)):
+            assert lib.lrcc_plan_op(h, which, i, kif) == 0
+            if kif[0] != 0 or kif[1] in seen:
+                continue
+            idx = kif[1]
+            ints = (C.c_int32 * 15)()
+            assert lib.lrcc_plan_gemm(h, idx, ints, None, None, None, None, None, None) == 0
+            nb = ints[13]
+            sbeg = np.zeros(nb + 1, np.int32)
+            assert lib.lrcc_plan_gemm(h, idx, None, None, None, None,
+                                      sbeg.ctypes.data_as(C.c_void_p), None, None) == 0
+            maxseg = int(np.diff(sbeg).max()) if nb > 0 else 0
+            seen[idx] = (ints[0], ints[1], ints[2], maxseg)
+    return seen
+
+
+def _choice(lib, h, idx, prec):
+    out = (C.c_int32 * 7)()
+    assert lib.lrcc_plan_choice(h, idx, prec, out) == 0
+    return dict(zip(("packed", "special", "tc", "f32", "tile", "nsplit", "max_seg"), list(out)))
+
+
+def _fp32_chain(c, K, maxseg):
+    """Longest run of complex terms one FP32 accumulator sums under choice c (None: FP64)."""
+    cdiv = lambda a, b: -(-a // b)
+    if c["packed"]:
+        return maxseg * K  # one TMEM accumulator per tile over the whole contraction
+    if c["tc"]:
+        iters = maxseg * cdiv(K, TC_BK)
+        return cdiv(iters, c["nsplit"]) * TC_BK
+    if not c["f32"]:
+        return None
+    if c["special"] == 1:
+        return maxseg * K
+    if c["special"] == 2:  # splits take whole segments; a lane sums every 32nd element
+        return LANES * cdiv(K, LANES) * cdiv(maxseg, c["nsplit"])
+    iters = maxseg * cdiv(K, TILE_BK)
+    return cdiv(iters, c["nsplit"]) * TILE_BK
+
+
+@pytest.mark.parametrize("shape", sorted(SHAPES))
+def test_fp32_chains_capped_and_fp64_pure(lib, shape):
+    h = _plan(lib, SHAPES[shape])
+    try:
+        ops = _gemm_ops(lib, h)
+        assert ops
+        for idx, (M, N, K, maxseg) in ops.items():
+            c0 = _choice(lib, h, idx, 0)
+            assert not (c0["packed"] or c0["tc"] or c0["f32"]), (shape, idx, c0)
+            assert c0["nsplit"] >= 1
+            for prec in (1, 2):
+                c = _choice(lib, h, idx, prec)
+                assert c["max_seg"] == max(maxseg, 1)
+                assert c["nsplit"] >= 1
+                assert not (c["packed"] and c["tc"])
+                chain = _fp32_chain(c, K, max(maxseg, 1))
+                if chain is not None:
+                    assert chain <= CHAIN_MAX, (shape, idx, (M, N, K, maxseg), prec, c, chain)
+    finally:
+        lib.lrcc_plan_destroy(h)
+
+
+def test_long_contractions_leave_the_packed_kernel(lib):
+    """At Nk=5, nocc=8, nvir=40 the v x v and o x o intermediates summed over three momenta
+    contract up to 64000 complex terms per output; none of them may run on the packed kernel
+    (one FP32 accumulator per tile), while the ladder-sized GEMMs (K >= 16) still do."""
+    h = _plan(lib, SHAPES["c2"])
+    try:
+        ops = _gemm_ops(lib, h)
+        long_ops = [i for i, (M, N, K, ms) in ops.items() if ms * K > CHAIN_MAX and M >= 32 and N >= 32]
+        assert len(long_ops) >= 2
+        for prec in (1, 2):
+            for i in long_ops:
+                assert not _choice(lib, h, i, prec)["packed"]
+            big = [i for i, (M, N, K, ms) in ops.items()
+                   if M >= 1600 and N >= 1600 and K >= 16 and ms * K <= CHAIN_MAX]
+            assert big and all(_choice(lib, h, i, prec)["packed"] for i in big)
+    finally:
+        lib.lrcc_plan_destroy(h)
+
+
+def test_plan_choice_rejects_bad_arguments(lib):
+    h = _plan(lib, SHAPES["tiny"])
+    try:
+        out = (C.c_int32 * 7)()
+        assert lib.lrcc_plan_choice(h, -1, 0, out) != 0
+        assert lib.lrcc_plan_choice(h, 1 << 20, 0, out) != 0
+        assert lib.lrcc_plan_choice(h, 0, 3, out) != 0
+        assert lib.lrcc_plan_choice(h, 0, 0, None) != 0
+        assert lib.lrcc_plan_choice(None, 0, 0, out) != 0
+    finally:
+        lib.lrcc_plan_destroy(h)
