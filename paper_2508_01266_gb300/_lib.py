@@ -37,6 +37,7 @@ _SIGS = {
     "lrcc_set_integrals": (C.c_int, [VP, VP, VP, VP, C.c_int32]),
     "lrcc_set_ground_state": (C.c_int, [VP, VP, VP, VP, VP, C.c_int32]),
     "lrcc_jacobian_apply": (C.c_int, [VP, C.c_int32, C.c_int32, VP, VP, VP, VP, C.POINTER(lrcc_options), VP]),
+    "lrcc_jacobian_apply_noalloc": (C.c_int, [VP, C.c_int32, VP, VP, VP, VP, VP]),
     "lrcc_polarizability": (C.c_int, [VP, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_double), C.c_int32,
                                       C.POINTER(lrcc_options), VP, C.POINTER(C.c_int32)]),
     "lrcc_last_error": (C.c_char_p, [VP]),
