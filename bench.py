@@ -288,7 +288,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2")
     ap.add_argument("--nrhs", type=int, default=0, help="vectors per step (default: all systems of the workload)")
-    ap.add_argument("--ref-blocks", type=int, default=4)
+    ap.add_argument("--ref-blocks", type=int, default=8, help="doubles blocks of one vector in the oracle sample (about 1.6 s each on 16 cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-alpha", action="store_true", help="skip the alpha wall-time measurement")
