@@ -11,7 +11,11 @@ the same comparison passes unpatched:
       response function (Eq. 15), the perturbation right-hand side (Eq. 12) off by its
       factor 1/2, a wrong sign of eta;
   P5  decoupled replicas: alpha per cell independent of Nk: the 1/Nk of alpha per cell
-      missing.
+      missing;
+  P9, term by term: every contraction of the closed-shell residual, dressing, Fock build
+      and energy dropped, sign-flipped or index-transposed in turn (mutations that cannot
+      change the compared quantities are listed with their reason); the energy's singles
+      term, zero at the canonical reference, through P6.
 """
 import numpy as np
 import pytest
@@ -117,3 +121,96 @@ def test_p5_catches_missing_per_cell_factor(monkeypatch):
     orig = rcc.polarizability
     monkeypatch.setattr(rcc, "polarizability", lambda R, *a, **k: orig(R, *a, **k) * R.nk)
     assert _p5_deviation() > 1e3 * P5_TOL
+
+
+# P9, term by term -------------------------------------------------------------------
+def _p9_case():
+    nk, o, v, seed = 2, 2, 3, 4
+    p = make_problem(nk, o, v, 5, seed=seed, sigma_l=0.3, tr=False)
+    S = spinorb.SpinOrbitalSystem(p)
+    t1k, t2k = random_amplitudes(nk, o, v, seed=seed + 3, scale1=0.1, scale2=0.1)
+    t1, t2 = spinorb.to_spinorb(S, t1k, t2k)
+    ref = spinorb.from_spinorb(S, *spinorb.residual(S, t1, t2)), spinorb.energy(S, t1, t2)
+    return p, t1k, t2k, ref
+
+
+def _p9_case_deviation(case):
+    p, t1k, t2k, ((c1, c2), e) = case
+    R = rcc.RCC(p)
+    b1, b2 = R.residual(T(t1k), T(t2k))
+    de = abs(e - complex(R.energy(T(t1k), T(t2k))))
+    return max(np.abs(c1 - b1.numpy()).max(), np.abs(c2 - b2.numpy()).max(), de)
+
+
+def _swap_first_equal_pair(spec, r):
+    """Transpose the first two output indices of equal extent (a wrong-index mistake)."""
+    out = spec.split("->")[1]
+    for a in range(len(out)):
+        for b in range(a + 1, len(out)):
+            if r.shape[a] == r.shape[b] and r.shape[a] > 1:
+                return r.transpose(a, b)
+    return None
+
+
+# Mutations that cannot change the compared quantities, with the reason:
+EQUIVALENT = {
+    # the dressed DF factors enter every integral in pairs, so L~ -> -L~ is exact
+    ("pr,Qrs,sq->Qpq", "sign"): "DF factors enter in pairs",
+    # 2 f_ia t1_ia vanishes for the canonical reference (f_ia = 0); the term matters once
+    # the one-body part is perturbed (eta of Eq. 15) and P6 guards it there
+    ("ia,ia->", "drop"): "f_ia = 0 (canonical)",
+    ("ia,ia->", "sign"): "f_ia = 0 (canonical)",
+}
+
+
+def test_p9_guards_every_contraction_of_the_closed_shell_residual(monkeypatch):
+    """Every contraction the closed-shell residual, its T1 dressing, its Fock build and
+    its energy evaluate is planted, one at a time, with a dropped term, a flipped sign and
+    (where two output indices have equal extent) transposed output indices; the
+    comparison with the independent spin-orbital oracle fails for each, except the
+    mutations listed in EQUIVALENT, which leave the compared quantities unchanged."""
+    case = _p9_case()
+    shapes = {}
+    orig = rcc.ein
+
+    def record(spec, *ops):
+        r = orig(spec, *ops)
+        shapes.setdefault(spec, tuple(r.shape))
+        return r
+
+    monkeypatch.setattr(rcc, "ein", record)
+    assert _p9_case_deviation(case) < P9_TOL
+    assert len(shapes) >= 20, sorted(shapes)
+    missed, tried = [], 0
+    for target, shape in shapes.items():
+        for kind in ("drop", "sign", "swap"):
+            if kind == "swap" and _swap_first_equal_pair(target, torch.zeros(shape)) is None:
+                continue  # no two output indices of equal extent: nothing to transpose
+
+            def mutated(spec, *ops, _t=target, _k=kind):
+                r = orig(spec, *ops)
+                if spec != _t:
+                    return r
+                if _k == "drop":
+                    return torch.zeros_like(r)
+                if _k == "sign":
+                    return -r
+                return _swap_first_equal_pair(spec, r)
+
+            monkeypatch.setattr(rcc, "ein", mutated)
+            tried += 1
+            if _p9_case_deviation(case) <= 1e3 * P9_TOL:
+                missed.append((target, kind))
+    assert tried >= 50
+    assert sorted(missed) == sorted(EQUIVALENT), sorted(set(missed) ^ set(EQUIVALENT))
+
+
+def test_p6_catches_energy_singles_term(monkeypatch):
+    """The singles term of the energy (Eq. 6), invisible to P9 at the canonical reference,
+    enters alpha through eta (the one-body part perturbed by the dipole): dropping it
+    fails P6."""
+    assert _p6_deviation() < P6_TOL
+    orig = rcc.ein
+    monkeypatch.setattr(rcc, "ein", lambda spec, *ops: torch.zeros_like(orig(spec, *ops)) if spec == "ia,ia->"
+                        else orig(spec, *ops))
+    assert _p6_deviation() > 1e3 * P6_TOL
