@@ -214,3 +214,63 @@ def test_p6_catches_energy_singles_term(monkeypatch):
     monkeypatch.setattr(rcc, "ein", lambda spec, *ops: torch.zeros_like(orig(spec, *ops)) if spec == "ia,ia->"
                         else orig(spec, *ops))
     assert _p6_deviation() > 1e3 * P6_TOL
+
+
+# P1, term by term ---------------------------------------------------------------------
+def test_p1_guards_every_contraction_of_the_spin_orbital_residual(monkeypatch):
+    """Every contraction of the spin-orbital residual (Oracle-A, the paper's arrangement of
+    Eqs. 7-8) is planted in turn with a dropped term, a flipped sign and transposed output
+    indices; the determinant-space brute force detects each.  A non-canonical one-body
+    part (random Hermitian shift) and amplitudes that are neither spin-adapted nor
+    momentum-conserving keep every term alive."""
+    nk, o, v = 2, 1, 2
+    p = make_problem(nk, o, v, 4, seed=5, sigma_l=0.3, tr=False)
+    rng = np.random.default_rng(3)
+    n = o + v
+    F = 0.05 * (rng.normal(size=(nk, n, n)) + 1j * rng.normal(size=(nk, n, n)))
+    F = F + F.conj().transpose(0, 2, 1)
+    S = spinorb.SpinOrbitalSystem(p, fock_shift=F)
+    O, V = S.O, S.V
+    t1 = 0.1 * (rng.normal(size=(O, V)) + 1j * rng.normal(size=(O, V)))
+    t2 = 0.1 * (rng.normal(size=(O, O, V, V)) + 1j * rng.normal(size=(O, O, V, V)))
+    t2 = t2 - t2.transpose(1, 0, 2, 3)
+    t2 = t2 - t2.transpose(0, 1, 3, 2)
+    b1, b2 = fci.cc_residual(S, t1, t2)
+
+    def deviation():
+        a1, a2 = spinorb.residual(S, t1, t2)
+        return max(np.abs(a1 - b1).max(), np.abs(a2 - b2).max())
+
+    shapes = {}
+    orig = spinorb.einsum
+
+    def record(spec, *ops):
+        r = orig(spec, *ops)
+        shapes.setdefault(spec, r.shape)
+        return r
+
+    monkeypatch.setattr(spinorb, "einsum", record)
+    assert deviation() < 1e-13
+    assert len(shapes) >= 25, sorted(shapes)
+    missed, tried = [], 0
+    for target, shape in shapes.items():
+        for kind in ("drop", "sign", "swap"):
+            if kind == "swap" and _swap_first_equal_pair(target, torch.zeros(shape)) is None:
+                continue
+
+            def mutated(spec, *ops, _t=target, _k=kind):
+                r = orig(spec, *ops)
+                if spec != _t:
+                    return r
+                if _k == "drop":
+                    return np.zeros_like(r)
+                if _k == "sign":
+                    return -r
+                return np.asarray(_swap_first_equal_pair(spec, torch.as_tensor(r)))
+
+            monkeypatch.setattr(spinorb, "einsum", mutated)
+            tried += 1
+            if deviation() <= 1e-10:
+                missed.append((target, kind))
+    assert tried >= 60
+    assert not missed, missed
