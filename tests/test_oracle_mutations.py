@@ -12,6 +12,9 @@ the same comparison passes unpatched:
       factor 1/2, a wrong sign of eta;
   P5  decoupled replicas: alpha per cell independent of Nk: the 1/Nk of alpha per cell
       missing;
+  P2  A.X vs the brute-force commutator: a 3-point stencil, inexact for the quartic residual;
+  P3  adjoint identity: a transpose that forgets to undo the conjugation of the autograd
+      gradient;
   P9, term by term: every contraction of the closed-shell residual, dressing, Fock build
       and energy dropped, sign-flipped or index-transposed in turn (mutations that cannot
       change the compared quantities are listed with their reason); the energy's singles
@@ -274,3 +277,81 @@ def test_p1_guards_every_contraction_of_the_spin_orbital_residual(monkeypatch):
                 missed.append((target, kind))
     assert tried >= 60
     assert not missed, missed
+
+
+# P2, P3 -------------------------------------------------------------------------------
+def _p2_deviation():
+    """max deviation of the oracle's A.X from the brute-force commutator
+    <mu| exp(-T) [H, X] exp(T) |0> (the P2 pin's comparison)."""
+    nk, o, v = 2, 1, 2
+    p = make_problem(nk, o, v, 4, seed=21, sigma_l=0.3)
+    S = spinorb.SpinOrbitalSystem(p)
+    R = rcc.RCC(p)
+    t1k, t2k = random_amplitudes(nk, o, v, seed=22, scale1=0.1, scale2=0.1)
+    x1k, x2k = random_amplitudes(nk, o, v, seed=23, scale1=1.0, scale2=1.0)
+    a1, a2 = R.jacobian(T(t1k), T(t2k), T(x1k), T(x2k))
+    t1, t2 = spinorb.to_spinorb(S, t1k, t2k)
+    x1, x2 = spinorb.to_spinorb(S, x1k, x2k)
+    O, N = S.O, S.N
+    ds = fci.DetSpace(N, O)
+    g = S.g
+    h = S.f - np.einsum("piqi->pq", (g - g.transpose(0, 1, 3, 2))[:, :O, :, :O])
+    psi = fci._exp_T(ds, O, t1, t2, ds.ref(), 1.0)
+    hx = fci._apply_H(ds, h, g, fci._apply_T(ds, O, x1, x2, psi))
+    xh = fci._apply_T(ds, O, x1, x2, fci._apply_H(ds, h, g, psi))
+    om = fci._exp_T(ds, O, t1, t2, hx - xh, -1.0)
+    ref = ds.ref()
+    V = N - O
+    b1 = np.zeros((O, V), complex)
+    b2 = np.zeros((O, O, V, V), complex)
+    for I in range(O):
+        for A in range(V):
+            b1[I, A] = np.vdot(ds.E(O + A, I) @ ref, om)
+            for J in range(O):
+                for B in range(V):
+                    if I != J and A != B:
+                        b2[I, J, A, B] = np.vdot(ds.E(O + A, I) @ (ds.E(O + B, J) @ ref), om)
+    c1, c2 = spinorb.from_spinorb(S, b1, b2)
+    return max(np.abs(c1 - a1.numpy()).max(), np.abs(c2 - a2.numpy()).max())
+
+
+def _p3_deviation():
+    """relative violation of <Y, A X> = <A^T Y, X> (the P3 pin's comparison), complex data."""
+    nk, o, v = 3, 1, 2
+    p = make_problem(nk, o, v, 4, seed=31, sigma_l=0.2, tr=False)
+    R = rcc.RCC(p)
+    t1, t2 = map(T, random_amplitudes(nk, o, v, seed=32, scale1=0.05, scale2=0.05))
+    x1, x2 = map(T, random_amplitudes(nk, o, v, seed=40, scale1=1, scale2=1))
+    y1, y2 = map(T, random_amplitudes(nk, o, v, seed=50, scale1=1, scale2=1))
+    a1, a2 = R.jacobian(t1, t2, x1, x2)
+    b1, b2 = R.transpose(t1, t2, y1, y2)
+    lhs = complex((y1 * a1).sum() + (y2 * a2).sum())
+    rhs = complex((b1 * x1).sum() + (b2 * x2).sum())
+    return abs(lhs - rhs) / abs(lhs)
+
+
+def _jacobian_three_point(self, t1, t2, x1, x2, h=None, blocks=None):
+    # central difference [f(s) - f(-s)] / 2s: not exact for the quartic CCSD residual
+    s = max(float(torch.max(torch.abs(x1))), float(torch.max(torch.abs(x2))), 1e-300)
+    hh = 1e-2 / s
+    rp = self.residual(t1 + hh * x1, t2 + hh * x2, h, blocks)
+    rm = self.residual(t1 - hh * x1, t2 - hh * x2, h, blocks)
+    return (rp[0] - rm[0]) / (2 * hh), (rp[1] - rm[1]) / (2 * hh)
+
+
+def _transpose_without_conj(orig):
+    # the autograd gradient of a holomorphic function comes back conjugated; forgetting to
+    # undo it turns the bilinear transpose into a sesquilinear one
+    return lambda self, t1, t2, y1, y2, h=None: tuple(z.conj().resolve_conj() for z in orig(self, t1, t2, y1, y2, h))
+
+
+def test_p2_catches_inexact_stencil(monkeypatch):
+    assert _p2_deviation() < 1e-12
+    monkeypatch.setattr(rcc.RCC, "jacobian", _jacobian_three_point)
+    assert _p2_deviation() > 1e-9
+
+
+def test_p3_catches_missing_conjugation(monkeypatch):
+    assert _p3_deviation() < 1e-12
+    monkeypatch.setattr(rcc.RCC, "transpose", _transpose_without_conj(rcc.RCC.transpose))
+    assert _p3_deviation() > 1e-6
