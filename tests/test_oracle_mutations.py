@@ -9,7 +9,7 @@ the same comparison passes unpatched:
       T1 terms (Eq. 6);
   P6  two electrons: alpha = FCI sum over states: the quadratic F term dropped from the
       response function (Eq. 15), the perturbation right-hand side (Eq. 12) off by its
-      factor 1/2, a wrong sign of eta;
+      factor 1/2, a wrong sign of eta, Lambda with the wrong sign of dE/dt;
   P5  decoupled replicas: alpha per cell independent of Nk: the 1/Nk of alpha per cell
       missing;
   P2  A.X vs the brute-force commutator: a 3-point stencil, inexact for the quartic residual;
@@ -355,3 +355,18 @@ def test_p3_catches_missing_conjugation(monkeypatch):
     assert _p3_deviation() < 1e-12
     monkeypatch.setattr(rcc.RCC, "transpose", _transpose_without_conj(rcc.RCC.transpose))
     assert _p3_deviation() > 1e-6
+
+
+def test_p6_catches_lambda_sign(monkeypatch):
+    """Lambda solved from A^T lam = +dE/dt instead of -dE/dt (Eqs. 10-11): alpha, which
+    sees Lambda through eta and F, no longer equals FCI."""
+    assert _p6_deviation() < P6_TOL
+    orig = rcc.lagrangian_grad
+
+    def wrong_sign(R, t1, t2, l1, l2, h=None):
+        g1, g2 = orig(R, t1, t2, l1, l2, h)
+        e1, e2 = R.energy_grad(t1, t2, h)
+        return g1 - 2 * e1, g2 - 2 * e2
+
+    monkeypatch.setattr(rcc, "lagrangian_grad", wrong_sign)
+    assert _p6_deviation() > 1e3 * P6_TOL
