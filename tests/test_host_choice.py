@@ -136,3 +136,29 @@ def test_plan_choice_rejects_bad_arguments(lib):
         assert lib.lrcc_plan_choice(None, 0, 0, out) != 0
     finally:
         lib.lrcc_plan_destroy(h)
+
+
+def test_small_shapes_take_fp32_kernels_in_mixed_precision(lib):
+    """At nvir = 40 the mixed modes run the Fock-like 8 x 1600 x 8 blocks on the FP32
+    short-contraction kernel, and the 40 x 40 blocks that the packed path does not take
+    (K < 16, or contractions over the FP32 chain cap) on the FP32 tiled kernel with the
+    48 x 48 tile; FP64 products keep FP64 kernels for both."""
+    h = _plan(lib, SHAPES["c2"])
+    try:
+        ops = _gemm_ops(lib, h)
+        skinny = [i for i, (M, N, K, ms) in ops.items() if (M, N, K) == (8, 1600, 8) and ms == 1]
+        small = [i for i, (M, N, K, ms) in ops.items()
+                 if (M, N) == (40, 40) and K <= 40 and (K < 16 or ms * K > CHAIN_MAX)]
+        assert skinny and small
+        for prec in (1, 2):
+            for i in skinny:
+                c = _choice(lib, h, i, prec)
+                assert (c["special"], c["f32"]) == (1, 1), c
+            for i in small:
+                c = _choice(lib, h, i, prec)
+                assert c["f32"] == 1 and not (c["tc"] or c["packed"] or c["special"]), c
+                assert c["tile"] == 10, c  # the 48 x 48 tile
+        for i in skinny + small:
+            assert _choice(lib, h, i, 0)["f32"] == 0
+    finally:
+        lib.lrcc_plan_destroy(h)
