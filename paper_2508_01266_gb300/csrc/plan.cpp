@@ -1251,6 +1251,10 @@ Program transpose_program(Plan& P, const Program& fwd) {
   // walk backwards, and when a variable GEMM reads the WS arena, emit the fixed
   // build op(s) that precede it in the forward program first.
   std::vector<int> pending;  // index in fwd of fixed-only ops not yet emitted
+  // Only W builds write the WS arena and the contractions only read it, so a build is
+  // emitted once for the run of transposed contractions that use it (the forward program
+  // builds one W chunk for both ladder contractions of that chunk).
+  int last_build = -1;
   for (int i = (int)fwd.ops.size() - 1; i >= 0; --i) {
     const Op& op = fwd.ops[i];
     if (op.fixed_only || op.kind == OP_ZERO) continue;
@@ -1267,7 +1271,8 @@ Program transpose_program(Plan& P, const Program& fwd) {
         // find the nearest preceding fixed-only op (its W build)
         for (int j = i - 1; j >= 0; --j)
           if (fwd.ops[j].fixed_only) {
-            out.ops.push_back(fwd.ops[j]);
+            if (j != last_build) out.ops.push_back(fwd.ops[j]);
+            last_build = j;
             break;
           }
       }
