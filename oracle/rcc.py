@@ -111,8 +111,15 @@ class RCC:
         O, Vs = slice(0, o), slice(o, self.n)
         Lt, ft = self.dress(t1, h)
 
+        memo = {}
+
         def eri(kp, kq, kr, ks, sp, sq, sr, ss):
-            return ein("Qpq,Qrs->pqrs", Lt[kp, kq][:, sp, sq], Lt[kr, ks][:, sr, ss])
+            # (pq|rs) = sum_Q L~_pq L~_rs, built once per call and block (the same block is
+            # asked for by several amplitude blocks; the value does not depend on which)
+            key = (kp, kq, kr, ks, sp.start, sq.start, sr.start, ss.start)
+            if key not in memo:
+                memo[key] = ein("Qpq,Qrs->pqrs", Lt[kp, kq][:, sp, sq], Lt[kr, ks][:, sr, ss])
+            return memo[key]
 
         kb = self.kb
         T = lambda ki, kj, ka: t2[ki, kj, ka]                                       # noqa: E731
@@ -477,6 +484,40 @@ def polarizability(R: RCC, t1, t2, l1, l2, mus, omegas, tol=1e-11, verbose=False
                      + F_dot(R, t1, t2, l1, l2, *tp[x], *tm[y]))
                 lr = 0.5 * (complex(a) + np.conj(complex(b)))
                 out[iw, x, y] = -lr / R.nk
+    return out
+
+
+def symmetric_alpha(nk, etas, tp, tm, ftp, ftm):
+    """alpha_XY(w) per cell in the symmetric form of Eq. 15, assembled from vectors under the
+    plain pairing: etas[c] = eta^X (eta_vector), tp[c] / tm[c] = t^X(+w) / t^X(-w)
+    (solve_response), ftp[c] / ftm[c] = F t^X(+w) / F t^X(-w) (F_vector).  Same formula as
+    `polarizability`, whose scalar stencils eta^X . w and F(u, w) are the pairings
+    <eta^X, w> and <F u, w> of these vectors (all vectors pair-symmetric)."""
+    nc = len(etas)
+    out = np.zeros((nc, nc), dtype=np.complex128)
+    for x in range(nc):
+        for y in range(nc):
+            a = _pair(*etas[x], *tp[y]) + _pair(*etas[y], *tm[x]) + _pair(*ftm[x], *tp[y])
+            b = _pair(*etas[x], *tm[y]) + _pair(*etas[y], *tp[x]) + _pair(*ftp[x], *tm[y])
+            out[x, y] = -0.5 * (a + np.conj(b)) / nk
+    return out
+
+
+def polarizability_vectors(R: RCC, t1, t2, l1, l2, mus, omegas, tol=1e-11):
+    """`polarizability` (symmetric form, Eq. 15) evaluated through eta and F vectors: one
+    eta vector per component and one F vector per response solution instead of one scalar
+    stencil per (X, Y, w) pair, so that large problems need far fewer Lagrangian
+    evaluations.  Mathematically identical; per cell."""
+    nc = len(mus)
+    out = np.zeros((len(omegas), nc, nc), dtype=np.complex128)
+    xis = [perturbation_rhs(R, t1, t2, m) for m in mus]
+    etas = [eta_vector(R, t1, t2, l1, l2, m) for m in mus]
+    for iw, w in enumerate(omegas):
+        tp = [solve_response(R, t1, t2, *xis[c], w, tol)[:2] for c in range(nc)]
+        tm = [solve_response(R, t1, t2, *xis[c], -w, tol)[:2] for c in range(nc)] if w != 0 else tp
+        ftp = [F_vector(R, t1, t2, l1, l2, *tp[c]) for c in range(nc)]
+        ftm = [F_vector(R, t1, t2, l1, l2, *tm[c]) for c in range(nc)] if w != 0 else ftp
+        out[iw] = symmetric_alpha(R.nk, etas, tp, tm, ftp, ftm)
     return out
 
 
