@@ -5,10 +5,14 @@ One step = one pass of the response solver's hot path over a batch of right-hand
 sides: the full Jacobian product A.X (particle-particle ladder with W built from the
 dressed DF factors, hole-hole, ring, singles-coupling and Fock-like terms) on every
 vector of the batch.  The default workload is the Nk=5, nocc=8, nvir=40, naux=160
-chain with the 15 (component, +-omega) systems of the 3x3 alpha tensor at
-omega in {0, 0.05, 0.1} Ha.  Inputs are seeded synthetic data (synth.make_problem);
-ground-state amplitudes are random with the magnitude of converged ones (the cost of
-a product does not depend on their values).
+chain of the 3x3 alpha tensor at omega in {0, 0.05, 0.1} Ha; a step is the batch of
+the three dipole components at one frequency (one right-hand-side batch of that alpha
+solve; 15 such vectors make the whole tensor).  Inputs are seeded synthetic data
+(synth.make_problem); ground-state amplitudes are random with the magnitude of
+converged ones (the cost of a product does not depend on their values).
+
+--gpus N without a launcher starts N replica ranks itself (one process per GPU, gloo
+for the max-over-ranks timing); under torchrun the ranks come from the environment.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a bounded
 sample of the same workload.
@@ -27,9 +31,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 pipe, nominal (profiling recipe table)
-# DRAM bytes (read + write) of one FP64 ladder-contraction launch of this workload (15 vectors),
-# from a one-pass ncu capture of this build's kernel (profiles/ladder_c2_fp64.md)
-LADDER_TRAFFIC_BYTES = 23.36e9 + 1.00e9
+# DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of a small
+# case scaled to the workload (profiles/): (kernel source file, its sha256 prefix when the
+# counters were taken, bytes per launch at the default workload).  The bench reports null
+# once the source has changed since.
+TRAFFIC_RECORD = None
 
 
 def _dist():
@@ -39,6 +45,57 @@ def _dist():
         dist.init_process_group("nccl" if os.environ.get("LRCC_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
         return dist, dist.get_rank(), ws
     return None, 0, 1
+
+
+def _free_port():
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _replica(rank, argv, world, port, backend):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), LOCAL_RANK=str(rank),
+                      WORLD_SIZE=str(world), LRCC_BENCH_BACKEND=backend)
+    sys.argv = [sys.argv[0]] + list(argv)
+    main()
+
+
+def spawn_replicas(n, argv):
+    """--gpus N without a launcher: N replica ranks, one process per GPU (RANK, LOCAL_RANK,
+    WORLD_SIZE set as torchrun would), gloo for the barrier and the max-over-ranks time (the
+    replicas exchange nothing else)."""
+    import torch.multiprocessing as mp
+    mp.start_processes(_replica, args=(argv, n, _free_port(), os.environ.get("LRCC_BENCH_BACKEND", "gloo")),
+                       nprocs=n, join=True, start_method="spawn")
+
+
+def _source_sha(rel):
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
+def host_cpu():
+    """CPU model and logical core count of the host (for the oracle baseline)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k = ln.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware") and ":" in ln:
+                    model = ln.split(":", 1)[1].strip()
+                    break
+                if k == "cpu part" and model is None:
+                    model = "arm cpu part " + ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return {"cpu_model": model, "host_logical_cores": os.cpu_count()}
 
 
 def _max_over_ranks(dist, x):
@@ -163,6 +220,9 @@ def cpu_oracle_rate(cfg, nblocks, seed=1266):
 
 
 def run_reference(args):
+    """The oracle as it stands, on the host cores, on a bounded sample of the same workload:
+    each step runs the oracle's product on a sample of doubles blocks of one vector; value =
+    products/s scaled by the block fraction (the oracle's cost is the same for every block)."""
     dist, rank, ws = _dist()
     if rank != 0:
         return
@@ -170,21 +230,25 @@ def run_reference(args):
     nb = args.ref_blocks
     for _ in range(args.warmup):
         cpu_oracle_rate(cfg, nb)
-    rates, secs = [], 0.0
+    rates, secs = [], []
     threads, sample = None, ""
     for _ in range(args.steps):
         r, dt, threads, sample = cpu_oracle_rate(cfg, nb)
         rates.append(r)
-        secs += dt
+        secs.append(dt)
     value = args.steps / sum(1.0 / r for r in rates)
+    cpu = {"kind": "oracle", "cores": threads, "sample": sample, "value": value, "unit": "products/s",
+           **host_cpu()}
     line = {"impl": "reference", "metric": "LR-CCSD Jacobian products/s", "value": value,
             "unit": "products/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": 1000.0 * sum(secs) / len(secs),
+            "ms_per_step_note": "wall time of one sampled step (a fraction of one product); value is scaled "
+                                "to whole products",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c128", "data": "synthetic",
             "config": {"workload": f"{args.config}: Nk={cfg['nk']} nocc={cfg['nocc']} nvir={cfg['nvir']} "
                                    f"naux={cfg['naux']}", "rhs_per_step": 1},
-            "cpu_baseline": {"kind": "oracle", "cores": threads, "sample": sample, "value": value,
-                             "unit": "products/s"},
+            "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -233,9 +297,10 @@ def alpha_wall_time(lr):
     return out
 
 
-def time_mixed(lr, prob, X1, X2, Y1, Y2, args, st, dist, products):
+def time_mixed(lr, prob, X1, X2, Y1, Y2, steps, warmup, st, dist, products):
     """Time the tensor-core products (BF16x3 and TF32) on the same vectors; Y1/Y2 are the
-    FP64 results (None: no error column)."""
+    FP64 results (None: no error column).  The timed loop runs without per-op events; one
+    more product with per-op events (same tuned kernels, eager) gives the ladder rate."""
     import torch
     mixed = {}
     e0 = torch.cuda.Event(enable_timing=True)
@@ -246,18 +311,17 @@ def time_mixed(lr, prob, X1, X2, Y1, Y2, args, st, dist, products):
         # during warm-up) and as CUDA graphs
         opts = lr.default_options(precision=prec, autotune=1, use_graphs=1)
         M1, M2 = torch.empty_like(X1), torch.empty_like(X2)
-        for _ in range(args.warmup):
+        for _ in range(max(warmup, 2)):
             prob.jacobian_apply(X1, X2, y1=M1, y2=M2, options=opts)
         torch.cuda.synchronize()
         m0 = prob.kernel_launches
         e0.record(st)
-        for _ in range(args.steps):
+        for _ in range(steps):
             prob.jacobian_apply(X1, X2, y1=M1, y2=M2, options=opts)
         e1.record(st)
         torch.cuda.synchronize()
         mms = _max_over_ranks(dist, e0.elapsed_time(e1))
         launches = int(prob.kernel_launches - m0)
-        # one more product with per-op events (eager, same tuned kernels) for the ladder rate
         prob.profile(True)
         prob.jacobian_apply(X1, X2, y1=M1, y2=M2, options=opts)
         lms, ln, lfl = prob.profile_query("ladder")
@@ -267,8 +331,8 @@ def time_mixed(lr, prob, X1, X2, Y1, Y2, args, st, dist, products):
         if Y1 is not None:
             err = max(float((M1 - Y1).abs().max() / Y1.abs().max()), float((M2 - Y2).abs().max() / Y2.abs().max()))
         lach = (lfl / max(ln, 1)) / ((lms / max(ln, 1)) * 1e-3) / 1e12 if ln else None
-        mixed[name] = {"value": products / (mms / 1000.0), "unit": "products/s", "ms_per_step": mms / args.steps,
-                       "autotune": True, "cuda_graphs": True,
+        mixed[name] = {"value": products / (mms / 1000.0), "unit": "products/s", "ms_per_step": mms / steps,
+                       "steps": steps, "autotune": True, "cuda_graphs": True,
                        "gpu_launches": launches,
                        "max_rel_err_vs_fp64": err,
                        "ladder": {"achieved_tflops_algorithmic": lach,
@@ -280,28 +344,87 @@ def time_mixed(lr, prob, X1, X2, Y1, Y2, args, st, dist, products):
     return mixed
 
 
+def extra_workload(lr, name, steps, dist, rank):
+    """BF16x3 products/s (autotuned, CUDA graphs) at a larger workload: all (component, +-omega)
+    vectors of the workload in one batch, as many as fit."""
+    import torch
+    from synth import make_problem, random_amplitudes, random_probe
+    cfg, comps, omegas, nsys = workload(name)
+    nk, o, v, Q = cfg["nk"], cfg["nocc"], cfg["nvir"], cfg["naux"]
+    nrhs = {"c4": 1, "c5": 4}.get(name, nsys)
+    t0 = time.perf_counter()
+    p = make_problem(nk, o, v, Q, seed=1266)
+    t1, t2 = random_amplitudes(nk, o, v, seed=1267, scale1=0.01, scale2=0.01)
+    prob = lr.Problem(nk, o, v, Q)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    prob.set_ground_state(t1, t2 * nk)
+    del p, t1, t2
+    x1, x2 = random_probe(nk, o, v, seed=replica_seed(rank), nrhs=nrhs)
+    X1 = torch.as_tensor(x1).cuda()
+    X2 = torch.as_tensor(x2 * nk).cuda()
+    del x1, x2
+    torch.cuda.synchronize()
+    setup = time.perf_counter() - t0
+    st = torch.cuda.current_stream()
+    m = time_mixed(lr, prob, X1, X2, None, None, steps, 1, st, dist, nrhs * steps)["bf16x3"]
+    prob.close()
+    del X1, X2
+    torch.cuda.empty_cache()
+    return {"workload": f"{name}: Nk={nk} nocc={o} nvir={v} naux={Q}", "rhs_per_step": nrhs, "bf16x3": m,
+            "setup_seconds": setup}
+
+
+def dry_run(args):
+    """Rank setup only (no GPU, no library): every rank reports its rank and replica seed; rank 0
+    prints one line.  Used by the CPU tests of the replica launch."""
+    dist, rank, ws = _dist()
+    t = _max_over_ranks(dist, 1.0 + rank)
+    seeds = [replica_seed(r) for r in range(ws)]
+    if dist is not None:
+        import torch
+        got = [None] * ws
+        dist.all_gather_object(got, (rank, int(os.environ.get("LOCAL_RANK", "0")), replica_seed(rank)))
+        seeds = got
+        dist.barrier()
+    if rank == 0:
+        print(json.dumps({"dry_run": True, "n_gpus": ws, "ranks": seeds, "max_over_ranks": t}), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2")
-    ap.add_argument("--nrhs", type=int, default=0, help="vectors per step (default: all systems of the workload)")
+    ap.add_argument("--nrhs", type=int, default=0,
+                    help="vectors per step (default: the dipole components of the workload, one frequency)")
     ap.add_argument("--ref-blocks", type=int, default=8, help="doubles blocks of one vector in the oracle sample (about 1.6 s each on 16 cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-alpha", action="store_true", help="skip the alpha wall-time measurement")
+    ap.add_argument("--extra", default="c3,c4",
+                    help="comma-separated larger workloads whose BF16x3 products/s are added (empty: none)")
+    ap.add_argument("--extra-steps", type=int, default=3)
     ap.add_argument("--mixed-only", action="store_true",
                     help="time only the tensor-core (mixed precision) products (profiling runs)")
+    ap.add_argument("--fp64-only", action="store_true", help="time only the FP64 product (profiling runs)")
     ap.add_argument("--shape", default="",
                     help="Nk,nocc,nvir,naux overriding the workload's sizes (small cases for ncu captures)")
+    ap.add_argument("--dry-run", action="store_true", help="rank setup only, no GPU (CPU tests)")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        spawn_replicas(args.gpus, sys.argv[1:])
+        return
+    if args.dry_run:
+        dry_run(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
 
-    import numpy as np
     import torch
     dist, rank, ws = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -318,7 +441,7 @@ def main():
     if args.shape:
         cfg = dict(zip(("nk", "nocc", "nvir", "naux"), (int(x) for x in args.shape.split(","))))
     nk, o, v, Q = cfg["nk"], cfg["nocc"], cfg["nvir"], cfg["naux"]
-    nrhs = args.nrhs or nsys
+    nrhs = args.nrhs or len(comps)
     p = make_problem(nk, o, v, Q, seed=1266)
     t1, t2 = random_amplitudes(nk, o, v, seed=1267, scale1=0.01, scale2=0.01)
     prob = lr.Problem(nk, o, v, Q)
@@ -333,7 +456,7 @@ def main():
     Y2 = torch.empty_like(X2)
     st = torch.cuda.current_stream()
     if args.mixed_only:  # profiling runs: tensor-core products only, one informational line
-        mixed = time_mixed(lr, prob, X1, X2, None, None, args, st, dist, nrhs * args.steps * ws)
+        mixed = time_mixed(lr, prob, X1, X2, None, None, args.steps, args.warmup, st, dist, nrhs * args.steps * ws)
         if rank == 0:
             print(json.dumps({"profiling": True, "workload": cfg, "rhs_per_step": nrhs, "mixed_precision": mixed}),
                   flush=True)
@@ -350,7 +473,6 @@ def main():
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    prob.profile(True)
     n0 = prob.kernel_launches
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -364,14 +486,26 @@ def main():
         dist.barrier()
     ms = e0.elapsed_time(e1)
     launches = prob.kernel_launches - n0
-    lad_ms, lad_n, lad_fl = prob.profile_query("ladder")
-    wb_ms, wb_n, wb_fl = prob.profile_query("W build")
-    all_ms, all_n, all_fl = prob.profile_query("")
-    prob.profile(False)
     clk = clocks.stop()
     ms = _max_over_ranks(dist, ms)
     products = nrhs * args.steps * ws
     value = products / (ms / 1000.0)
+
+    # per-op CUDA events on one more (untimed) product: the GEMM kernel's rate and the ladder
+    prob.profile(True)
+    step()
+    rep = prob.profile_report()
+    lad_ms, lad_n, lad_fl = prob.profile_query("ladder")
+    all_ms, all_n, all_fl = prob.profile_query("")
+    prob.profile(False)
+    gemm_ms = sum(r[1] for r in rep if r[3] > 0)
+    gemm_fl = sum(r[3] for r in rep if r[3] > 0)
+    gemm_n = sum(r[2] for r in rep if r[3] > 0)
+    if rank == 0 and args.fp64_only:
+        print(json.dumps({"profiling": True, "workload": cfg, "rhs_per_step": nrhs, "ms_per_step": ms / args.steps,
+                          "value": value, "report": rep[:20]}), flush=True)
+        prob.close()
+        return
 
     # end to end through the Python/C-ABI call with pinned host buffers
     h1 = torch.as_tensor(x1).pin_memory()
@@ -397,20 +531,37 @@ def main():
            "h2d_bytes_per_step": int(h1.numel() * 16 + h2.numel() * 16),
            "d2h_bytes_per_step": int(o1.numel() * 16 + o2.numel() * 16)}
 
-    lad_per_launch_fl = lad_fl / max(lad_n, 1)
-    lad_avg_ms = lad_ms / max(lad_n, 1)
-    achieved = lad_per_launch_fl / (lad_avg_ms * 1e-3) / 1e9 if lad_n else None
-    default_workload = args.config == "c2" and not args.shape and nrhs == 15
+    # roofline of the dominant kernel: the FP64 tiled GEMM (every contraction of the FP64 product;
+    # the ladder is its largest op).  Algorithmic flops count 8 real flops per complex
+    # multiply-add; the kernel executes 6 (Gauss's three-product form), so the pipe's own
+    # utilisation is `executed_frac`.
+    achieved = gemm_fl / (gemm_ms * 1e-3) / 1e9 if gemm_ms else None
+    lad_rate = lad_fl / (lad_ms * 1e-3) / 1e9 if lad_ms else None
+    default_workload = args.config == "c2" and not args.shape and nrhs == len(comps)
+    traffic = None
+    if TRAFFIC_RECORD and default_workload and _source_sha(TRAFFIC_RECORD[0]) == TRAFFIC_RECORD[1]:
+        traffic = TRAFFIC_RECORD[2]
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
             "frac": (achieved / FP64_NOMINAL_GFLOPS) if achieved else None,
-            "traffic": LADDER_TRAFFIC_BYTES if default_workload else None,
-            "kernel": "zgemm_seg_kernel (ladder contraction)",
-            "peak_source": "FP64 nominal 1.25 TFLOP/s of the profiling recipe (DFMA probe measured 1.195)",
-            "ladder_share_of_step": lad_ms / max(all_ms, 1e-9), "wbuild_share_of_step": wb_ms / max(all_ms, 1e-9),
-            "step_gflops_algorithmic": all_fl / (all_ms * 1e-3) / 1e9 if all_ms else None}
+            "executed_frac": (0.75 * achieved / FP64_NOMINAL_GFLOPS) if achieved else None,
+            "traffic": traffic,
+            "kernel": "zgemm_seg_kernel<double> (all FP64 contractions of the product)",
+            "launches_per_step": gemm_n,
+            "peak_source": "FP64 nominal 1.25 TFLOP/s of the profiling recipe (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+            "ladder_gflops": lad_rate, "ladder_share_of_step": lad_ms / max(all_ms, 1e-9),
+            "gemm_share_of_step": gemm_ms / max(all_ms, 1e-9),
+            "step_gflops_algorithmic": all_fl / (all_ms * 1e-3) / 1e9 if all_ms else None,
+            "profile": "per-op CUDA events on one untimed product after the timed region"}
 
     # mixed precision: the same product with the GEMMs on tcgen05 (BF16x3 and TF32, FP32 accumulate)
-    mixed = {} if args.no_mixed else time_mixed(lr, prob, X1, X2, Y1, Y2, args, st, dist, products)
+    mixed = {} if args.no_mixed else time_mixed(lr, prob, X1, X2, Y1, Y2, args.steps, args.warmup, st, dist,
+                                                 products)
+    prob.close()
+    del X1, X2, Y1, Y2, h1, h2, o1, o2
+    torch.cuda.empty_cache()
+    extras = {}
+    for name in [x for x in args.extra.split(",") if x] if not args.no_mixed and not args.shape else []:
+        extras[name] = extra_workload(lr, name, args.extra_steps, dist, rank)
 
     alpha = None
     if rank == 0 and not args.no_alpha:
@@ -420,24 +571,26 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         r, dt, threads, sample = cpu_oracle_rate(cfg, args.ref_blocks)
         cpu = {"value": r, "unit": "products/s", "cores": threads, "kind": "oracle", "sample": sample,
-               "seconds": dt}
+               "seconds": dt, **host_cpu()}
     if rank == 0:
         line = {"metric": "LR-CCSD Jacobian products/s", "value": value, "unit": "products/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
                 "data": "synthetic",
                 "config": {"workload": (f"{args.config}: Nk={nk} nocc={o} nvir={v} naux={Q}, {nrhs} vectors per "
-                                        f"step ({len(comps)} dipole components x omega in {omegas} Ha, +-omega)"),
+                                        f"step (the {len(comps)} dipole components at one frequency of the "
+                                        f"alpha tensor at omega in {omegas} Ha)"),
                            "precision": "fp64", "rhs_per_step": nrhs, "parallelism": f"replicas x{ws}",
                            "l2": (f"working set larger than L2 (vector {16 * nk**3 * o * o * v * v / 1e6:.0f} MB, "
                                   f"fixed intermediates {prob_fixed_gb:.1f} GB); no flush")},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "mixed_precision": mixed, "alpha_wall_time": alpha,
+                "mixed_precision": mixed, "larger_workloads": extras, "alpha_wall_time": alpha,
                 "clocks": clk}
         print(json.dumps(line), flush=True)
-    prob.close()
     if dist is not None:
+        dist.barrier()
         dist.destroy_process_group()
+
 
 if __name__ == "__main__":
     main()

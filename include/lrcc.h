@@ -129,8 +129,10 @@ lrcc_status lrcc_jacobian_apply(lrcc_problem* p, int32_t transpose, int32_t nrhs
  * library keeps until exit; the problem's own buffers (allocated by lrcc_create and
  * lrcc_set_ground_state) are used as they are.  Calls no cudaMalloc, cudaFree or
  * other allocating routine.  Problems whose vectors plus scratch exceed the array
- * return LRCC_EUNSUPPORTED with the sizes in lrcc_last_error.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * return LRCC_EUNSUPPORTED with the sizes in lrcc_last_error.  The device the problem
+ * was created on must be current (LRCC_EINVAL otherwise).  The first call on a device
+ * (and the first after that device's context was replaced, e.g. by cudaDeviceReset)
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture.  Every call, from any
  * problem, shares the one array: calls whose GPU work overlaps in time race and give
  * wrong results, so serialize them (for example on one stream).  Asynchronous on

@@ -105,6 +105,10 @@ struct PGemmArgs {
   double2* C;
   long long abytes, bbytes, sA, sB, sC;
   int nrhs = 1;  // persistent kernel: right-hand sides folded into its tile loop
+  // persistent kernel: most k-steps (P_BKR real K each) summed in one FP32 accumulator; a
+  // tile with more is done in chunks, each added into the FP64 destination by the epilogue
+  // (accumulating epilogue only)
+  int kchunk = 1 << 30;
 };
 long long packed_bytes(int mode, int R, int K);
 cudaError_t launch_pack(const PackArgs& p, int prec, int nrhs, cudaStream_t st);

@@ -3,8 +3,9 @@
 //
 // On GB300 the FP64 pipe (measured ~1.2 TFLOP/s for DFMA) is the bound of every
 // FP64 contraction in this path, so the GEMM is a shared-memory tiled DFMA kernel:
-// each thread owns a TM x TN register tile of complex accumulators (4 DFMA per
-// complex MAC); tiles are picked per op to minimise padded work.
+// each thread owns a TM x TN register tile of complex accumulators (3 DFMA per
+// complex MAC: Gauss's three-product form); tiles are picked per op to minimise padded
+// work.
 //
 // The same GEMM with FP32 arithmetic (operands rounded to FP32 when staged in shared
 // memory, FP32 accumulators, the FP64 destination updated in FP64) serves the mixed-
@@ -43,8 +44,15 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   constexpr int NTX = BN / TN, NTY = BM / TM, NT = NTX * NTY;
   using C2 = Cplx<T>;
   using V2 = typename C2::t;
-  __shared__ V2 As[BK][BM];
-  __shared__ V2 Bs[BK][BN];
+  // FP64: Gauss's three-product form of the complex MAC.  With P1 = ar br, P2 = ai bi,
+  // P3 = (ar + ai)(br + bi) summed over K, C = (P1 - P2) + i (P3 - P1 - P2): 3 DFMA per
+  // complex MAC instead of 4 on the FP64 pipe that bounds these GEMMs.  The sums ar + ai and
+  // br + bi are formed once per element when the tiles are staged (a third shared-memory
+  // plane).  FP32 (mixed precision, HBM-bound shapes) keeps the four-product form.
+  constexpr bool G3 = sizeof(T) == 8;
+  constexpr int NP = G3 ? 3 : 2;
+  __shared__ T As[NP][BK][BM];
+  __shared__ T Bs[NP][BK][BN];
   const int tpb = g.tiles_m * g.tiles_n;
   const int bid = blockIdx.x;
   const int per_batch = tpb * g.nsplit;
@@ -61,14 +69,14 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   const int tid = threadIdx.x;
   const int tx = tid % NTX, ty = tid / NTX;
   const int M = g.M, N = g.N, K = g.K;
-  T accr[TM][TN], acci[TM][TN];
+  // G3: acc[0] = P1, acc[1] = P2, acc[2] = P3; otherwise acc[0] = Re, acc[1] = Im
+  T acc[NP][TM][TN];
 #pragma unroll
-  for (int i = 0; i < TM; ++i)
+  for (int q = 0; q < NP; ++q)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) {
-      accr[i][j] = T(0);
-      acci[i][j] = T(0);
-    }
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[q][i][j] = T(0);
   // iteration space of this batch entry: (segment, K block), segment-major; this CTA
   // takes the split's contiguous range of it
   const int s0 = g.sbeg[batch], s1 = g.sbeg[batch + 1];
@@ -93,7 +101,10 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         const int gm = m0 + m, gk = k0 + k;
         double2 val = make_double2(0.0, 0.0);
         if (gm < M && gk < K) val = g.ta ? Ap[(long long)gk * g.lda + gm] : Ap[(long long)gm * g.lda + gk];
-        As[k][m] = C2::from(val);
+        const V2 cv = C2::from(val);
+        As[0][k][m] = cv.x;
+        As[1][k][m] = cv.y;
+        if constexpr (G3) As[2][k][m] = cv.x + cv.y;
       }
       for (int idx = tid; idx < BK * BN; idx += NT) {
         int k, n;
@@ -107,24 +118,36 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         const int gn = n0 + n, gk = k0 + k;
         double2 val = make_double2(0.0, 0.0);
         if (gn < N && gk < K) val = g.tb ? Bp[(long long)gn * g.ldb + gk] : Bp[(long long)gk * g.ldb + gn];
-        Bs[k][n] = C2::from(val);
+        const V2 cv = C2::from(val);
+        Bs[0][k][n] = cv.x;
+        Bs[1][k][n] = cv.y;
+        if constexpr (G3) Bs[2][k][n] = cv.x + cv.y;
       }
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        V2 a[TM], b[TN];
+        T a[NP][TM], b[NP][TN];
 #pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * NTY];
+        for (int q = 0; q < NP; ++q) {
 #pragma unroll
-        for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + j * NTX];
+          for (int i = 0; i < TM; ++i) a[q][i] = As[q][kk][ty + i * NTY];
+#pragma unroll
+          for (int j = 0; j < TN; ++j) b[q][j] = Bs[q][kk][tx + j * NTX];
+        }
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
           for (int j = 0; j < TN; ++j) {
-            accr[i][j] = C2::mad(a[i].x, b[j].x, accr[i][j]);
-            accr[i][j] = C2::mad(-a[i].y, b[j].y, accr[i][j]);
-            acci[i][j] = C2::mad(a[i].x, b[j].y, acci[i][j]);
-            acci[i][j] = C2::mad(a[i].y, b[j].x, acci[i][j]);
+            if constexpr (G3) {
+              acc[0][i][j] = C2::mad(a[0][i], b[0][j], acc[0][i][j]);
+              acc[1][i][j] = C2::mad(a[1][i], b[1][j], acc[1][i][j]);
+              acc[2][i][j] = C2::mad(a[2][i], b[2][j], acc[2][i][j]);
+            } else {
+              acc[0][i][j] = C2::mad(a[0][i], b[0][j], acc[0][i][j]);
+              acc[0][i][j] = C2::mad(-a[1][i], b[1][j], acc[0][i][j]);
+              acc[1][i][j] = C2::mad(a[0][i], b[1][j], acc[1][i][j]);
+              acc[1][i][j] = C2::mad(a[1][i], b[0][j], acc[1][i][j]);
+            }
           }
       }
       __syncthreads();
@@ -134,6 +157,19 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       ++s;
     }
   }
+  T accr[TM][TN], acci[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      if constexpr (G3) {
+        accr[i][j] = acc[0][i][j] - acc[1][i][j];
+        acci[i][j] = acc[2][i][j] - acc[0][i][j] - acc[1][i][j];
+      } else {
+        accr[i][j] = acc[0][i][j];
+        acci[i][j] = acc[1][i][j];
+      }
+    }
   if (g.nsplit > 1) {  // raw partial tile; alpha and the epilogue come in the reduction
     double2* Pp = g.part + ((rhs * g.nbatch + batch) * g.nsplit + sp) * (long long)M * N;
 #pragma unroll

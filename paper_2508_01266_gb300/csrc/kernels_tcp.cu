@@ -466,6 +466,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
       const int s0 = g.sbeg[batch], total = (g.sbeg[batch + 1] - s0) * nkt;
       const unsigned char* Ab = g.A + rhs * g.sA;
       const unsigned char* Bb = g.B + rhs * g.sB;
+      // the chunks of a tile are consecutive items of this CTA: the k-steps in order
       for (int i = 0; i < total; ++i) {
         const int s = (int)(it % P_STAGES);
         if (it >= P_STAGES && !wait_or_fail(su32(&empty[s]), (uint32_t)(((it / P_STAGES) - 1) & 1), &fail_sh)) {
@@ -509,10 +510,13 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
     long long it = 0;
     int local = 0;
     bool ok = true;
-    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++local) {
-      int rhs, batch, mt, nt;
-      decode_tile(g, tile, rhs, batch, mt, nt);
-      const int total = (g.sbeg[batch + 1] - g.sbeg[batch]) * nkt;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+     int rhs, batch, mt, nt;
+     decode_tile(g, tile, rhs, batch, mt, nt);
+     const int total = (g.sbeg[batch + 1] - g.sbeg[batch]) * nkt;
+     const int nch = total > 0 ? (total + g.kchunk - 1) / g.kchunk : 1;
+     for (int ch = 0; ch < nch && ok; ++ch, ++local) {
+      const int lo = ch * g.kchunk, hi = min(total, lo + g.kchunk);
       const int b = local & 1;
       if (local >= 2 && !wait_or_fail(su32(&acce[b]), (uint32_t)(((local / 2) - 1) & 1), &fail_sh)) {
         ok = false;
@@ -520,7 +524,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t acc = tmem + (uint32_t)(b * P_BNR);
-      for (int i = 0; i < total; ++i, ++it) {
+      for (int i = lo; i < hi; ++i, ++it) {
         const int s = (int)(it % P_STAGES);
         if (!wait_or_fail(su32(&full[s]), (uint32_t)((it / P_STAGES) & 1), &fail_sh)) {
           ok = false;
@@ -533,7 +537,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
           for (int ks = 0; ks < P_BKR / 8; ++ks) {
             const uint32_t ko = ks * 2 * LBO;
             const uint64_t ad = sdesc(a0 + ko, LBO, SBO_A), bd = sdesc(b0 + ko, LBO, SBO_A);
-            const uint32_t accum = (i > 0 || ks > 0) ? 1u : 0u;
+            const uint32_t accum = (i > lo || ks > 0) ? 1u : 0u;
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
@@ -546,7 +550,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
             const uint64_t ahi = sdesc(a0 + ko, LBO, SBO_A), bhi = sdesc(b0 + ko, LBO, SBO_A);
             const uint64_t alo = sdesc(a0 + P_BM * 64 + ko, LBO, SBO_A),
                            blo = sdesc(b0 + P_BNR * 64 + ko, LBO, SBO_A);
-            const uint32_t accum = (i > 0 || ks > 0) ? 1u : 0u;
+            const uint32_t accum = (i > lo || ks > 0) ? 1u : 0u;
             asm volatile(
                 "{\n .reg .pred p, q;\n setp.ne.b32 p, %6, 0;\n setp.ne.b32 q, 1, 0;\n"
                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
@@ -560,10 +564,11 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
                      : "memory");
       }
       if (!ok) break;
-      // accumulator b complete once every MMA above is (immediately when total == 0)
+      // accumulator b complete once every MMA above is (immediately when the item is empty)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        su32(&accf[b]))
                    : "memory");
+     }
     }
     if (!ok) fail_sh = 1;
     // tracks every MMA this thread issued: TMEM is released only after it completes
@@ -589,20 +594,26 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
       asm volatile("prefetch.global.L2 [%0];" ::"l"(row + cnt - 1));
     };
     int local = 0;
+    bool eok = true;
     if (blockIdx.x < ntiles) prefetch_c(blockIdx.x);
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++local) {
-      int rhs, batch, mt, nt;
-      decode_tile(g, tile, rhs, batch, mt, nt);
-      const int total = (g.sbeg[batch + 1] - g.sbeg[batch]) * nkt;
+    for (long long tile = blockIdx.x; tile < ntiles && eok; tile += gridDim.x) {
+     int rhs, batch, mt, nt;
+     decode_tile(g, tile, rhs, batch, mt, nt);
+     const int tot = (g.sbeg[batch + 1] - g.sbeg[batch]) * nkt;
+     const int nch = tot > 0 ? (tot + g.kchunk - 1) / g.kchunk : 1;
+     // chunk by chunk, the same thread adds each chunk's sum into the same C elements
+     for (int ch = 0; ch < nch; ++ch, ++local) {
+      const int total = min(tot - ch * g.kchunk, g.kchunk);
       const int b = local & 1;
       bool ok = wait_or_fail(su32(&accf[b]), (uint32_t)((local / 2) & 1), &fail_sh);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
         if (lane == 0) fail_sh = 1;
+        eok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      prefetch_c(tile + gridDim.x);
+      if (ch == nch - 1) prefetch_c(tile + gridDim.x);
       const int m = mt * P_BM + q * 32 + lane;
       double2* Cp = g.C + rhs * g.sC + g.coff[batch];
 #pragma unroll 1
@@ -664,6 +675,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&acce[b])) : "memory");
+     }
     }
   }
   __syncthreads();

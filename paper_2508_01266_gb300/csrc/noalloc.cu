@@ -23,9 +23,29 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocElems];
 
-// Device addresses of g_noalloc_scratch, filled on the first call on each device.
-double2* g_noalloc_ptr[kMaxDevices] = {nullptr};
+// Device address of g_noalloc_scratch per device, with the CUDA context it was looked up
+// in: a new context on that device (after cudaDeviceReset, for example) has its own copy
+// of the array, so the address is looked up again.
+struct ScratchAddr {
+  void* ctx = nullptr;
+  double2* ptr = nullptr;
+};
+ScratchAddr g_noalloc_addr[kMaxDevices];
 std::mutex g_noalloc_mu;
+
+// cuCtxGetCurrent through the runtime's driver entry-point query (no link against libcuda).
+typedef int (*CtxGetCurrentFn)(void**);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = []() -> CtxGetCurrentFn {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return (CtxGetCurrentFn)f;
+  }();
+  return fn;
+}
 
 }  // namespace
 
@@ -52,6 +72,11 @@ extern "C" lrcc_status lrcc_jacobian_apply_noalloc(lrcc_problem* p, int32_t tran
   }
   int dev = 0;
   if (!rt.ck(cudaGetDevice(&dev), "jacobian_apply_noalloc: cudaGetDevice")) return LRCC_ECUDA;
+  if (dev != rt.device) {
+    rt.err = "jacobian_apply_noalloc: device " + std::to_string(dev) + " is current, but the problem's buffers " +
+             "are on device " + std::to_string(rt.device) + "; make that device current";
+    return LRCC_EINVAL;
+  }
   if (dev < 0 || dev >= kMaxDevices) {
     rt.err = "jacobian_apply_noalloc: device ordinal out of range";
     return LRCC_EUNSUPPORTED;
@@ -59,14 +84,18 @@ extern "C" lrcc_status lrcc_jacobian_apply_noalloc(lrcc_problem* p, int32_t tran
   double2* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    void* ctx = nullptr;
+    if (CtxGetCurrentFn f = ctx_get_current()) f(&ctx);
+    ScratchAddr& a = g_noalloc_addr[dev];
+    if (!a.ptr || ctx != a.ctx) {
       void* addr = nullptr;
       // host code must not use the symbol itself: ask the runtime for its device address
       if (!rt.ck(cudaGetSymbolAddress(&addr, g_noalloc_scratch), "jacobian_apply_noalloc: cudaGetSymbolAddress"))
         return LRCC_ECUDA;
-      g_noalloc_ptr[dev] = (double2*)addr;
+      a.ptr = (double2*)addr;
+      a.ctx = ctx;
     }
-    base = g_noalloc_ptr[dev];
+    base = a.ptr;
   }
   // a null handle is the caller's legacy default stream (this library is built with
   // per-thread default streams, under which 0 would name the calling thread's stream)

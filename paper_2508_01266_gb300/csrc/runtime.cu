@@ -84,6 +84,7 @@ void Runtime::release() {
 
 lrcc_status Runtime::init(const lrcc_dims& d, int64_t ws_budget) {
   dims = d;
+  if (cudaGetDevice(&device) != cudaSuccess) device = -1;
   try {
     Dims dd{d.nk, d.nocc, d.nvir, d.naux};
     plan = build_plan(dd, ws_budget);
@@ -185,17 +186,30 @@ static int reduce_f32_min_split(const Gemm& g, const GemmDesc& d) {
   return (int)std::max<long long>(1, (d.max_seg + segs - 1) / segs);
 }
 
+// Complex K terms per k-step of the packed kernel (32 real K = 16 complex).
+constexpr long long TCP_KSTEP = 16;
+// Output tiles (128 x 128 complex) of one vector of a packed GEMM.
+static long long tcp_tiles(const Gemm& g) {
+  return (long long)((g.M + 127) / 128) * ((g.N + 127) / 128) * g.nbatch();
+}
 // Packed-operand tensor-core path for GEMMs with both output dimensions at least
-// LRCC_PACKED_MIN (default 32), K >= 16 and a contraction within TC_CHAIN_MAX (the
-// packed kernel sums a tile's whole contraction in one FP32 accumulator); the
-// autotuner may also choose it per op, under the same chain limit.
+// LRCC_PACKED_MIN (default 32) and K >= 16.  The persistent packed kernel sums at most
+// TC_CHAIN_MAX complex terms in one FP32 accumulator: a longer contraction is done in
+// chunks whose sums its epilogue adds into the FP64 destination one after the other
+// (same thread, same elements).  That serialises a tile's chunks, so long contractions
+// take this path only when one vector alone has a few dozen output tiles and the chunks
+// are few (the ladder at Nk = 7 and 9: two or three); a storing epilogue (the W-block
+// build) cannot be chunked.  The autotuner may also choose it per op, under the same rules.
 static bool packed_ok(const Gemm& g, const GemmDesc& d) {
   static const int pmin = []() {
     const char* e = std::getenv("LRCC_PACKED_MIN");
     const int v = e ? std::atoi(e) : 0;
     return v > 0 ? v : 32;
   }();
-  return g.M >= pmin && g.N >= pmin && g.K >= 16 && chain_len(g, d) <= TC_CHAIN_MAX;
+  if (g.M < pmin || g.N < pmin || g.K < 16) return false;
+  const long long chain = chain_len(g, d);
+  if (chain <= TC_CHAIN_MAX) return true;
+  return g.epi == 0 && chain <= 4 * TC_CHAIN_MAX && tcp_tiles(g) >= 32;
 }
 bool Runtime::use_packed(const Gemm& g, const GemmDesc& d) const { return packed_ok(g, d); }
 
@@ -382,8 +396,15 @@ lrcc_status Runtime::run_packed(int gi, const Gemm& g, double2* const ar[AR_COUN
     return !(e && std::string(e) == "classic");
   }();
   const int nrr = fixed_only ? 1 : nr;
-  const cudaError_t e = persistent ? launch_gemm_tcp_persistent(a, prec, nrr, dflag, st)
-                                   : launch_gemm_tcp(a, prec, nrr, dflag, st);
+  // FP32 accumulator chains within TC_CHAIN_MAX: longer tiles in chunks (persistent kernel)
+  a.kchunk = (int)(TC_CHAIN_MAX / TCP_KSTEP);
+  const bool chunked = chain_len(g, d) > TC_CHAIN_MAX;
+  if (chunked && g.epi != 0) {
+    err = "packed gemm: a storing epilogue cannot take a chunked contraction";
+    return LRCC_EINVAL;
+  }
+  const cudaError_t e = (persistent || chunked) ? launch_gemm_tcp_persistent(a, prec, nrr, dflag, st)
+                                                : launch_gemm_tcp(a, prec, nrr, dflag, st);
   if (!ck(e, "packed gemm")) return LRCC_ECUDA;
   ++launches;
   return LRCC_OK;
@@ -608,6 +629,8 @@ lrcc_status Runtime::launch_gemm(GemmArgs a, const Gemm& g, const GemmChoice& c,
 // events) and keep the fastest.  Ops whose default already takes over 50 ms are
 // compute-saturated large GEMMs and keep their default.  The timing launches
 // accumulate into the op's destination, so the caller reruns the product afterwards.
+constexpr int kTuneVectors = 4;
+
 lrcc_status Runtime::autotune(const Program& pr, double2* const ar[AR_COUNT], int nrhs, cudaStream_t st, int prec,
                               std::map<int, GemmChoice>& out) {
   long long stride[AR_COUNT] = {0, plan.arena_size[AR_IN], plan.arena_size[AR_OUT], plan.arena_size[AR_SCR], 0};
@@ -619,7 +642,9 @@ lrcc_status Runtime::autotune(const Program& pr, double2* const ar[AR_COUNT], in
     const Gemm& g = plan.gemms[op.idx];
     if (g.arC == AR_FIX) continue;  // never disturb fixed data
     const GemmDesc& d = gdesc[op.idx];
-    const int nr = op.fixed_only ? 1 : nrhs;
+    // candidates are timed on the first few vectors of the batch (per-vector work is the
+    // same for every vector; a large batch would multiply the tuning time)
+    const int nr = op.fixed_only ? 1 : std::min(nrhs, kTuneVectors);
     GemmArgs a;
     a.M = g.M; a.N = g.N; a.K = g.K; a.ta = g.ta; a.tb = g.tb;
     a.epi = g.epi; a.ep1 = g.ep[1]; a.ep2 = g.ep[2]; a.ep3 = g.ep[3];
@@ -685,7 +710,8 @@ lrcc_status Runtime::autotune(const Program& pr, double2* const ar[AR_COUNT], in
           if (key(x) == key(c)) return;
         cand.push_back(c);
       };
-      if (mixed && g.M >= 8 && g.N >= 8 && g.K >= 8 && chain_len(g, d) <= TC_CHAIN_MAX) {
+      if (mixed && g.M >= 8 && g.N >= 8 && g.K >= 8 &&
+          (chain_len(g, d) <= TC_CHAIN_MAX || packed_ok(g, d))) {
         GemmChoice pk;
         pk.packed = true;
         add(pk);
@@ -834,14 +860,24 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
       // a scratch buffer starts its lifetime at zero (buffers with disjoint lifetimes share memory)
       const ZeroSpec& z = plan.zeros[op.idx];
       const size_t pitch = (size_t)std::max<long long>(stride[z.arena], z.n) * sizeof(double2);
-      e = cudaMemset2DAsync(ar[z.arena] + z.off, pitch, 0, (size_t)z.n * sizeof(double2), nr, st);
+      if (nr == 1 || pitch <= (size_t)INT32_MAX) {
+        e = cudaMemset2DAsync(ar[z.arena] + z.off, pitch, 0, (size_t)z.n * sizeof(double2), nr, st);
+      } else {  // a 2-D memset's pitch is limited to 2^31 - 1 bytes: one range per vector
+        for (int r = 0; r < nr && e == cudaSuccess; ++r)
+          e = cudaMemsetAsync(ar[z.arena] + z.off + (long long)r * stride[z.arena], 0,
+                              (size_t)z.n * sizeof(double2), st);
+      }
     }
     if (prof) {
       cudaEventRecord(rec.b, st);
       prof_recs.push_back(rec);
     }
     nvtxRangePop();
-    if (!ck(e, "kernel launch")) return LRCC_ECUDA;
+    if (e != cudaSuccess) {
+      static const char* kinds[] = {"gemm", "permute", "transpose", "zero"};
+      const std::string what = std::string("kernel launch (") + kinds[op.kind] + " op '" + optag + "')";
+      if (!ck(e, what.c_str())) return LRCC_ECUDA;
+    }
   }
   if (prec > 0 && !capturing) return read_flag(st);
   return LRCC_OK;
@@ -1191,6 +1227,20 @@ lrcc_status lrcc_set_ground_state(lrcc_problem* p, const void* t1, const void* t
   return LRCC_OK;
 }
 
+// Strided device-to-device copy of `rows` rows of `width` bytes.  A 2-D copy's pitches are
+// limited to 2^31 - 1 bytes, and a vector arena of the larger workloads is wider than that
+// (6.9 GB per vector at Nk=9, nocc=12, nvir=64): then one copy per row.
+static cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, int rows,
+                             cudaStream_t st) {
+  if (rows == 1) return cudaMemcpyAsync(dst, src, width, cudaMemcpyDeviceToDevice, st);
+  if (dpitch <= (size_t)INT32_MAX && spitch <= (size_t)INT32_MAX)
+    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, cudaMemcpyDeviceToDevice, st);
+  cudaError_t e = cudaSuccess;
+  for (int r = 0; r < rows && e == cudaSuccess; ++r)
+    e = cudaMemcpyAsync((char*)dst + r * dpitch, (const char*)src + r * spitch, width, cudaMemcpyDeviceToDevice, st);
+  return e;
+}
+
 lrcc_status lrcc_jacobian_apply(lrcc_problem* p, int32_t transpose, int32_t nrhs, const void* x1, const void* x2,
                                 void* y1, void* y2, const lrcc_options* opt, void* stream) {
   if (!p) return LRCC_EINVAL;
@@ -1212,13 +1262,13 @@ lrcc_status lrcc_jacobian_apply(lrcc_problem* p, int32_t transpose, int32_t nrhs
   const size_t pitch = (size_t)P.arena_size[AR_IN] * sizeof(double2);
   double2* src = transpose ? rt.out : rt.in;
   double2* dst = transpose ? rt.in : rt.out;
-  if (!rt.ck(cudaMemcpy2DAsync(src + P.off_x1, pitch, x1, b1, b1, nrhs, cudaMemcpyDeviceToDevice, st), "copy x1") ||
-      !rt.ck(cudaMemcpy2DAsync(src + P.off_x2, pitch, x2, b2, b2, nrhs, cudaMemcpyDeviceToDevice, st), "copy x2"))
+  if (!rt.ck(copy_rows(src + P.off_x1, pitch, x1, b1, b1, nrhs, st), "copy x1") ||
+      !rt.ck(copy_rows(src + P.off_x2, pitch, x2, b2, b2, nrhs, st), "copy x2"))
     return LRCC_ECUDA;
   s = rt.apply(transpose, nrhs, st, prec, opt && opt->use_graphs, opt && opt->autotune);
   if (s != LRCC_OK) return s;
-  if (!rt.ck(cudaMemcpy2DAsync(y1, b1, dst + P.off_x1, pitch, b1, nrhs, cudaMemcpyDeviceToDevice, st), "copy y1") ||
-      !rt.ck(cudaMemcpy2DAsync(y2, b2, dst + P.off_x2, pitch, b2, nrhs, cudaMemcpyDeviceToDevice, st), "copy y2"))
+  if (!rt.ck(copy_rows(y1, b1, dst + P.off_x1, pitch, b1, nrhs, st), "copy y1") ||
+      !rt.ck(copy_rows(y2, b2, dst + P.off_x2, pitch, b2, nrhs, st), "copy y2"))
     return LRCC_ECUDA;
   return LRCC_OK;
 }

@@ -49,6 +49,7 @@ struct PackPlan {
 
 struct Runtime {
   lrcc_dims dims{};
+  int device = -1;  // CUDA device current when the problem was created (its buffers live there)
   Plan plan;
   Program jacT;
   std::vector<GemmDesc> gdesc;

@@ -31,10 +31,12 @@ def _setup(lr, nk, o, v, Q, seed=11, sigma=0.1):
 
 
 @pytest.mark.parametrize("nk,o,v,Q,sigma", [(2, 1, 3, 5, 0.1), (3, 2, 4, 6, 0.1), (3, 4, 16, 48, 0.1),
-                                            (2, 8, 16, 40, 0.1), (5, 8, 40, 160, 0.02)])
+                                            (2, 8, 16, 40, 0.1), (5, 8, 40, 160, 0.02),
+                                            (5, 4, 48, 60, 0.02)])
 @pytest.mark.parametrize("prec,bound", [(1, 3e-3), (2, 5e-5)])
 def test_mixed_products_vs_fp64(lr, nk, o, v, Q, sigma, prec, bound):
-    """sigma: DF factor scale (0.02 is the workloads' value)."""
+    """sigma: DF factor scale (0.02 is the workloads' value).  At (5, 4, 48, 60) the ladder
+    contracts 5 x 48^2 = 11520 terms per output: the packed kernel sums it in two chunks."""
     prob = _setup(lr, nk, o, v, Q, sigma=sigma)
     dev = torch.device("cuda")
     x1, x2 = random_amplitudes(nk, o, v, seed=5, scale1=1.0, scale2=1.0)

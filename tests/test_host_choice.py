@@ -1,7 +1,8 @@
 """Host-side tests (no GPU) of the executor's default kernel choices, read through the plan
 introspection call lrcc_plan_choice: in the mixed-precision modes every FP32 accumulation
 chain stays within 8192 complex terms (longer contractions go through K splits whose
-partials are summed in FP64), and FP64 products use FP64 arithmetic only.
+partials are summed in FP64, or through the packed kernel's chunks, each added into the
+FP64 destination), and FP64 products use FP64 arithmetic only.
 
 The chain lengths are recomputed here from each kernel's split rule and the plan's own
 segment lists, not from the library's split formulas."""
@@ -16,6 +17,8 @@ CHAIN_MAX = 8192  # complex terms summed in one FP32 accumulator
 TC_BK = 16        # complex K per iteration of the unpacked tensor-core kernel
 TILE_BK = 8       # complex K per iteration of the tiled kernel
 LANES = 32        # lanes of the reduction kernel's warp sums
+PK_STEP = 16      # complex K per k-step of the packed kernel (32 real K)
+PK_CHUNK = 512    # k-steps the packed kernel sums in one FP32 accumulator before adding it to C
 
 SHAPES = dict(CONFIGS)
 SHAPES.update({"chain_a": dict(nk=3, nocc=4, nvir=24, naux=60),
@@ -39,8 +42,9 @@ def _plan(lib, s):
     return h
 
 
-def _gemm_ops(lib, h):
-    """(gemm index, M, N, K, most segments of a batch entry) of every GEMM op of every program."""
+def _gemm_ops(lib, h, epi=None):
+    """(gemm index, M, N, K, most segments of a batch entry) of every GEMM op of every program;
+    `epi` (a dict) receives each op's epilogue kind (1: storing W-block build)."""
     seen = {}
     kif = (C.c_int32 * 3)()
     for which in range(7):
@@ -57,6 +61,8 @@ def _gemm_ops(lib, h):
                                       sbeg.ctypes.data_as(C.c_void_p), None, None) == 0
             maxseg = int(np.diff(sbeg).max()) if nb > 0 else 0
             seen[idx] = (ints[0], ints[1], ints[2], maxseg)
+            if epi is not None:
+                epi[idx] = ints[8]
     return seen
 
 
@@ -70,7 +76,8 @@ def _fp32_chain(c, K, maxseg):
     """Longest run of complex terms one FP32 accumulator sums under choice c (None: FP64)."""
     cdiv = lambda a, b: -(-a // b)
     if c["packed"]:
-        return maxseg * K  # one TMEM accumulator per tile over the whole contraction
+        # one TMEM accumulator per chunk of at most PK_CHUNK k-steps of a tile's contraction
+        return min(maxseg * cdiv(K, PK_STEP), PK_CHUNK) * PK_STEP
     if c["tc"]:
         iters = maxseg * cdiv(K, TC_BK)
         return cdiv(iters, c["nsplit"]) * TC_BK
@@ -88,7 +95,8 @@ def _fp32_chain(c, K, maxseg):
 def test_fp32_chains_capped_and_fp64_pure(lib, shape):
     h = _plan(lib, SHAPES[shape])
     try:
-        ops = _gemm_ops(lib, h)
+        epi = {}
+        ops = _gemm_ops(lib, h, epi)
         assert ops
         for idx, (M, N, K, maxseg) in ops.items():
             c0 = _choice(lib, h, idx, 0)
@@ -99,6 +107,8 @@ def test_fp32_chains_capped_and_fp64_pure(lib, shape):
                 assert c["max_seg"] == max(maxseg, 1)
                 assert c["nsplit"] >= 1
                 assert not (c["packed"] and c["tc"])
+                if c["packed"] and maxseg * K > CHAIN_MAX:  # chunked: only an accumulating epilogue
+                    assert epi[idx] == 0, (shape, idx)
                 chain = _fp32_chain(c, K, max(maxseg, 1))
                 if chain is not None:
                     assert chain <= CHAIN_MAX, (shape, idx, (M, N, K, maxseg), prec, c, chain)
@@ -108,8 +118,9 @@ def test_fp32_chains_capped_and_fp64_pure(lib, shape):
 
 def test_long_contractions_leave_the_packed_kernel(lib):
     """At Nk=5, nocc=8, nvir=40 the v x v and o x o intermediates summed over three momenta
-    contract up to 64000 complex terms per output; none of them may run on the packed kernel
-    (one FP32 accumulator per tile), while the ladder-sized GEMMs (K >= 16) still do."""
+    contract up to 64000 complex terms per output into a few small tiles; none of them may run
+    on the packed kernel (its chunks of one tile run one after the other), while the
+    ladder-sized GEMMs (K >= 16) still do."""
     h = _plan(lib, SHAPES["c2"])
     try:
         ops = _gemm_ops(lib, h)
@@ -121,6 +132,26 @@ def test_long_contractions_leave_the_packed_kernel(lib):
             big = [i for i, (M, N, K, ms) in ops.items()
                    if M >= 1600 and N >= 1600 and K >= 16 and ms * K <= CHAIN_MAX]
             assert big and all(_choice(lib, h, i, prec)["packed"] for i in big)
+    finally:
+        lib.lrcc_plan_destroy(h)
+
+
+def test_long_ladder_chains_take_the_packed_kernel_in_chunks(lib):
+    """At Nk=7, nocc=8, nvir=48 the ladder contracts 7 x 48^2 = 16128 complex terms per output;
+    its GEMMs stay on the packed kernel (two chunks of at most 8192 terms per tile), which
+    the tile counts fill."""
+    h = _plan(lib, SHAPES["c3"])
+    try:
+        ops = _gemm_ops(lib, h)
+        ladder = [i for i, (M, N, K, ms) in ops.items() if (M, N, K) == (448, 2304, 2304)]
+        assert ladder
+        for prec in (1, 2):
+            for i in ladder:
+                M, N, K, ms = ops[i]
+                c = _choice(lib, h, i, prec)
+                assert c["packed"] == 1, (i, c)
+                if ms * K > CHAIN_MAX:
+                    assert _fp32_chain(c, K, ms) <= CHAIN_MAX
     finally:
         lib.lrcc_plan_destroy(h)
 

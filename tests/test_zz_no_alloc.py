@@ -68,6 +68,23 @@ def test_noalloc_matches_allocating_entry_point(lr, nk, o, v, Q):
     prob.close()
 
 
+def test_noalloc_first_on_fresh_problem(lr):
+    """The allocation-free call comes first on a freshly created problem (no allocating product
+    has run on it, so no lazily created buffer exists), in both directions, and only then is
+    it compared with the allocating entry point."""
+    nk, o, v, Q = 3, 2, 4, 6
+    dev = torch.device("cuda")
+    for transpose in (0, 1):
+        prob = _problem(lr, nk, o, v, Q, seed=41 + transpose)
+        x1, x2 = random_amplitudes(nk, o, v, seed=200 + transpose, scale1=1.0, scale2=1.0)
+        X1 = torch.as_tensor(x1, device=dev)[None].contiguous()
+        X2 = torch.as_tensor(x2 * nk, device=dev)[None].contiguous()
+        y1, y2 = _noalloc(lr, prob, transpose, X1, X2)
+        r1, r2 = prob.jacobian_apply(X1, X2, transpose=bool(transpose))
+        assert _rel(y1, r1[0]) < TOL and _rel(y2, r2[0]) < TOL
+        prob.close()
+
+
 def test_noalloc_rejects_problems_beyond_its_limit(lr):
     prob = _problem(lr, 4, 4, 24, 32, seed=31)
     dev = torch.device("cuda")
