@@ -297,7 +297,7 @@ def alpha_wall_time(lr):
     return out
 
 
-def time_mixed(lr, prob, X1, X2, Y1, Y2, steps, warmup, st, dist, products):
+def time_mixed(lr, prob, X1, X2, Y1, Y2, steps, warmup, st, dist, products, autotune=True, precs=(2, 1)):
     """Time the tensor-core products (BF16x3 and TF32) on the same vectors; Y1/Y2 are the
     FP64 results (None: no error column).  The timed loop runs without per-op events; one
     more product with per-op events (same tuned kernels, eager) gives the ladder rate."""
@@ -307,9 +307,11 @@ def time_mixed(lr, prob, X1, X2, Y1, Y2, steps, warmup, st, dist, products):
     e1 = torch.cuda.Event(enable_timing=True)
     BF16_PEAK = _measured_peak("bf16_tflops", 1900.0)
     for prec, name, peak, passes in ((2, "bf16x3", BF16_PEAK, 3), (1, "tf32", BF16_PEAK * 1.1 / 2.25, 1)):
-        # the tensor-core products run with the autotuner (per-op kernel choice measured once
-        # during warm-up) and as CUDA graphs
-        opts = lr.default_options(precision=prec, autotune=1, use_graphs=1)
+        if prec not in precs:
+            continue
+        # the tensor-core products run as CUDA graphs, with the autotuner (per-op kernel choice
+        # measured once during warm-up) unless autotune is off
+        opts = lr.default_options(precision=prec, autotune=int(autotune), use_graphs=1)
         M1, M2 = torch.empty_like(X1), torch.empty_like(X2)
         for _ in range(max(warmup, 2)):
             prob.jacobian_apply(X1, X2, y1=M1, y2=M2, options=opts)
@@ -332,7 +334,7 @@ def time_mixed(lr, prob, X1, X2, Y1, Y2, steps, warmup, st, dist, products):
             err = max(float((M1 - Y1).abs().max() / Y1.abs().max()), float((M2 - Y2).abs().max() / Y2.abs().max()))
         lach = (lfl / max(ln, 1)) / ((lms / max(ln, 1)) * 1e-3) / 1e12 if ln else None
         mixed[name] = {"value": products / (mms / 1000.0), "unit": "products/s", "ms_per_step": mms / steps,
-                       "steps": steps, "autotune": True, "cuda_graphs": True,
+                       "steps": steps, "autotune": bool(autotune), "cuda_graphs": True,
                        "gpu_launches": launches,
                        "max_rel_err_vs_fp64": err,
                        "ladder": {"achieved_tflops_algorithmic": lach,
@@ -366,7 +368,9 @@ def extra_workload(lr, name, steps, dist, rank):
     torch.cuda.synchronize()
     setup = time.perf_counter() - t0
     st = torch.cuda.current_stream()
-    m = time_mixed(lr, prob, X1, X2, None, None, steps, 1, st, dist, nrhs * steps)["bf16x3"]
+    # default kernel choices: the autotuner's per-op timing would take minutes at these sizes
+    m = time_mixed(lr, prob, X1, X2, None, None, steps, 1, st, dist, nrhs * steps, autotune=False,
+                   precs=(2,))["bf16x3"]
     prob.close()
     del X1, X2
     torch.cuda.empty_cache()

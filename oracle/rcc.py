@@ -51,6 +51,11 @@ def ein(spec, *ops):
     return torch.einsum(spec, *ops)
 
 
+def blocks_of(t2):
+    """Nested lists of the momentum blocks t2[ki][kj][ka] (views)."""
+    return [[list(x.unbind(0)) for x in y.unbind(0)] for y in t2.unbind(0)]
+
+
 class RCC:
     """Closed-shell k-point CCSD system built from a synth.Problem."""
 
@@ -88,9 +93,10 @@ class RCC:
         h = self.h if h is None else h
         eye = torch.eye(self.n, dtype=DT)
         Xl, Xr = [], []
+        t1b = t1.unbind(0)
         for k in range(nk):
             tau = torch.zeros((self.n, self.n), dtype=DT)
-            tau[o:, :o] = t1[k].T
+            tau[o:, :o] = t1b[k].T
             Xl.append(eye - tau)
             Xr.append(eye + tau)
         Lt = torch.stack([torch.stack([ein("pr,Qrs,sq->Qpq", Xl[k1], self.L[k1, k2], Xr[k2])
@@ -121,9 +127,23 @@ class RCC:
                 memo[key] = ein("Qpq,Qrs->pqrs", Lt[kp, kq][:, sp, sq], Lt[kr, ks][:, sr, ss])
             return memo[key]
 
+        v = self.v
+
+        def vvvv(ka, kc, kb_, kd):
+            # (ac|bd) as the matrix [(c,d), (a,b)], built once per call and block: the same
+            # block serves every (ki, kj) pair with ki + kj = ka + kb
+            key = ("vvvv", ka, kc, kb_, kd)
+            if key not in memo:
+                blk = ein("Qac,Qbd->cdab", Lt[ka, kc][:, Vs, Vs], Lt[kb_, kd][:, Vs, Vs])
+                memo[key] = blk.reshape(v * v, v * v)
+            return memo[key]
+
         kb = self.kb
-        T = lambda ki, kj, ka: t2[ki, kj, ka]                                       # noqa: E731
-        U = lambda ki, kj, ka: 2.0 * t2[ki, kj, ka] - t2[ki, kj, kb(ki, kj, ka)].transpose(2, 3)  # noqa: E731
+        # amplitude blocks t2[ki][kj][ka] taken apart once (one stacked gradient per level
+        # under reverse-mode differentiation, instead of a full-size one per block read)
+        t2b = blocks_of(t2)
+        T = lambda ki, kj, ka: t2b[ki][kj][ka]                                      # noqa: E731
+        U = lambda ki, kj, ka: 2.0 * t2b[ki][kj][ka] - t2b[ki][kj][kb(ki, kj, ka)].transpose(2, 3)  # noqa: E731
         K = range(nk)
         Ct, Dt, Ev, Eo = {}, {}, {}, {}
 
@@ -185,15 +205,16 @@ class RCC:
             return y
 
         out_blocks = [(ki, kj, ka) for ki in K for kj in K for ka in K] if blocks is None else list(blocks)
-        r2 = torch.zeros_like(t2)
+        zero2 = torch.zeros((o, o, v, v), dtype=DT)
+        r2b = [[[zero2 for _ in K] for _ in K] for _ in K]
         for (ki, kj, ka) in out_blocks:
             kb_ = kb(ki, kj, ka)
             # (ai|bj)
             r = eri(ka, ki, kb_, kj, Vs, O, Vs, O).permute(1, 3, 0, 2).clone()
-            # A: particle-particle ladder
+            # A: particle-particle ladder, sum_cd t_ij^cd (ac|bd)
             for kc in K:
                 kd = (ki + kj - kc) % nk
-                r = r + ein("ijcd,acbd->ijab", T(ki, kj, kc), eri(ka, kc, kb_, kd, Vs, Vs, Vs, Vs))
+                r = r + (T(ki, kj, kc).reshape(o * o, v * v) @ vvvv(ka, kc, kb_, kd)).reshape(o, o, v, v)
             # B: hole-hole ladder with the quadratic tau-like piece
             for kk in K:
                 kl = (ki + kj - kk) % nk
@@ -204,9 +225,10 @@ class RCC:
                 r = r + ein("klab,kilj->ijab", T(kk, kl, ka), W)
             # C, D, E with the pair symmetrizer P_ij^ab
             r = r + sym_part(ki, kj, ka) + sym_part(kj, ki, kb_).permute(1, 0, 3, 2)
-            r2[ki, kj, ka] = r
+            r2b[ki][kj][ka] = r
+        r2 = torch.stack([torch.stack([torch.stack(r2b[ki][kj]) for kj in K]) for ki in K])
 
-        r1 = torch.zeros_like(t1)
+        r1b = [torch.zeros((o, self.v), dtype=DT) for _ in K]
         if blocks is None:
             for k in K:
                 r = ft[k][Vs, O].T.clone()
@@ -218,8 +240,8 @@ class RCC:
                     for kn in K:
                         ke = (km + kn - k) % nk
                         r = r - ein("mnae,nemi->ia", U(km, kn, k), eri(kn, ke, km, k, O, Vs, O, O))
-                r1[k] = r
-        return r1, r2
+                r1b[k] = r
+        return torch.stack(r1b), r2
 
     def energy(self, t1, t2, h=None):
         """Closed-shell supercell correlation energy (Eq. 6); divide by Nk per cell."""
@@ -229,17 +251,19 @@ class RCC:
         f = h + self._G(self.L)
         L = self.L
         e = 0.0
+        t1b = t1.unbind(0)
+        t2b = blocks_of(t2)
         for k in range(nk):
-            e = e + 2.0 * ein("ia,ia->", f[k][O, Vs], t1[k])
+            e = e + 2.0 * ein("ia,ia->", f[k][O, Vs], t1b[k])
         for ki in range(nk):
             for kj in range(nk):
                 for ka in range(nk):
                     kb = self.kb(ki, kj, ka)
                     iajb = ein("Qia,Qjb->iajb", L[ki, ka][:, O, Vs], L[kj, kb][:, O, Vs])
                     ibja = ein("Qib,Qja->iajb", L[ki, kb][:, O, Vs], L[kj, ka][:, O, Vs])
-                    tau = t2[ki, kj, ka]
+                    tau = t2b[ki][kj][ka]
                     if ka == ki:
-                        tau = tau + ein("ia,jb->ijab", t1[ki], t1[kj])
+                        tau = tau + ein("ia,jb->ijab", t1b[ki], t1b[kj])
                     e = e + ein("iajb,ijab->", 2.0 * iajb - ibja, tau)
         return e
 
@@ -332,6 +356,10 @@ class DIIS:
         for i in range(m):
             for j in range(m):
                 B[i, j] = torch.vdot(self.e[i], self.e[j])
+        # the coefficients minimise |sum c_i e_i| subject to sum c_i = 1 and do not change
+        # when the error block is scaled; scaling it to O(1) keeps the bordered system
+        # well conditioned when the errors are tiny near convergence
+        B[:m, :m] = B[:m, :m] / torch.max(torch.abs(torch.diagonal(B[:m, :m])))
         B[m, :m] = -1.0
         B[:m, m] = -1.0
         rhs = torch.zeros(m + 1, dtype=DT)
@@ -499,6 +527,20 @@ def symmetric_alpha(nk, etas, tp, tm, ftp, ftm):
         for y in range(nc):
             a = _pair(*etas[x], *tp[y]) + _pair(*etas[y], *tm[x]) + _pair(*ftm[x], *tp[y])
             b = _pair(*etas[x], *tm[y]) + _pair(*etas[y], *tp[x]) + _pair(*ftp[x], *tm[y])
+            out[x, y] = -0.5 * (a + np.conj(b)) / nk
+    return out
+
+
+def symmetric_alpha_from_scalars(nk, etas, tp, tm, Fmp):
+    """alpha_XY(w) per cell in the symmetric form of Eq. 15 from eta vectors and the scalars
+    Fmp[x][y] = F(t^x(-w), t^y(+w)) (F_dot); F is symmetric, so F(t^x(+w), t^y(-w)) =
+    Fmp[y][x].  Same formula as `polarizability`."""
+    nc = len(etas)
+    out = np.zeros((nc, nc), dtype=np.complex128)
+    for x in range(nc):
+        for y in range(nc):
+            a = _pair(*etas[x], *tp[y]) + _pair(*etas[y], *tm[x]) + complex(Fmp[x][y])
+            b = _pair(*etas[x], *tm[y]) + _pair(*etas[y], *tp[x]) + complex(Fmp[y][x])
             out[x, y] = -0.5 * (a + np.conj(b)) / nk
     return out
 

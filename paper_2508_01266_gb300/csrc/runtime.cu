@@ -860,7 +860,9 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
       // a scratch buffer starts its lifetime at zero (buffers with disjoint lifetimes share memory)
       const ZeroSpec& z = plan.zeros[op.idx];
       const size_t pitch = (size_t)std::max<long long>(stride[z.arena], z.n) * sizeof(double2);
-      if (nr == 1 || pitch <= (size_t)INT32_MAX) {
+      if (nr == 1) {
+        e = cudaMemsetAsync(ar[z.arena] + z.off, 0, (size_t)z.n * sizeof(double2), st);
+      } else if (pitch <= (size_t)INT32_MAX) {
         e = cudaMemset2DAsync(ar[z.arena] + z.off, pitch, 0, (size_t)z.n * sizeof(double2), nr, st);
       } else {  // a 2-D memset's pitch is limited to 2^31 - 1 bytes: one range per vector
         for (int r = 0; r < nr && e == cudaSuccess; ++r)

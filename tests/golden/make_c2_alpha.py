@@ -7,30 +7,31 @@ throughout.  Every value comes from oracle/rcc.py on synth/ inputs:
   * ground state: CCSD amplitudes (Eqs. 7-8) to max|Omega| <= 1e-10 and the Lambda
     multipliers (Eqs. 10-11) to max|grad L| <= 1e-10 (Jacobi + DIIS, Sec. II.D);
   * perturbed amplitudes (Eqs. 13-14) for the 15 systems (3 components x {0, +-0.05, +-0.1})
-    to a relative residual <= 1e-11;
-  * alpha from eta and F vectors (rcc.polarizability_vectors' formula, rcc.symmetric_alpha).
+    to a relative residual <= 1e-11 (rcc.solve_response);
+  * eta^X vectors (rcc.eta_vector), the quadratic-term scalars F(t^x(-w), t^y(w))
+    (rcc.F_dot), and alpha from them (rcc.symmetric_alpha_from_scalars).
 
-It takes hours of CPU time, so each stage is cached under tests/golden/cache/ (not part of
-the repository) and a rerun resumes where the last one stopped.  Besides alpha the fixture
-keeps the CCSD energy per cell and a seeded sample of T and Lambda elements in the paper's
-normalization (t2 and lambda2 carry the factor Nk; lambda as the paper's multipliers), so
-that a GPU ground state can be compared element by element.
+It takes hours of CPU time.  The independent pieces (one response system, one F scalar) run
+in a pool of worker processes (each needs about 14 GB), the memory-heavy gradient stages
+(Lambda, eta: about 55 GB) alone; every result is cached under tests/golden/cache/ (not part
+of the repository), so a rerun resumes where the last one stopped.  Besides alpha the
+fixture keeps the CCSD energy per cell and a seeded sample of T and Lambda elements in the
+paper's normalization (t2 and lambda2 carry the factor Nk; lambda as the paper's
+multipliers), so that a GPU ground state can be compared element by element.
 
-    python tests/golden/make_c2_alpha.py [threads]      # from the repository root
+    python tests/golden/make_c2_alpha.py [workers] [threads per worker]   # from the repo root
 """
 import json
+import multiprocessing as mp
 import os
 import sys
 import time
 
 import numpy as np
-import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
-
-from synth import make_problem, CONFIGS  # noqa: E402
-from oracle import rcc  # noqa: E402
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
 
 CACHE = os.path.join(HERE, "cache", "c2_seed1266")
 COMPS = (0, 1, 2)
@@ -44,8 +45,18 @@ def _path(name):
     return os.path.join(CACHE, name + ".pt")
 
 
+def tname(c, w):
+    """Cache name of the response solution of component c at frequency w (w = -0 is 0)."""
+    return f"t{c}_w{w + 0.0:+.3f}"
+
+
+def _log(msg):
+    print(f"[{time.strftime('%H:%M:%S')}] {msg}", flush=True)
+
+
 def staged(name, fn):
-    """Run fn() once and keep its result (tensors / tuples of tensors) in the cache."""
+    """Run fn() once and keep its result in the cache."""
+    import torch
     p = _path(name)
     if os.path.exists(p):
         return torch.load(p)
@@ -53,13 +64,70 @@ def staged(name, fn):
     out = fn()
     torch.save(out, p + ".tmp")
     os.replace(p + ".tmp", p)
-    print(f"[{time.strftime('%H:%M:%S')}] {name}: {time.time() - t0:.0f} s", flush=True)
+    _log(f"{name}: {time.time() - t0:.0f} s")
     return out
+
+
+_W = {}
+
+
+def _system():
+    """The problem and its oracle object (per process)."""
+    if "R" not in _W:
+        from synth import make_problem, CONFIGS
+        from oracle import rcc
+        c = CONFIGS["c2"]
+        p = make_problem(c["nk"], c["nocc"], c["nvir"], c["naux"], seed=1266)
+        _W["p"], _W["R"] = p, rcc.RCC(p)
+    return _W["p"], _W["R"]
+
+
+def _init_worker(threads):
+    import torch
+    torch.set_num_threads(threads)
+
+
+def _resp_task_iters(args):
+    """One perturbed-amplitude system, (A - w) t = -xi^X, with its iteration count."""
+    ic, w = args
+    import torch
+    from oracle import rcc
+    name = tname(COMPS[ic], w)
+    if os.path.exists(_path(name)):
+        return name
+    p, R = _system()
+    t1, t2, _ = torch.load(_path("ccsd"))
+    xi = torch.load(_path(f"xi{COMPS[ic]}"))
+
+    def run():
+        x1, x2, it = rcc.solve_response(R, t1, t2, *xi, w, RESP_TOL)
+        return x1, x2, torch.tensor(it)
+
+    staged(name, run)
+    return name
+
+
+def _F_task(args):
+    """F(t^x(-w), t^y(+w)), the quadratic term of Eq. 15 (rcc.F_dot)."""
+    x, y, w = args
+    import torch
+    from oracle import rcc
+    name = f"F{COMPS[x]}{COMPS[y]}_w{w:.3f}"
+    if os.path.exists(_path(name)):
+        return name
+    p, R = _system()
+    t1, t2, _ = torch.load(_path("ccsd"))
+    l1, l2, _ = torch.load(_path("lambda"))
+    um = torch.load(_path(tname(COMPS[x], -w)))
+    wp = torch.load(_path(tname(COMPS[y], w)))
+    staged(name, lambda: torch.tensor(complex(rcc.F_dot(R, t1, t2, l1, l2, um[0], um[1], wp[0], wp[1]))))
+    return name
 
 
 def paper_lambda(nk, l1, l2):
     """Oracle multipliers (plain pairing, supercell units) -> the paper's Lambda: the
     alpha-beta block of the spin-orbital multipliers, paper units."""
+    import torch
     sw = torch.zeros_like(l2)
     for ki in range(nk):
         for kj in range(nk):
@@ -74,51 +142,74 @@ def _cplx(z):
 
 
 def main():
-    if len(sys.argv) > 1:
-        torch.set_num_threads(int(sys.argv[1]))
+    import torch
+    from oracle import rcc
+    workers = int(sys.argv[1]) if len(sys.argv) > 1 else 3
+    wthreads = int(sys.argv[2]) if len(sys.argv) > 2 else 2
+    torch.set_num_threads(os.cpu_count() or 8)
     os.makedirs(CACHE, exist_ok=True)
-    c = CONFIGS["c2"]
-    nk, o, v, Q = c["nk"], c["nocc"], c["nvir"], c["naux"]
-    p = make_problem(nk, o, v, Q, seed=1266)
-    R = rcc.RCC(p)
+    p, R = _system()
+    nk = p.nk
     t0 = time.time()
 
     def ccsd():
-        t1, t2, it = rcc.solve_ccsd(R, tol=GS_TOL, verbose=True)
+        t1, t2, it = rcc.solve_ccsd(R, tol=GS_TOL)
         return t1, t2, torch.tensor(it)
 
     t1, t2, it_cc = staged("ccsd", ccsd)
+    mus = rcc.dipole_ops(p, COMPS)
+    for c, m in zip(COMPS, mus):
+        staged(f"xi{c}", lambda m=m: rcc.perturbation_rhs(R, t1, t2, m))
+    ctx = mp.get_context("spawn")
+    # response systems (need T only)
+    jobs = [(ic, w) for w in OMEGAS for ic in range(len(COMPS))]
+    jobs += [(ic, -w) for w in OMEGAS if w != 0 for ic in range(len(COMPS))]
+    todo = [j for j in jobs if not os.path.exists(_path(tname(COMPS[j[0]], j[1])))]
+    if todo:
+        _log(f"response systems: {len(todo)} on {workers} workers x {wthreads} threads")
+        with ctx.Pool(workers, initializer=_init_worker, initargs=(wthreads,)) as pool:
+            for name in pool.imap_unordered(_resp_task_iters, todo):
+                _log(f"done {name}")
 
     def lam():
-        l1, l2, it = rcc.solve_lambda(R, t1, t2, tol=GS_TOL, verbose=True)
+        l1, l2, it = rcc.solve_lambda(R, t1, t2, tol=GS_TOL)
         return l1, l2, torch.tensor(it)
 
     l1, l2, it_l = staged("lambda", lam)
-    mus = rcc.dipole_ops(p, COMPS)
-    xis = [staged(f"xi{c}", lambda m=m: rcc.perturbation_rhs(R, t1, t2, m)) for c, m in zip(COMPS, mus)]
     etas = [staged(f"eta{c}", lambda m=m: rcc.eta_vector(R, t1, t2, l1, l2, m)) for c, m in zip(COMPS, mus)]
-
-    iters = {}
-
-    def resp(ic, w):
-        def run():
-            x1, x2, it = rcc.solve_response(R, t1, t2, *xis[ic], w, RESP_TOL, verbose=True)
-            return x1, x2, torch.tensor(it)
-        x1, x2, it = staged(f"t{COMPS[ic]}_w{w:+.3f}", run)
-        iters[f"{COMPS[ic]},{w:+.3f}"] = int(it)
-        return x1, x2
-
-    def fvec(ic, w, x):
-        return staged(f"F{COMPS[ic]}_w{w:+.3f}", lambda: rcc.F_vector(R, t1, t2, l1, l2, *x))
-
-    alpha = []
+    nc = len(COMPS)
+    fjobs = []
     for w in OMEGAS:
-        nc = len(COMPS)
-        tp = [resp(ic, w) for ic in range(nc)]
-        tm = [resp(ic, -w) for ic in range(nc)] if w != 0 else tp
-        ftp = [fvec(ic, w, tp[ic]) for ic in range(nc)]
-        ftm = [fvec(ic, -w, tm[ic]) for ic in range(nc)] if w != 0 else ftp
-        alpha.append(rcc.symmetric_alpha(nk, etas, tp, tm, ftp, ftm))
+        for x in range(nc):
+            for y in range(nc):
+                if w == 0 and y < x:
+                    continue  # F is symmetric: F(t^x, t^y) = F(t^y, t^x) at w = 0
+                fjobs.append((x, y, w))
+    todo = [j for j in fjobs if not os.path.exists(_path(f"F{COMPS[j[0]]}{COMPS[j[1]]}_w{j[2]:.3f}"))]
+    if todo:
+        _log(f"F scalars: {len(todo)} on {workers} workers x {wthreads} threads")
+        with ctx.Pool(workers, initializer=_init_worker, initargs=(wthreads,)) as pool:
+            for name in pool.imap_unordered(_F_task, todo):
+                _log(f"done {name}")
+
+    alpha, iters = [], {}
+    for w in OMEGAS:
+        tp, tm = [], []
+        for ic in range(nc):
+            a = torch.load(_path(tname(COMPS[ic], w)))
+            b = torch.load(_path(tname(COMPS[ic], -w)))
+            tp.append(a[:2])
+            tm.append(b[:2])
+            iters[f"{COMPS[ic]},{w + 0.0:+.3f}"] = int(a[2])
+            iters[f"{COMPS[ic]},{-w + 0.0:+.3f}"] = int(b[2])
+
+        def F(x, y):
+            if w == 0 and y < x:
+                x, y = y, x
+            return complex(torch.load(_path(f"F{COMPS[x]}{COMPS[y]}_w{w:.3f}")))
+
+        Fmp = [[F(x, y) for y in range(nc)] for x in range(nc)]
+        alpha.append(rcc.symmetric_alpha_from_scalars(nk, etas, tp, tm, Fmp))
     alpha = np.asarray(alpha)
 
     # seeded sample of ground-state elements, paper normalization
@@ -137,7 +228,7 @@ def main():
         "source": "oracle/rcc.py on synth.make_problem(5, 8, 40, 160, seed=1266); written by "
                   "tests/golden/make_c2_alpha.py",
         "units": "hartree (energy), a.u. per cell (alpha); amplitudes in the paper's normalization",
-        "nk": nk, "nocc": o, "nvir": v, "naux": Q, "seed": 1266,
+        "nk": nk, "nocc": p.nocc, "nvir": p.nvir, "naux": p.naux, "seed": 1266,
         "comps": list(COMPS), "omegas": list(OMEGAS),
         "tolerances": {"ccsd_max_abs_residual": GS_TOL, "lambda_max_abs_gradient": GS_TOL,
                        "response_relative_residual": RESP_TOL},
@@ -145,13 +236,12 @@ def main():
         "energy_per_cell": _cplx(R.energy(t1, t2) / nk),
         "alpha": [[[_cplx(x) for x in row] for row in blk] for blk in alpha],
         "ground_state_sample": sample,
-        "cpu_seconds_this_run": round(time.time() - t0, 1),
-        "threads": torch.get_num_threads(),
     }
     with open(os.path.join(HERE, "oracle_c2_alpha.json"), "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")
-    print("alpha", alpha.real)
+    _log(f"alpha written ({time.time() - t0:.0f} s this run)")
+    print(alpha.real)
 
 
 if __name__ == "__main__":

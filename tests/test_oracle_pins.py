@@ -242,6 +242,14 @@ def test_vector_form_alpha_equals_fci_and_stencil_form():
         a = rcc.polarizability(R, t1, t2, l1, l2, mus, [0.0, 0.09])
         b = rcc.polarizability_vectors(R, t1, t2, l1, l2, mus, [0.0, 0.09])
         assert np.abs(a - b).max() < 1e-10 * np.abs(a).max()
+        # eta vectors with the F scalars F(t^x(-w), t^y(w))
+        etas = [rcc.eta_vector(R, t1, t2, l1, l2, m) for m in mus]
+        xis = [rcc.perturbation_rhs(R, t1, t2, m) for m in mus]
+        tp = [rcc.solve_response(R, t1, t2, *xi, 0.09)[:2] for xi in xis]
+        tm = [rcc.solve_response(R, t1, t2, *xi, -0.09)[:2] for xi in xis]
+        Fmp = [[complex(rcc.F_dot(R, t1, t2, l1, l2, *tm[x], *tp[y])) for y in range(3)] for x in range(3)]
+        c = rcc.symmetric_alpha_from_scalars(R.nk, etas, tp, tm, Fmp)
+        assert np.abs(c - a[1]).max() < 1e-10 * np.abs(a).max()
 
 
 # excitation energies (Jacobian eigenvalues) -------------------------------------
