@@ -154,6 +154,20 @@ lrcc_status lrcc_jacobian_apply_noalloc(lrcc_problem* p, int32_t transpose, cons
 lrcc_status lrcc_polarizability(lrcc_problem* p, const int32_t* comps, int32_t ncomp, const double* omegas,
                                 int32_t nomega, const lrcc_options* opt, void* alpha, int32_t* info);
 
+/* Linear-response function <<X;Y>>_w per cell (Eq. 15's response function, of which the
+ * polarizability is alpha_XY = -<<mu_X;mu_Y>>) for arbitrary one-body operators instead of
+ * the dipole components: electric dipole, quadrupole or magnetic-dipole-like operators, in
+ * any mix.  The paper computes dipole polarizabilities and names other response
+ * properties as future work (Sec. IV); the response function is the same for any
+ * Hermitian one-body perturbation h -> h + eps X (Eq. 12 with X in place of mu).
+ * ops: host c128 [nops][nk][n][n], <p|X_c|q> in the crystal-orbital basis, k-diagonal and
+ * Hermitian per k (LRCC_EINVAL otherwise, or for non-finite elements); 1 <= nops <= 16.
+ * out: host c128 [nomega][nops][nops], out[w][x][y] = <<X_x;X_y>>_w.  opt->response_form
+ * and the other options as for lrcc_polarizability; info int32 [2 + nops] likewise.
+ * Requires set_integrals and set_ground_state with Lambda.  Synchronous. */
+lrcc_status lrcc_response_function(lrcc_problem* p, int32_t nops, const void* ops, const double* omegas,
+                                   int32_t nomega, const lrcc_options* opt, void* out, int32_t* info);
+
 /* CCSD residual Omega(t) (Eqs. 7-8, paper units, layouts as for set_ground_state) for the
  * amplitudes t1, t2 (device pointers), into r1, r2 (device).  Evaluated from Jacobian
  * products: Omega(t) = Omega(0) + 1/2 [A(s1 t) t + A(s2 t) t], s1,2 = (1 -+ 1/sqrt 3)/2,
@@ -161,9 +175,13 @@ lrcc_status lrcc_polarizability(lrcc_problem* p, const int32_t* comps, int32_t n
  * problem's ground state (if set) is restored afterwards.  Synchronous. */
 lrcc_status lrcc_residual(lrcc_problem* p, const void* t1, const void* t2, void* r1, void* r2);
 
-/* Ground state on the GPU: CCSD amplitudes (Jacobi + DIIS on the residual above, until
- * max |Omega| <= opt->conv_tol) and the Lambda multipliers of Eqs. 10-11 (transpose
- * products, relative residual <= opt->conv_tol), both in FP64.  On success they become
+/* Ground state on the GPU: CCSD amplitudes (Eqs. 7-8, max |Omega| <= opt->conv_tol for the
+ * FP64 residual above) and the Lambda multipliers of Eqs. 10-11 (transpose products).
+ * opt->precision 0: Jacobi + DIIS on the FP64 residual, Lambda in FP64 to a relative
+ * residual <= opt->conv_tol.  1 (TF32) and 2 (BF16x3): inexact Newton steps for the
+ * amplitudes (FP64 residual, correction A d = -Omega solved with tensor-core products to
+ * 1e-4 relative for BF16x3, 3e-3 for TF32) and Lambda by iterative refinement to an FP64
+ * relative residual <= opt->refine_tol.  On success they become
  * the problem's ground state (as set_ground_state with Lambda) and are also copied to
  * t1, t2, l1, l2 (each may be NULL; device memory when on_device, else host) in the
  * paper's normalization.  energy (may be NULL): CCSD correlation energy per cell.

@@ -147,6 +147,21 @@ def polarizability(h, comps, omegas, options=None):
     return out, info
 
 
+def response_function(h, ops, omegas, options=None):
+    """<<X;Y>>_w per cell for one-body operators ops[c][k][p][q] (Hermitian per k):
+    returns (out[nomega][nops][nops], info)."""
+    X = np.ascontiguousarray(ops, dtype=np.complex128)
+    om = np.ascontiguousarray(omegas, dtype=np.float64)
+    nops = X.shape[0]
+    out = np.zeros((len(om), nops, nops), dtype=np.complex128)
+    info = np.zeros(2 + nops, dtype=np.int32)
+    opt = options if options is not None else default_options()
+    _check(lib.lrcc_response_function(h, nops, C.c_void_p(X.ctypes.data), om.ctypes.data_as(C.POINTER(C.c_double)),
+                                      len(om), C.byref(opt), C.c_void_p(out.ctypes.data),
+                                      info.ctypes.data_as(C.POINTER(C.c_int32))), h)
+    return out, info
+
+
 def residual(h, t1: torch.Tensor, t2: torch.Tensor):
     """CCSD residual Omega(t) (paper units) of CUDA complex128 amplitudes t1, t2."""
     t1 = _dense(t1)
@@ -226,6 +241,9 @@ class Problem:
 
     def polarizability(self, comps, omegas, options=None):
         return polarizability(self.h, comps, omegas, options)
+
+    def response_function(self, ops, omegas, options=None):
+        return response_function(self.h, ops, omegas, options)
 
     def residual(self, t1, t2):
         return residual(self.h, t1, t2)

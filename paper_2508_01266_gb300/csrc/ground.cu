@@ -8,10 +8,17 @@
 // residual costs two ground-state rebuilds at s1 t, s2 t and two Jacobian products.
 //
 // CCSD: Jacobi updates t <- t - Omega(t) / D (D from Eq. 9) with DIIS on e = t_new - t
-// (Sec. II.D), until max |Omega| <= conv_tol.
+// (Sec. II.D), until max |Omega| <= conv_tol.  In the mixed-precision modes the amplitudes
+// are found by inexact Newton steps instead: the FP64 residual Omega(t) above, then the
+// correction A(t) d = -Omega(t) solved by the same Jacobi + DIIS iteration with tensor-core
+// products (and tensor-core ground-state intermediates) to a loose relative tolerance,
+// t <- t + d.  The FP64 residual decides convergence, so the result meets the same
+// max |Omega| <= conv_tol; each step costs one FP64 residual instead of one per Jacobi
+// iteration.
 // Lambda: the stationarity conditions of E + <lam, Omega> are A^T lam = -dE/dt (plain
 // pairing, paper units; dE/dt from the tgrad program), solved with the transpose
-// products by the batched Jacobi + DIIS solver.  The result is returned in the paper's
+// products by the batched Jacobi + DIIS solver (mixed precision: its iterative refinement
+// with FP64 residuals).  The result is returned in the paper's
 // normalization (alpha-beta block of the spin-orbital multipliers):
 //   l1 = lam1 / 2,   l2 = Nk^2 (2 lam2 + lam2(a<->b)) / 3.
 #include <algorithm>
@@ -40,16 +47,17 @@ struct Ground {
     n2 = (size_t)nk * nk * nk * o * o * v * v;
   }
 
-  lrcc_status rebuild() {
+  lrcc_status rebuild(int prec = 0) {
     if (!rt.ck(cudaMemsetAsync(rt.fix + P.off_derived, 0, (P.arena_size[AR_FIX] - P.off_derived) * sizeof(double2),
                                st),
                "memset derived"))
       return LRCC_ECUDA;
     double2* ar[AR_COUNT] = {rt.fix, nullptr, nullptr, nullptr, rt.ws};
-    return rt.run(P.ground, ar, 1, st, 0);
+    return rt.run(P.ground, ar, 1, st, prec);
   }
-  // ground-state amplitudes in FIX <- s * T (T in the vector layout)
-  lrcc_status set_t(const double2* T, double s) {
+  // ground-state amplitudes in FIX <- s * T (T in the vector layout); intermediates built
+  // with the GEMM arithmetic prec
+  lrcc_status set_t(const double2* T, double s, int prec = 0) {
     if (!rt.ck(launch_axpby(make_double2(s, 0.0), T + P.off_x1, make_double2(0.0, 0.0), rt.fix + P.off_t1,
                             (long long)n1, st),
                "t1 <- s t") ||
@@ -58,7 +66,7 @@ struct Ground {
                "t2 <- s t"))
       return LRCC_ECUDA;
     rt.launches += 2;
-    return rebuild();
+    return rebuild(prec);
   }
   // OUT <- program(IN) for one vector
   lrcc_status run_prog(const Program& pr) {
@@ -152,7 +160,11 @@ lrcc_status lrcc_solve_ground_state(lrcc_problem* p, const lrcc_options* optp, v
   lrcc_options opt;
   lrcc_default_options(&opt);
   if (optp) opt = *optp;
-  opt.precision = 0;  // the ground state is solved in FP64
+  if (opt.precision < 0 || opt.precision > 2) {
+    rt.err = "solve_ground_state: precision must be 0, 1 or 2";
+    return LRCC_EINVAL;
+  }
+  const int prec = opt.precision;
   if (info) std::memset(info, 0, 4 * sizeof(int32_t));
   lrcc_status s = rt.ensure_rhs(1);
   if (s != LRCC_OK) return s;
@@ -188,7 +200,25 @@ lrcc_status lrcc_solve_ground_state(lrcc_problem* p, const lrcc_options* optp, v
   int nhist = 0, it = 0;
   bool conv = false;
   double err = 0.0;
-  for (; it < bs.maxit; ++it) {
+  for (; it < bs.maxit && prec > 0; ++it) {  // inexact Newton (mixed precision)
+    if ((s = G.residual(T, O0, bs.RES)) != LRCC_OK) return s;
+    std::vector<double> rmax;
+    if ((s = bs.maxabs(bs.RES, 1, rmax)) != LRCC_OK) return s;
+    err = rmax[0];
+    log_iteration(opt, "ccsd_newton", it, {err});
+    if (err <= opt.conv_tol) {
+      conv = true;
+      break;
+    }
+    // A(t) d = -Omega(t): tensor-core products at tensor-core intermediates of t
+    if ((s = G.set_t(T, 1.0, prec)) != LRCC_OK) return s;
+    bool iconv = false;
+    const double inner_tol = prec == 1 ? 3e-3 : 1e-4;
+    if ((s = bs.jacobi_diis(0, bs.RES, rmax, W0, prec, inner_tol, bs.maxit, iconv)) != LRCC_OK) return s;
+    CK(launch_axpby(make_double2(1.0, 0.0), rt.in, make_double2(1.0, 0.0), T, G.vec, G.st), "t += d");
+    rt.launches++;
+  }
+  for (; it < bs.maxit && prec == 0; ++it) {
     if ((s = G.residual(T, O0, bs.RES)) != LRCC_OK) return s;
     const int slot = it % depth;
     CK(cudaMemsetAsync(bs.RMAX, 0, sizeof(unsigned long long), G.st), "memset");

@@ -1281,6 +1281,40 @@ lrcc_status lrcc_polarizability(lrcc_problem* p, const int32_t* comps, int32_t n
   return lrcc_polarize_impl(p->rt, p->have_t, p->have_l, comps, ncomp, omegas, nomega, opt, alpha, info);
 }
 
+lrcc_status lrcc_response_function(lrcc_problem* p, int32_t nops, const void* ops, const double* omegas,
+                                   int32_t nomega, const lrcc_options* opt, void* out, int32_t* info) {
+  if (!p) return LRCC_EINVAL;
+  Runtime& rt = p->rt;
+  if (!ops || nops < 1 || nops > 16 || !out) return fail(p, LRCC_EINVAL, "response_function: bad arguments");
+  const int nk = rt.dims.nk, n = rt.dims.nocc + rt.dims.nvir;
+  const double2* X = (const double2*)ops;
+  const size_t per = (size_t)nk * n * n;
+  for (int c = 0; c < nops; ++c) {
+    double xmax = 0.0, herr = 0.0;
+    for (size_t i = 0; i < per; ++i) {
+      const double2 x = X[c * per + i];
+      if (!std::isfinite(x.x) || !std::isfinite(x.y))
+        return fail(p, LRCC_EINVAL, "response_function: non-finite operator matrix element");
+      xmax = std::max(xmax, std::hypot(x.x, x.y));
+    }
+    for (int k = 0; k < nk; ++k)
+      for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+          const double2 x = X[c * per + ((size_t)k * n + a) * n + b], y = X[c * per + ((size_t)k * n + b) * n + a];
+          herr = std::max(herr, std::hypot(x.x - y.x, x.y + y.y));
+        }
+    if (herr > 1e-10 * std::max(xmax, 1e-300))
+      return fail(p, LRCC_EINVAL, "response_function: operator " + std::to_string(c) + " is not Hermitian");
+  }
+  const lrcc_status s =
+      lrcc_polarize_impl(rt, p->have_t, p->have_l, nullptr, nops, omegas, nomega, opt, out, info, X);
+  if (s != LRCC_OK) return s;
+  // the driver returns alpha = -<<X;Y>>; this call returns the response function itself
+  double2* r = (double2*)out;
+  for (size_t i = 0; i < (size_t)nomega * nops * nops; ++i) r[i] = make_double2(-r[i].x, -r[i].y);
+  return LRCC_OK;
+}
+
 lrcc_status lrcc_batch_polarizability(lrcc_problem* const* probs, int32_t nprob, const int32_t* comps,
                                       int32_t ncomp, const double* omegas, int32_t nomega,
                                       const lrcc_options* opt, void* const* alphas, int32_t* const* infos) {

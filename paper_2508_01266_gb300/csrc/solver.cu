@@ -329,7 +329,7 @@ lrcc_status BatchSolver::solve(int tr, const double2* rhs, const double* om, dou
 
 lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int32_t* comps, int32_t ncomp,
                                const double* omegas, int32_t nomega, const lrcc_options* optp, void* alpha_out,
-                               int32_t* info) {
+                               int32_t* info, const double2* ops) {
   if (!have_t) {
     rt.err = "polarizability: ground state not set";
     return LRCC_EINVAL;
@@ -338,7 +338,7 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
     rt.err = "polarizability: Lambda multipliers not set";
     return LRCC_EINVAL;
   }
-  if (!comps || ncomp < 1 || ncomp > 3 || !omegas || nomega < 1 || !alpha_out) {
+  if ((!ops && (!comps || ncomp > 3)) || ncomp < 1 || ncomp > 16 || !omegas || nomega < 1 || !alpha_out) {
     rt.err = "polarizability: bad arguments";
     return LRCC_EINVAL;
   }
@@ -354,11 +354,12 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
     return LRCC_EINVAL;
   }
   const int form = opt.response_form;
-  for (int c = 0; c < ncomp; ++c)
-    if (comps[c] < 0 || comps[c] > 2) {
-      rt.err = "polarizability: component index out of range";
-      return LRCC_EINVAL;
-    }
+  if (!ops)
+    for (int c = 0; c < ncomp; ++c)
+      if (comps[c] < 0 || comps[c] > 2) {
+        rt.err = "polarizability: component index out of range";
+        return LRCC_EINVAL;
+      }
   for (int w = 0; w < nomega; ++w)
     if (!std::isfinite(omegas[w])) {
       rt.err = "polarizability: non-finite frequency";
@@ -368,12 +369,16 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
   const Plan& P = rt.plan;
   const long long vec = P.arena_size[AR_IN];
   const cudaStream_t st = 0;
+  // the one-body operator of each component: a dipole component, or the caller's matrices
+  std::vector<const double2*> opm(ncomp);
+  for (int c = 0; c < ncomp; ++c)
+    opm[c] = ops ? ops + (size_t)c * nk * n * n : rt.dip_host.data() + (size_t)comps[c] * nk * n * n;
 
   // components whose integrals vanish are skipped (Sec. II.C)
   std::vector<int> active(ncomp, 1);
   for (int c = 0; c < ncomp; ++c) {
     double m = 0.0;
-    const double2* d = rt.dip_host.data() + (size_t)comps[c] * nk * n * n;
+    const double2* d = opm[c];
     for (size_t i = 0; i < (size_t)nk * n * n; ++i) m = std::max(m, std::hypot(d[i].x, d[i].y));
     if (m < 1e-14) active[c] = 0;
   }
@@ -434,8 +439,8 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
     if (!rt.ck(cudaMemsetAsync(rt.out, 0, (size_t)vec * nrhs * sizeof(double2), st), "memset")) return LRCC_ECUDA;
     return rt.run_chunked(pr, nrhs, st, 0);
   };
-  auto set_mu = [&](int comp) -> lrcc_status {
-    const double2* d = rt.dip_host.data() + (size_t)comp * nk * n * n;
+  auto set_mu = [&](int c) -> lrcc_status {
+    const double2* d = opm[c];
     std::vector<double2> blk;
     blk.reserve((size_t)nk * (o * o + 3 * o * v + v * v));
     auto el = [&](int k, int p, int q) { return d[((size_t)k * n + p) * n + q]; };
@@ -502,7 +507,7 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
   // 1. right-hand sides -------------------------------------------------------------
   for (int c = 0; c < ncomp; ++c) {
     if (!active[c]) continue;
-    if ((s = set_mu(comps[c])) != LRCC_OK) return s;
+    if ((s = set_mu(c)) != LRCC_OK) return s;
     CK(cudaMemcpy(rt.in, TV, vec * sizeof(double2), cudaMemcpyDeviceToDevice), "t -> in");
     if ((s = run_prog(P.xi, 1)) != LRCC_OK) return s;
     for (int i = 0; i < ns; ++i)
@@ -533,7 +538,7 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
   std::vector<std::vector<cd>> etaw(ncomp, std::vector<cd>(ns, 0.0));
   for (int c = 0; c < ncomp; ++c) {
     if (!active[c]) continue;
-    if ((s = set_mu(comps[c])) != LRCC_OK) return s;
+    if ((s = set_mu(c)) != LRCC_OK) return s;
     for (int k = 0; k < 4; ++k) {
       for (int i = 0; i < ns; ++i) {
         CK(cudaMemcpy(rt.in + (size_t)i * vec, TV, vec * sizeof(double2), cudaMemcpyDeviceToDevice), "t");
@@ -627,7 +632,7 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
     std::vector<double2> fm(f0h.size());
     for (int c = 0; c < ncomp; ++c) {
       if (!active[c]) continue;
-      const double2* mu = rt.dip_host.data() + (size_t)comps[c] * nk * n * n;
+      const double2* mu = opm[c];
       double2* E = ETA + (size_t)c * vec;
       for (int sg = 1; sg >= -1; sg -= 2) {
         for (size_t i = 0; i < fm.size(); ++i)
@@ -643,7 +648,7 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
           rt.launches++;
         }
       }
-      if ((s = set_mu(comps[c])) != LRCC_OK) return s;
+      if ((s = set_mu(c)) != LRCC_OK) return s;
       CK(launch_axpby(make_double2(2.0, 0.0), rt.fix + P.off_mu + (size_t)nk * o * o, make_double2(1.0, 0.0),
                       E + P.off_x1, (long long)n1, st),
          "eta 2 mu");

@@ -5,8 +5,8 @@ inputs must have (Hermiticity, time reversal, momentum structure).  It holds non
 of the method's arithmetic, so both the oracle and the GPU path can use it
 without sharing any computation.
 """
-from .gen import (Problem, make_problem, kmesh_neg, pair_index, random_amplitudes,
+from .gen import (Problem, make_problem, make_operator, kmesh_neg, pair_index, random_amplitudes,
                   random_probe, CONFIGS)
 
-__all__ = ["Problem", "make_problem", "kmesh_neg", "pair_index", "random_amplitudes",
+__all__ = ["Problem", "make_problem", "make_operator", "kmesh_neg", "pair_index", "random_amplitudes",
            "random_probe", "CONFIGS"]

@@ -199,6 +199,36 @@ def make_problem(nk: int, nocc: int, nvir: int, naux: int, seed: int = 1266, *,
                    dict(seed=seed, kind=kind, sigma_l=sigma_l, sigma_mu=sigma_mu, tr=tr))
 
 
+def make_operator(nk: int, n: int, seed: int, parity: int = 1, sigma: float = 0.5, kmesh: int = 0) -> np.ndarray:
+    """A k-diagonal one-body operator X[k, p, q], Hermitian per k, with time-reversal parity
+    X(-k) = parity * conj(X(k)): +1 for electric-multipole-like operators (dipole, quadrupole;
+    real symmetric at self-conjugate k), -1 for magnetic-dipole-like ones (purely imaginary
+    at self-conjugate k)."""
+    if parity not in (1, -1):
+        raise ValueError("parity must be +1 or -1")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    neg = kmesh_neg(nk, kmesh)
+    X = np.zeros((nk, n, n), dtype=np.complex128)
+    done = np.zeros(nk, dtype=bool)
+    for k in range(nk):
+        if done[k]:
+            continue
+        if neg[k] == k:  # X = parity conj(X) and Hermitian: real symmetric or imaginary antisymmetric
+            if parity == 1:
+                blk = _hermitian_block(rng, 1, n, sigma, real=True)[0]
+            else:
+                a = rng.normal(0.0, sigma, (n, n))
+                blk = 1j * (a - a.T) / np.sqrt(2.0)
+        else:
+            blk = _hermitian_block(rng, 1, n, sigma, real=False)[0]
+        X[k] = blk
+        done[k] = True
+        if neg[k] != k:
+            X[neg[k]] = parity * np.conj(blk)
+            done[neg[k]] = True
+    return X
+
+
 def symmetrize_pairs(t2: np.ndarray) -> np.ndarray:
     """Impose t2[ki,kj,ka,i,j,a,b] = t2[kj,ki,kb,j,i,b,a] by averaging."""
     nk = t2.shape[0]

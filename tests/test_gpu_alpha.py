@@ -162,3 +162,55 @@ def test_alpha_host_history_and_chunks_bitwise(lr):
     prob.close()
     assert info[1] == 0
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("form", [0, 2])
+def test_response_function_general_operators(lr, form):
+    """lrcc_response_function with operators other than the dipole (a magnetic-dipole-like
+    time-reversal-odd operator, a quadrupole-like even one, a dipole component) against the
+    oracle's response function <<X;Y>> = -alpha_XY, symmetric (form 0) and asymmetric
+    (form 2) forms, X != Y included; non-TR data so that every element is non-trivial."""
+    from synth import make_operator
+    p = make_problem(2, 2, 3, 4, seed=8, sigma_l=0.15, tr=False)
+    nk, o, v, Q = p.nk, p.nocc, p.nvir, p.naux
+    n = o + v
+    ops = np.stack([make_operator(nk, n, seed=301, parity=-1), make_operator(nk, n, seed=302, parity=1),
+                    p.dip[0]])
+    R = rcc.RCC(p)
+    t1, t2, _ = rcc.solve_ccsd(R, tol=1e-11)
+    l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=1e-11)
+    mus = [torch.as_tensor(X) for X in ops]
+    om = [0.0, 0.06]
+    if form == 0:
+        ref = -rcc.polarizability(R, t1, t2, l1, l2, mus, om, tol=1e-11)
+    else:
+        ref = -rcc.polarizability_left(R, t1, t2, l1, l2, mus, om, tol=1e-11)[1]
+    pl1, pl2 = paper_lambda(nk, l1, l2)
+    prob = lr.Problem(nk, o, v, Q)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    prob.set_ground_state(t1, t2 * nk, pl1, pl2)
+    got, info = prob.response_function(ops, om, lr.default_options(conv_tol=1e-11, max_iter=300,
+                                                                    response_form=form))
+    prob.close()
+    assert info[1] == 0
+    rel = np.abs(got - ref).max() / np.abs(ref).max()
+    print(f"form {form}: <<X;Y>> rel err {rel:.2e}; odd-even element {got[1, 0, 1]}")
+    assert rel < 1e-8
+    assert np.abs(got[1, 0, 1]) > 1e-3 * np.abs(got).max()  # X != Y coupling present
+
+
+def test_response_function_rejects_non_hermitian(lr):
+    p = make_problem(1, 1, 2, 3, seed=9, sigma_l=0.1)
+    R = rcc.RCC(p)
+    t1, t2, _ = rcc.solve_ccsd(R, tol=1e-10)
+    l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=1e-10)
+    pl1, pl2 = paper_lambda(1, l1, l2)
+    prob = lr.Problem(1, 1, 2, 3)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    prob.set_ground_state(t1, t2, pl1, pl2)
+    bad = np.zeros((1, 1, 3, 3), dtype=np.complex128)
+    bad[0, 0, 0, 1] = 1.0
+    with pytest.raises(lr.LrccError) as e:
+        prob.response_function(bad, [0.0])
+    assert "not Hermitian" in str(e.value)
+    prob.close()

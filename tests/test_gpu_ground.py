@@ -79,3 +79,53 @@ def test_alpha_c1_from_gpu_ground_state(lr):
     print("C1 alpha_zz from GPU ground state", got.ravel(), "oracle", ref.ravel(), "rel", rel)
     assert rel < 1e-8
     prob.close()
+
+
+@pytest.mark.parametrize("prec", [2, 1])
+def test_mixed_precision_ground_state_vs_oracle(lr, prec):
+    """Tensor-core inner solves (inexact Newton for T, iterative refinement for Lambda) reach
+    the oracle's ground state to the FP64 tolerances given: the FP64 residual decides."""
+    from test_gpu_alpha import paper_lambda
+    nk, o, v, Q = 3, 2, 5, 8
+    p = make_problem(nk, o, v, Q, seed=73, sigma_l=0.15)
+    R = rcc.RCC(p)
+    t1, t2, _ = rcc.solve_ccsd(R, tol=1e-12)
+    l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=1e-12)
+    pl1, pl2 = paper_lambda(nk, l1, l2)
+    e_ref = complex(R.energy(t1, t2)) / nk
+    prob = lr.Problem(nk, o, v, Q)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    g1, g2, h1, h2, e, info = prob.solve_ground_state(
+        lr.default_options(precision=prec, conv_tol=1e-11, refine_tol=1e-11, max_iter=300))
+    print(f"precision {prec}: Newton steps {info[0]}, Lambda iterations {info[2]}")
+    assert info[1] == 0 and info[3] == 0
+    assert info[0] <= 8
+    assert _rel(g1.cpu().numpy(), t1.numpy()) < 1e-8
+    assert _rel(g2.cpu().numpy(), nk * t2.numpy()) < 1e-8
+    assert _rel(h1.cpu().numpy(), pl1.numpy()) < 1e-8
+    assert _rel(h2.cpu().numpy(), pl2.numpy()) < 1e-8
+    assert abs(e - e_ref.real) < 1e-10 * abs(e_ref)
+    prob.close()
+
+
+def test_alpha_c1_mixed_end_to_end(lr):
+    """C1 workload, everything in BF16x3 with FP64 refinement (ground state and alpha):
+    alpha_zz(0, 0.1) within 1e-5 a.u. of the oracle."""
+    c = CONFIGS["c1"]
+    nk, o, v, Q = c["nk"], c["nocc"], c["nvir"], c["naux"]
+    p = make_problem(nk, o, v, Q, seed=1266)
+    R = rcc.RCC(p)
+    t1, t2, _ = rcc.solve_ccsd(R, tol=1e-10)
+    l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=1e-10)
+    ref = rcc.polarizability(R, t1, t2, l1, l2, rcc.dipole_ops(p, [2]), [0.0, 0.1], tol=1e-11)
+    prob = lr.Problem(nk, o, v, Q)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    opts = lr.default_options(precision=2, conv_tol=1e-9, refine_tol=1e-8, max_iter=300)
+    *_, e, info = prob.solve_ground_state(opts)
+    assert info[1] == 0 and info[3] == 0
+    got, info = prob.polarizability([2], [0.0, 0.1], opts)
+    assert info[1] == 0
+    err = np.abs(got - ref).max()
+    print("C1 alpha_zz, BF16x3 end to end", got.ravel(), "oracle", ref.ravel(), "|err|", err)
+    assert err <= 1e-5
+    prob.close()

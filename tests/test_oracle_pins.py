@@ -252,6 +252,34 @@ def test_vector_form_alpha_equals_fci_and_stencil_form():
         assert np.abs(c - a[1]).max() < 1e-10 * np.abs(a).max()
 
 
+@pytest.mark.parametrize("tr", [True, False])
+def test_mixed_operator_response_equals_fci_two_electrons(tr):
+    """Response functions between different one-body operators (a magnetic-dipole-like
+    time-reversal-odd operator, a quadrupole-like even one and a dipole component): the
+    symmetric form of Eq. 15 and the asymmetric (left-response) form with arbitrary
+    Hermitian operators both equal the FCI sum over states for two electrons."""
+    from synth import make_operator
+    p = make_problem(1, 1, 3, 4, seed=61, sigma_l=0.15, tr=tr)
+    R = rcc.RCC(p)
+    S = spinorb.SpinOrbitalSystem(p)
+    t1, t2, _ = rcc.solve_ccsd(R, tol=1e-12)
+    l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=1e-12)
+    ops = [make_operator(1, 4, seed=201, parity=-1), make_operator(1, 4, seed=202, parity=1), p.dip[2]]
+    assert np.abs(ops[0].real).max() == 0.0 and np.abs(ops[1].imag).max() == 0.0
+    mus = [T(X) for X in ops]
+    for w in (0.0, 0.07):
+        _, a_fci = fci.sos_polarizability(S, [spinorb.one_body_to_spinorb(S, X) for X in ops], w)
+        a_cc = rcc.polarizability(R, t1, t2, l1, l2, mus, [w])[0]
+        assert np.abs(a_cc - a_fci).max() < 1e-9 * np.abs(a_fci).max()
+        _, a_left = rcc.polarizability_left(R, t1, t2, l1, l2, mus, [w])
+        assert np.abs(a_left[0] - a_fci).max() < 1e-9 * np.abs(a_fci).max()
+    # the odd-even response is imaginary, antisymmetric and vanishes in the static limit
+    # under time reversal; a sanity check that the operators are what they claim to be
+    if tr:
+        _, a0 = fci.sos_polarizability(S, [spinorb.one_body_to_spinorb(S, X) for X in ops[:2]], 0.0)
+        assert abs(a0[0, 1]) < 1e-12 * np.abs(a0).max()
+
+
 # excitation energies (Jacobian eigenvalues) -------------------------------------
 @pytest.mark.parametrize("tr", [True, False])
 def test_excitation_energies_are_fci_two_electrons(tr):
