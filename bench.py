@@ -353,7 +353,7 @@ def extra_workload(lr, name, steps, dist, rank):
     from synth import make_problem, random_amplitudes, random_probe
     cfg, comps, omegas, nsys = workload(name)
     nk, o, v, Q = cfg["nk"], cfg["nocc"], cfg["nvir"], cfg["naux"]
-    nrhs = {"c4": 1, "c5": 4}.get(name, nsys)
+    nrhs = {"c3": 18, "c4": 1, "c5": 4}.get(name, nsys)  # c3: 3 components x 6 frequencies
     t0 = time.perf_counter()
     p = make_problem(nk, o, v, Q, seed=1266)
     t1, t2 = random_amplitudes(nk, o, v, seed=1267, scale1=0.01, scale2=0.01)
@@ -376,6 +376,61 @@ def extra_workload(lr, name, steps, dist, rank):
     torch.cuda.empty_cache()
     return {"workload": f"{name}: Nk={nk} nocc={o} nvir={v} naux={Q}", "rhs_per_step": nrhs, "bf16x3": m,
             "setup_seconds": setup}
+
+
+# alpha(w) runs at full size (one JSON line each): components, frequencies (Ha), whether both
+# forms of the response function are computed (the left-response workload)
+ALPHA_RUNS = {
+    "c2": ([0, 1, 2], [0.0, 0.05, 0.1], False),
+    "c3": ([0, 1, 2], [0.0, 0.03, 0.06, 0.09, 0.12, 0.15], False),
+    "c5": ([0, 2], [0.0, 0.05, 0.1], True),
+    "c4": ([0, 2], [0.0, 0.05, 0.1, 0.15], False),
+}
+
+
+def alpha_run(lr, name, prec, refine_tol=1e-7):
+    """Integrals in, ground state (T, Lambda) and alpha out, everything on the GPU: the
+    ground state in the same precision mode (FP64 residuals decide its convergence), the
+    perturbed-amplitude systems of all components and +-w solved as one batch."""
+    import numpy as np
+    from synth import make_problem, CONFIGS
+    comps, omegas, forms = ALPHA_RUNS[name]
+    c = CONFIGS[name]
+    nk, o, v, Q = c["nk"], c["nocc"], c["nvir"], c["naux"]
+    p = make_problem(nk, o, v, Q, seed=1266)
+    t0 = time.perf_counter()
+    prob = lr.Problem(nk, o, v, Q)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    del p
+    gopt = lr.default_options(precision=prec, conv_tol=1e-9, refine_tol=1e-9, max_iter=300)
+    *_, e, ginfo = prob.solve_ground_state(gopt)
+    t1 = time.perf_counter()
+    aopt = lr.default_options(precision=prec, conv_tol=1e-10, refine_tol=refine_tol, max_iter=300)
+    if forms:
+        a, asym, info = prob.polarizability_forms(comps, omegas, aopt)
+    else:
+        a, info = prob.polarizability(comps, omegas, aopt)
+        asym = None
+    t2 = time.perf_counter()
+    launches = prob.kernel_launches
+    prob.close()
+    out = {"alpha_run": name, "workload": f"{name}: Nk={nk} nocc={o} nvir={v} naux={Q}", "precision":
+           {0: "fp64", 1: "tf32", 2: "bf16x3"}[prec], "comps": comps, "omegas": omegas,
+           "systems": sum(len(comps) * (1 if w == 0 else 2) for w in omegas),
+           "ground_state": {"seconds": t1 - t0, "energy_per_cell": e, "newton_or_jacobi_steps": int(ginfo[0]),
+                            "lambda_iterations": int(ginfo[2]), "conv_tol": 1e-9},
+           "alpha_seconds": t2 - t1, "iterations": int(info[0]), "status": int(info[1]),
+           "refine_tol": refine_tol if prec else None,
+           "alpha_real": np.round(a.real, 9).tolist(),
+           "max_abs_imag": float(np.abs(a.imag).max()),
+           "max_abs_asymmetry": float(np.abs(a - a.transpose(0, 2, 1)).max()),
+           "gpu_launches": int(launches)}
+    if asym is not None:
+        sym_asym = 0.5 * (asym + asym.transpose(0, 2, 1))
+        out["left_response"] = {"alpha_symmetrised_real": np.round(sym_asym.real, 9).tolist(),
+                                "max_abs_diff_symmetrised_vs_symmetric_form": float(np.abs(sym_asym - a).max()),
+                                "max_rel_diff": float(np.abs(sym_asym - a).max() / np.abs(a).max())}
+    return out
 
 
 def dry_run(args):
@@ -418,6 +473,9 @@ def main():
     ap.add_argument("--shape", default="",
                     help="Nk,nocc,nvir,naux overriding the workload's sizes (small cases for ncu captures)")
     ap.add_argument("--dry-run", action="store_true", help="rank setup only, no GPU (CPU tests)")
+    ap.add_argument("--alpha", default="", help="run alpha(w) end to end at a workload (c2, c3, c5, c4) and print "
+                                                 "one JSON line instead of the product benchmark")
+    ap.add_argument("--alpha-precision", type=int, default=2, help="0 FP64, 1 TF32, 2 BF16x3")
     args = ap.parse_args()
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         spawn_replicas(args.gpus, sys.argv[1:])
@@ -440,6 +498,11 @@ def main():
         dist.barrier()
     import paper_2508_01266_gb300 as lr
     from synth import make_problem, random_amplitudes, random_probe
+
+    if args.alpha:
+        if rank == 0:
+            print(json.dumps(alpha_run(lr, args.alpha, args.alpha_precision)), flush=True)
+        return
 
     cfg, comps, omegas, nsys = workload(args.config)
     if args.shape:

@@ -154,6 +154,16 @@ lrcc_status lrcc_jacobian_apply_noalloc(lrcc_problem* p, int32_t transpose, cons
 lrcc_status lrcc_polarizability(lrcc_problem* p, const int32_t* comps, int32_t ncomp, const double* omegas,
                                 int32_t nomega, const lrcc_options* opt, void* alpha, int32_t* info);
 
+/* Both forms of the polarizability of lrcc_polarizability from one set of right-hand
+ * solutions: alpha_sym receives the symmetric form (response_form 0) and alpha_asym the
+ * asymmetric (left-response) form as computed (response_form 2), each c128
+ * [nomega][ncomp][ncomp] in host memory; they agree at convergence (Eq. 15 read through
+ * the paper's linear-response reference), so their difference measures the solution
+ * error.  opt->response_form is ignored; everything else as for lrcc_polarizability. */
+lrcc_status lrcc_polarizability_forms(lrcc_problem* p, const int32_t* comps, int32_t ncomp, const double* omegas,
+                                      int32_t nomega, const lrcc_options* opt, void* alpha_sym, void* alpha_asym,
+                                      int32_t* info);
+
 /* Linear-response function <<X;Y>>_w per cell (Eq. 15's response function, of which the
  * polarizability is alpha_XY = -<<mu_X;mu_Y>>) for arbitrary one-body operators instead of
  * the dipole components: electric dipole, quadrupole or magnetic-dipole-like operators, in

@@ -147,6 +147,21 @@ def polarizability(h, comps, omegas, options=None):
     return out, info
 
 
+def polarizability_forms(h, comps, omegas, options=None):
+    """Symmetric and asymmetric (left-response) alpha from one solve: (sym, asym, info)."""
+    comps = np.ascontiguousarray(comps, dtype=np.int32)
+    om = np.ascontiguousarray(omegas, dtype=np.float64)
+    sym = np.zeros((len(om), len(comps), len(comps)), dtype=np.complex128)
+    asym = np.zeros_like(sym)
+    info = np.zeros(2 + len(comps), dtype=np.int32)
+    opt = options if options is not None else default_options()
+    _check(lib.lrcc_polarizability_forms(h, comps.ctypes.data_as(C.POINTER(C.c_int32)), len(comps),
+                                         om.ctypes.data_as(C.POINTER(C.c_double)), len(om), C.byref(opt),
+                                         C.c_void_p(sym.ctypes.data), C.c_void_p(asym.ctypes.data),
+                                         info.ctypes.data_as(C.POINTER(C.c_int32))), h)
+    return sym, asym, info
+
+
 def response_function(h, ops, omegas, options=None):
     """<<X;Y>>_w per cell for one-body operators ops[c][k][p][q] (Hermitian per k):
     returns (out[nomega][nops][nops], info)."""
@@ -241,6 +256,9 @@ class Problem:
 
     def polarizability(self, comps, omegas, options=None):
         return polarizability(self.h, comps, omegas, options)
+
+    def polarizability_forms(self, comps, omegas, options=None):
+        return polarizability_forms(self.h, comps, omegas, options)
 
     def response_function(self, ops, omegas, options=None):
         return response_function(self.h, ops, omegas, options)

@@ -40,6 +40,8 @@ _SIGS = {
     "lrcc_jacobian_apply_noalloc": (C.c_int, [VP, C.c_int32, VP, VP, VP, VP, VP]),
     "lrcc_polarizability": (C.c_int, [VP, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_double), C.c_int32,
                                       C.POINTER(lrcc_options), VP, C.POINTER(C.c_int32)]),
+    "lrcc_polarizability_forms": (C.c_int, [VP, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_double),
+                                            C.c_int32, C.POINTER(lrcc_options), VP, VP, C.POINTER(C.c_int32)]),
     "lrcc_response_function": (C.c_int, [VP, C.c_int32, VP, C.POINTER(C.c_double), C.c_int32,
                                          C.POINTER(lrcc_options), VP, C.POINTER(C.c_int32)]),
     "lrcc_last_error": (C.c_char_p, [VP]),

@@ -1281,6 +1281,19 @@ lrcc_status lrcc_polarizability(lrcc_problem* p, const int32_t* comps, int32_t n
   return lrcc_polarize_impl(p->rt, p->have_t, p->have_l, comps, ncomp, omegas, nomega, opt, alpha, info);
 }
 
+lrcc_status lrcc_polarizability_forms(lrcc_problem* p, const int32_t* comps, int32_t ncomp, const double* omegas,
+                                      int32_t nomega, const lrcc_options* opt, void* alpha_sym, void* alpha_asym,
+                                      int32_t* info) {
+  if (!p) return LRCC_EINVAL;
+  if (!alpha_sym || !alpha_asym) return fail(p, LRCC_EINVAL, "polarizability_forms: null output");
+  lrcc_options o;
+  lrcc_default_options(&o);
+  if (opt) o = *opt;
+  o.response_form = 2;
+  return lrcc_polarize_impl(p->rt, p->have_t, p->have_l, comps, ncomp, omegas, nomega, &o, alpha_asym, info, nullptr,
+                            alpha_sym);
+}
+
 lrcc_status lrcc_response_function(lrcc_problem* p, int32_t nops, const void* ops, const double* omegas,
                                    int32_t nomega, const lrcc_options* opt, void* out, int32_t* info) {
   if (!p) return LRCC_EINVAL;

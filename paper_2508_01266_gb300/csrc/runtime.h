@@ -129,7 +129,8 @@ struct lrcc_problem {
 
 // Polarizability driver (solver.cu).
 // ops (optional): host c128 [ncomp][nk][n][n] one-body operators used instead of the dipole
-// components comps (then up to 16 of them).
+// components comps (then up to 16 of them).  alpha_sym (optional, asymmetric forms only):
+// receives the symmetric form from the same right-hand solutions.
 lrcc_status lrcc_polarize_impl(lrcc::Runtime& rt, bool have_t, bool have_l, const int32_t* comps, int32_t ncomp,
                                const double* omegas, int32_t nomega, const lrcc_options* opt, void* alpha,
-                               int32_t* info, const double2* ops = nullptr);
+                               int32_t* info, const double2* ops = nullptr, void* alpha_sym = nullptr);

@@ -283,29 +283,41 @@ lrcc_status BatchSolver::solve(int tr, const double2* rhs, const double* om, dou
       return LRCC_ECUDA;
     return LRCC_OK;
   }
-  if (!rt.ck(launch_guess(rhs, DEN, om, sol, vec, vec, ns, st), "guess")) return LRCC_ECUDA;
-  rt.launches++;
+  // refinement starts from x = 0, whose residual is the right-hand side itself: the first
+  // inner solve needs no FP64 product (the inner solver makes its own Jacobi guess)
+  if (!rt.ck(cudaMemsetAsync(sol, 0, (size_t)ns * vec * sizeof(double2), st), "sol = 0")) return LRCC_ECUDA;
   const double tol64 = std::min(opt.refine_tol, 1e-3);
   const double inner_tol = prec == 1 ? 3e-3 : 1e-4;
   for (int outer = 0; outer < 40 && !converged; ++outer) {
-    if (!rt.ck(cudaMemcpy(X, sol, (size_t)ns * vec * sizeof(double2), cudaMemcpyDeviceToDevice), "x -> in"))
-      return LRCC_ECUDA;
-    if ((s2 = rt.apply(tr, ns, st, 0, opt.use_graphs != 0, opt.autotune != 0)) != LRCC_OK) return s2;
-    ++total_it;
-    // R = rhs + A x - w x = -r ; its max is the FP64 residual
-    if (!rt.ck(cudaMemsetAsync(RMAX, 0, ns * sizeof(unsigned long long), st), "memset") ||
-        !rt.ck(launch_residual(X, Y, rhs, om, RES, RMAX, vec, vec, ns, st), "residual"))
-      return LRCC_ECUDA;
-    rt.launches++;
-    std::vector<unsigned long long> hr(ns);
-    if (!rt.ck(cudaMemcpy(hr.data(), RMAX, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "rmax"))
-      return LRCC_ECUDA;
-    double worst = 0.0;
     std::vector<double> rmx(ns);
-    for (int i = 0; i < ns; ++i) {
-      rmx[i] = u64_to_double(hr[i]);
-      rel[i] = rmx[i] / std::max(rhsmax[i], 1e-300);
-      worst = std::max(worst, rel[i]);
+    double worst = 0.0;
+    if (outer == 0) {
+      if (!rt.ck(cudaMemcpyAsync(RES, rhs, (size_t)ns * vec * sizeof(double2), cudaMemcpyDeviceToDevice, st),
+                 "R = rhs"))
+        return LRCC_ECUDA;
+      for (int i = 0; i < ns; ++i) {
+        rmx[i] = rhsmax[i];
+        rel[i] = rhsmax[i] > 0 ? 1.0 : 0.0;
+        worst = std::max(worst, rel[i]);
+      }
+    } else {
+      if (!rt.ck(cudaMemcpy(X, sol, (size_t)ns * vec * sizeof(double2), cudaMemcpyDeviceToDevice), "x -> in"))
+        return LRCC_ECUDA;
+      if ((s2 = rt.apply(tr, ns, st, 0, opt.use_graphs != 0, opt.autotune != 0)) != LRCC_OK) return s2;
+      ++total_it;
+      // R = rhs + A x - w x = -r ; its max is the FP64 residual
+      if (!rt.ck(cudaMemsetAsync(RMAX, 0, ns * sizeof(unsigned long long), st), "memset") ||
+          !rt.ck(launch_residual(X, Y, rhs, om, RES, RMAX, vec, vec, ns, st), "residual"))
+        return LRCC_ECUDA;
+      rt.launches++;
+      std::vector<unsigned long long> hr(ns);
+      if (!rt.ck(cudaMemcpy(hr.data(), RMAX, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "rmax"))
+        return LRCC_ECUDA;
+      for (int i = 0; i < ns; ++i) {
+        rmx[i] = u64_to_double(hr[i]);
+        rel[i] = rmx[i] / std::max(rhsmax[i], 1e-300);
+        worst = std::max(worst, rel[i]);
+      }
     }
     log_iteration(opt, tr ? "refinement_transpose" : "refinement", outer, rel);
     if (worst <= tol64) {
@@ -329,7 +341,7 @@ lrcc_status BatchSolver::solve(int tr, const double2* rhs, const double* om, dou
 
 lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int32_t* comps, int32_t ncomp,
                                const double* omegas, int32_t nomega, const lrcc_options* optp, void* alpha_out,
-                               int32_t* info, const double2* ops) {
+                               int32_t* info, const double2* ops, void* alpha_sym_out) {
   if (!have_t) {
     rt.err = "polarizability: ground state not set";
     return LRCC_EINVAL;
@@ -608,7 +620,8 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
   CK(cudaDeviceSynchronize(), "solver sync");
 
   // 3c. response function ------------------------------------------------------------------
-  if (form == 0) {
+  if (form == 0 || alpha_sym_out) {
+    cd* alpha_sym = form == 0 ? alpha : (cd*)alpha_sym_out;
     for (int iw = 0; iw < nomega; ++iw)
       for (int x = 0; x < ncomp; ++x)
         for (int y = 0; y < ncomp; ++y) {
@@ -618,9 +631,9 @@ lrcc_status lrcc_polarize_impl(Runtime& rt, bool have_t, bool have_l, const int3
           const cd a = etaw[x][yp] + etaw[y][xm] + F[(size_t)xm * ns + yp];
           const cd b = etaw[x][ym] + etaw[y][xp] + F[(size_t)xp * ns + ym];
           const cd lr = 0.5 * (a + std::conj(b));
-          alpha[((size_t)iw * ncomp + x) * ncomp + y] = -lr / (double)nk;
+          alpha_sym[((size_t)iw * ncomp + x) * ncomp + y] = -lr / (double)nk;
         }
-    return LRCC_OK;
+    if (form == 0) return LRCC_OK;
   }
 
   // 4. asymmetric (left-response) form -------------------------------------------------------

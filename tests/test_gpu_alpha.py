@@ -214,3 +214,27 @@ def test_response_function_rejects_non_hermitian(lr):
         prob.response_function(bad, [0.0])
     assert "not Hermitian" in str(e.value)
     prob.close()
+
+
+def test_polarizability_both_forms_from_one_solve(lr):
+    """lrcc_polarizability_forms: the symmetric and the asymmetric form from one set of
+    right-hand solutions, each against the oracle's, non-TR data."""
+    p = make_problem(2, 2, 3, 4, seed=7, sigma_l=0.15, tr=False)
+    nk, o, v, Q = p.nk, p.nocc, p.nvir, p.naux
+    R = rcc.RCC(p)
+    t1, t2, _ = rcc.solve_ccsd(R, tol=1e-11)
+    l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=1e-11)
+    mus = rcc.dipole_ops(p, [0, 2])
+    om = [0.0, 0.08]
+    ref_sym = rcc.polarizability(R, t1, t2, l1, l2, mus, om, tol=1e-11)
+    ref_asym = rcc.polarizability_left(R, t1, t2, l1, l2, mus, om, tol=1e-11)[1]
+    pl1, pl2 = paper_lambda(nk, l1, l2)
+    prob = lr.Problem(nk, o, v, Q)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    prob.set_ground_state(t1, t2 * nk, pl1, pl2)
+    sym, asym, info = prob.polarizability_forms([0, 2], om, lr.default_options(conv_tol=1e-11, max_iter=300))
+    prob.close()
+    assert info[1] == 0
+    assert np.abs(sym - ref_sym).max() < 1e-8 * np.abs(ref_sym).max()
+    assert np.abs(asym - ref_asym).max() < 1e-8 * np.abs(ref_asym).max()
+    assert np.abs(asym - asym.transpose(0, 2, 1)).max() > 1e-6 * np.abs(asym).max()  # forms differ element-wise
