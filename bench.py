@@ -406,11 +406,35 @@ def alpha_run(lr, name, prec, refine_tol=1e-7):
     *_, e, ginfo = prob.solve_ground_state(gopt)
     t1 = time.perf_counter()
     aopt = lr.default_options(precision=prec, conv_tol=1e-10, refine_tol=refine_tol, max_iter=300)
-    if forms:
-        a, asym, info = prob.polarizability_forms(comps, omegas, aopt)
-    else:
-        a, info = prob.polarizability(comps, omegas, aopt)
-        asym = None
+    # alpha at one frequency needs only that frequency's (component, +-w) systems; each system
+    # holds about 22 vectors in the solver (8-deep DIIS history of iterates and errors, right-hand
+    # side, solution, F vector, residual, product input and output; 25 with the left solves), so
+    # the frequencies are solved in as few groups as device memory allows
+    import torch
+    vec_gb = 16.0 * (nk * o * v + nk ** 3 * o * o * v * v) / 1e9
+    per_sys = (25 if forms else 22) * vec_gb
+    budget = 0.5 * torch.cuda.get_device_properties(torch.cuda.current_device()).total_memory / 1e9
+    groups, cur, cur_n = [], [], 0
+    for w in omegas:
+        ns = len(comps) * (1 if w == 0 else 2)
+        if cur and (cur_n + ns) * per_sys > budget:
+            groups.append(cur)
+            cur, cur_n = [], 0
+        cur.append(w)
+        cur_n += ns
+    groups.append(cur)
+    a_parts, s_parts, iters, status = [], [], 0, 0
+    for grp in groups:
+        if forms:
+            ag, sg, info = prob.polarizability_forms(comps, grp, aopt)
+            s_parts.append(sg)
+        else:
+            ag, info = prob.polarizability(comps, grp, aopt)
+        a_parts.append(ag)
+        iters += int(info[0])
+        status = status or int(info[1])
+    a = np.concatenate(a_parts)
+    asym = np.concatenate(s_parts) if forms else None
     t2 = time.perf_counter()
     launches = prob.kernel_launches
     prob.close()
@@ -419,7 +443,8 @@ def alpha_run(lr, name, prec, refine_tol=1e-7):
            "systems": sum(len(comps) * (1 if w == 0 else 2) for w in omegas),
            "ground_state": {"seconds": t1 - t0, "energy_per_cell": e, "newton_or_jacobi_steps": int(ginfo[0]),
                             "lambda_iterations": int(ginfo[2]), "conv_tol": 1e-9},
-           "alpha_seconds": t2 - t1, "iterations": int(info[0]), "status": int(info[1]),
+           "alpha_seconds": t2 - t1, "iterations": iters, "status": status,
+           "frequency_groups": groups,
            "refine_tol": refine_tol if prec else None,
            "alpha_real": np.round(a.real, 9).tolist(),
            "max_abs_imag": float(np.abs(a.imag).max()),
@@ -476,6 +501,12 @@ def main():
     ap.add_argument("--alpha", default="", help="run alpha(w) end to end at a workload (c2, c3, c5, c4) and print "
                                                  "one JSON line instead of the product benchmark")
     ap.add_argument("--alpha-precision", type=int, default=2, help="0 FP64, 1 TF32, 2 BF16x3")
+    ap.add_argument("--alpha-comps", default="", help="override the alpha run's components (e.g. 2)")
+    ap.add_argument("--alpha-omegas", default="", help="override the alpha run's frequencies (e.g. 0.0)")
+    ap.add_argument("--report", type=int, default=-1,
+                    help="print the per-op CUDA-event report of one product in this precision (0, 1, 2) "
+                         "over the step's vectors and exit (profiling runs)")
+    ap.add_argument("--transpose", action="store_true", help="--report: the transposed product")
     args = ap.parse_args()
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         spawn_replicas(args.gpus, sys.argv[1:])
@@ -500,6 +531,11 @@ def main():
     from synth import make_problem, random_amplitudes, random_probe
 
     if args.alpha:
+        if args.alpha_comps or args.alpha_omegas:
+            comps0, omegas0, forms0 = ALPHA_RUNS[args.alpha]
+            ALPHA_RUNS[args.alpha] = ([int(x) for x in args.alpha_comps.split(",")] if args.alpha_comps else comps0,
+                                      [float(x) for x in args.alpha_omegas.split(",")] if args.alpha_omegas
+                                      else omegas0, forms0)
         if rank == 0:
             print(json.dumps(alpha_run(lr, args.alpha, args.alpha_precision)), flush=True)
         return
@@ -527,6 +563,32 @@ def main():
         if rank == 0:
             print(json.dumps({"profiling": True, "workload": cfg, "rhs_per_step": nrhs, "mixed_precision": mixed}),
                   flush=True)
+        prob.close()
+        return
+
+    if args.report >= 0:  # per-op table of one product (after warm-up launches with the same options)
+        ropts = lr.default_options(precision=args.report, autotune=1 if args.report else 0)
+        for _ in range(max(args.warmup, 1)):
+            prob.jacobian_apply(X1, X2, transpose=args.transpose, y1=Y1, y2=Y2, options=ropts)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        prob.jacobian_apply(X1, X2, transpose=args.transpose, y1=Y1, y2=Y2, options=ropts)
+        e1.record(st)
+        torch.cuda.synchronize()
+        prob.profile(True)
+        prob.jacobian_apply(X1, X2, transpose=args.transpose, y1=Y1, y2=Y2, options=ropts)
+        rows = prob.profile_report()
+        prob.profile(False)
+        tot = sum(r[1] for r in rows)
+        if rank == 0:
+            print(f"# {args.config}{' ' + args.shape if args.shape else ''}: {nrhs} vectors, precision {args.report}, "
+                  f"{'transposed' if args.transpose else 'forward'} product: {e0.elapsed_time(e1):.2f} ms "
+                  f"(CUDA events, no per-op events); per-op events below sum to {tot:.2f} ms")
+            print("# op\tms\tlaunches\talgorithmic flops\tshare\tTFLOP/s")
+            for tag, ms_, n_, fl in rows:
+                print(f"{tag}\t{ms_:.3f}\t{n_}\t{fl:.4g}\t{100 * ms_ / tot:.1f}%\t"
+                      f"{(fl / (ms_ * 1e-3) / 1e12 if ms_ > 0 else 0):.3f}")
         prob.close()
         return
 
@@ -623,6 +685,16 @@ def main():
     # mixed precision: the same product with the GEMMs on tcgen05 (BF16x3 and TF32, FP32 accumulate)
     mixed = {} if args.no_mixed else time_mixed(lr, prob, X1, X2, Y1, Y2, args.steps, args.warmup, st, dist,
                                                  products)
+    if mixed and default_workload:
+        # the whole alpha batch of the workload (15 vectors: 3 components x {0, +-0.05, +-0.1})
+        z1, z2 = random_probe(nk, o, v, seed=replica_seed(rank) + 1, nrhs=nsys)
+        Z1 = torch.as_tensor(z1, device=dev)
+        Z2 = torch.as_tensor(z2 * nk, device=dev)
+        del z1, z2
+        m15 = time_mixed(lr, prob, Z1, Z2, None, None, args.steps, args.warmup, st, dist, nsys * args.steps * ws,
+                         precs=(2,))
+        mixed["bf16x3_whole_alpha_batch"] = dict(m15["bf16x3"], rhs_per_step=nsys)
+        del Z1, Z2
     prob.close()
     del X1, X2, Y1, Y2, h1, h2, o1, o2
     torch.cuda.empty_cache()
