@@ -196,7 +196,7 @@ lrcc_status lrcc_solve_ground_state(lrcc_problem* p, const lrcc_options* optp, v
 
   // CCSD amplitudes ------------------------------------------------------------------
   const int depth = bs.depth;
-  std::vector<std::vector<cd>> Bm(1, std::vector<cd>(depth * depth, 0.0));
+  if ((s = bs.diis_reset()) != LRCC_OK) return s;
   int nhist = 0, it = 0;
   bool conv = false;
   double err = 0.0;
@@ -235,7 +235,7 @@ lrcc_status lrcc_solve_ground_state(lrcc_problem* p, const lrcc_options* optp, v
       conv = true;
       break;
     }
-    if ((s = bs.diis(it, nhist, Bm, T)) != LRCC_OK) return s;
+    if ((s = bs.diis(it, nhist, T)) != LRCC_OK) return s;
   }
   if (info) {
     info[0] = it;

@@ -29,37 +29,6 @@
 using namespace lrcc;
 using cd = std::complex<double>;
 
-namespace {
-
-// Gaussian elimination with partial pivoting on a small dense complex system.
-bool solve_small(std::vector<cd> A, std::vector<cd> b, int n, std::vector<cd>& x) {
-  for (int c = 0; c < n; ++c) {
-    int piv = c;
-    for (int r = c + 1; r < n; ++r)
-      if (std::abs(A[r * n + c]) > std::abs(A[piv * n + c])) piv = r;
-    if (std::abs(A[piv * n + c]) < 1e-300) return false;
-    if (piv != c) {
-      for (int k = 0; k < n; ++k) std::swap(A[c * n + k], A[piv * n + k]);
-      std::swap(b[c], b[piv]);
-    }
-    for (int r = c + 1; r < n; ++r) {
-      cd f = A[r * n + c] / A[c * n + c];
-      for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
-      b[r] -= f * b[c];
-    }
-  }
-  x.assign(n, 0.0);
-  for (int r = n - 1; r >= 0; --r) {
-    cd s = b[r];
-    for (int k = r + 1; k < n; ++k) s -= A[r * n + k] * x[k];
-    x[r] = s / A[r * n + r];
-  }
-  for (auto& v : x)
-    if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return false;
-  return true;
-}
-
-}  // namespace
 
 namespace lrcc {
 
@@ -113,6 +82,7 @@ lrcc_status BatchSolver::init() {
   PART = dev.get<double2>(rt, dot_partial_elems(maxpairs), ok);
   DOT = dev.get<double2>(rt, (size_t)maxpairs, ok);
   COEF = dev.get<double2>(rt, (size_t)depth * ns, ok);
+  BDEV = dev.get<double2>(rt, (size_t)ns * depth * depth, ok);
   PV = dev.get<const double2*>(rt, (size_t)depth, ok);
   if (!ok) return LRCC_ENOMEM;
   const Plan& P = rt.plan;
@@ -168,59 +138,20 @@ lrcc_status BatchSolver::maxabs(const double2* x, int nrhs, std::vector<double>&
   return LRCC_OK;
 }
 
-lrcc_status BatchSolver::diis(int it, int& nhist, std::vector<std::vector<cd>>& Bm, double2* X) {
-  lrcc_status s2;
-  const int slot = it % depth;
+// DIIS step on the device: B entries of the newest error vectors, the per-system bordered
+// solve and the extrapolated iterates into X (solver_kernels.cu); no host round trip.
+lrcc_status BatchSolver::diis(int it, int& nhist, double2* X) {
   nhist = std::min(nhist + 1, depth);
-  std::vector<const double2*> pa, pb;
-  std::vector<int> slots;
-  for (int j = 0; j < nhist; ++j) {
-    const int sj = ((it - j) % depth + depth) % depth;
-    slots.push_back(sj);
-    for (int i = 0; i < ns; ++i) {
-      pa.push_back(HE + ((size_t)slot * ns + i) * vec);
-      pb.push_back(HE + ((size_t)sj * ns + i) * vec);
-    }
-  }
-  std::vector<cd> row;
-  if ((s2 = dots(pa, pb, 1, vec, row)) != LRCC_OK) return s2;
-  for (int j = 0; j < nhist; ++j)
-    for (int i = 0; i < ns; ++i) {
-      const int sj = slots[j];
-      Bm[i][slot * depth + sj] = row[j * ns + i];
-      Bm[i][sj * depth + slot] = std::conj(row[j * ns + i]);
-    }
-  std::vector<double2> coef((size_t)nhist * ns, make_double2(0.0, 0.0));
-  for (int i = 0; i < ns; ++i) {
-    std::vector<cd> x;
-    bool good = false;
-    if (nhist >= 2 && (opt.diis_period <= 1 || (it + 1) % opt.diis_period == 0)) {
-      const int m = nhist + 1;
-      std::vector<cd> A(m * m, 0.0), b(m, 0.0);
-      double sc = 0.0;
-      for (int a = 0; a < nhist; ++a) sc = std::max(sc, std::abs(Bm[i][slots[a] * depth + slots[a]]));
-      sc = sc > 0 ? 1.0 / sc : 1.0;
-      for (int a = 0; a < nhist; ++a) {
-        for (int c = 0; c < nhist; ++c) A[a * m + c] = sc * Bm[i][slots[a] * depth + slots[c]];
-        A[a * m + nhist] = -1.0;
-        A[nhist * m + a] = -1.0;
-      }
-      b[nhist] = -1.0;
-      good = solve_small(A, b, m, x);
-    }
-    for (int j = 0; j < nhist; ++j) {
-      cd cj = good ? x[j] : (j == 0 ? cd(1.0) : cd(0.0));
-      coef[(size_t)j * ns + i] = make_double2(cj.real(), cj.imag());
-    }
-  }
-  std::vector<const double2*> pv(nhist);
-  for (int j = 0; j < nhist; ++j) pv[j] = HX + (size_t)slots[j] * ns * vec;
-  if (!rt.ck(cudaMemcpy(PV, pv.data(), nhist * sizeof(void*), cudaMemcpyHostToDevice), "pv") ||
-      !rt.ck(cudaMemcpy(COEF, coef.data(), coef.size() * sizeof(double2), cudaMemcpyHostToDevice), "coef") ||
-      !rt.ck(launch_lincomb(PV, COEF, nhist, X, vec, vec, ns, st), "lincomb"))
+  const int extrapolate = (nhist >= 2 && (opt.diis_period <= 1 || (it + 1) % opt.diis_period == 0)) ? 1 : 0;
+  if (!rt.ck(launch_diis_device(HE, HX, BDEV, it, depth, ns, nhist, extrapolate, vec, PART, COEF, X, st), "diis"))
     return LRCC_ECUDA;
-  rt.launches++;
+  rt.launches += 3;
   return LRCC_OK;
+}
+
+lrcc_status BatchSolver::diis_reset() {
+  return rt.ck(cudaMemsetAsync(BDEV, 0, (size_t)ns * depth * depth * sizeof(double2), st), "diis reset") ? LRCC_OK
+                                                                                                         : LRCC_ECUDA;
 }
 
 // Jacobi + DIIS on (A - w) x = -rhs (tr = 0, iterate in rt.in) or (A^T - w) x = -rhs
@@ -233,7 +164,7 @@ lrcc_status BatchSolver::jacobi_diis(int tr, const double2* rhs, const std::vect
   double2* Y = tr ? rt.in : rt.out;
   if (!rt.ck(launch_guess(rhs, DEN, om, X, vec, vec, ns, st), "guess")) return LRCC_ECUDA;
   rt.launches++;
-  std::vector<std::vector<cd>> Bm(ns, std::vector<cd>(depth * depth, 0.0));
+  if ((s2 = diis_reset()) != LRCC_OK) return s2;
   int nhist = 0;
   conv = false;
   for (int it = 0; it < maxiter; ++it) {
@@ -261,7 +192,7 @@ lrcc_status BatchSolver::jacobi_diis(int tr, const double2* rhs, const std::vect
       conv = true;
       return LRCC_OK;
     }
-    if ((s2 = diis(it, nhist, Bm, X)) != LRCC_OK) return s2;
+    if ((s2 = diis(it, nhist, X)) != LRCC_OK) return s2;
   }
   return LRCC_OK;
 }

@@ -57,6 +57,7 @@ struct BatchSolver {
   cudaStream_t st = 0;
   Dev dev;
   double2 *HX = nullptr, *HE = nullptr, *RES = nullptr, *PART = nullptr, *DOT = nullptr, *COEF = nullptr;
+  double2* BDEV = nullptr;  // per-system DIIS B matrices [ns][depth][depth]
   double* DEN = nullptr;
   unsigned long long* RMAX = nullptr;
   const double2 **PA = nullptr, **PB = nullptr, **PV = nullptr;
@@ -72,8 +73,11 @@ struct BatchSolver {
                    long long len, std::vector<cd>& out);
   lrcc_status maxabs(const double2* x, int nrhs, std::vector<double>& out);
   // DIIS with error vectors HE[slot] and iterates HX[slot] (written by the update kernel):
-  // updates the per-system B matrices and writes the extrapolated iterates into X
-  lrcc_status diis(int it, int& nhist, std::vector<std::vector<cd>>& Bm, double2* X);
+  // updates the per-system B matrices (device memory) and writes the extrapolated iterates
+  // into X, all on the device
+  lrcc_status diis(int it, int& nhist, double2* X);
+  // zero the B matrices before a new iteration
+  lrcc_status diis_reset();
   lrcc_status jacobi_diis(int tr, const double2* rhs, const std::vector<double>& rhsmax, const double* om, int prec,
                           double tol, int maxiter, bool& conv);
   lrcc_status solve(int tr, const double2* rhs, const double* om, double2* sol, bool& converged);

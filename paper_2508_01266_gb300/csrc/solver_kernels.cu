@@ -184,6 +184,176 @@ cudaError_t launch_dots(const double2* const* a, const double2* const* b, int co
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------
+// DIIS on the device (Sec. II.D): the inner products of the newest error vector with the
+// history, each system's Hermitian B matrix, the bordered (m+1) x (m+1) solve and the
+// extrapolation, all in FP64 without host round trips.  The history is a ring of `depth`
+// slots of ns vectors (HE: errors, HX: iterates); iteration `it` wrote slot it % depth and
+// the j-th newest entry is slot (it - j) mod depth.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ int ring_slot(int it, int j, int depth) { return ((it - j) % depth + depth) % depth; }
+
+// pass 1 of <HE[newest][i], HE[(it - j)][i]> (first operand conjugated), pair p = j * ns + i
+__global__ void diis_dot_pass1(const double2* HE, int it, int depth, int ns, long long n, double2* part) {
+  const int p = blockIdx.y;
+  const int j = p / ns, i = p - j * ns;
+  const double2* A = HE + ((long long)ring_slot(it, 0, depth) * ns + i) * n;
+  const double2* Bv = HE + ((long long)ring_slot(it, j, depth) * ns + i) * n;
+  const long long chunk = (n + DOT_BLOCKS - 1) / DOT_BLOCKS;
+  const long long i0 = (long long)blockIdx.x * chunk;
+  const long long i1 = (i0 + chunk < n) ? i0 + chunk : n;
+  double sr = 0.0, si = 0.0;
+  for (long long k = i0 + threadIdx.x; k < i1; k += blockDim.x) {
+    const double2 x = A[k], y = Bv[k];
+    sr = fma(x.x, y.x, sr);
+    sr = fma(x.y, y.y, sr);
+    si = fma(x.x, y.y, si);
+    si = fma(-x.y, y.x, si);
+  }
+  __shared__ double rr[256], ri[256];
+  rr[threadIdx.x] = sr;
+  ri[threadIdx.x] = si;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      rr[threadIdx.x] += rr[threadIdx.x + s];
+      ri[threadIdx.x] += ri[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(long long)p * DOT_BLOCKS + blockIdx.x] = make_double2(rr[0], ri[0]);
+}
+
+__device__ __forceinline__ double cabs2(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double q = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / q, (a.y * b.x - a.x * b.y) / q);
+}
+
+constexpr int DIIS_MAX = 16;  // history depth limit (the bordered system is at most 17 x 17)
+
+// One thread per system: the second reduction pass (fixed order) of its nhist new B entries,
+// the B matrix update (B[slot][sj] and its conjugate), and when `extrapolate` the bordered
+// system scaled by 1 / max diag (the coefficients do not depend on the scale), solved by
+// Gaussian elimination with partial pivoting.  A singular or non-finite system keeps the
+// newest iterate (coefficient 1 on it).
+__global__ void diis_solve_kernel(const double2* part, double2* B, int it, int depth, int ns, int nhist,
+                                  int extrapolate, double2* coef) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ns) return;
+  double2* Bi = B + (long long)i * depth * depth;
+  const int slot = ring_slot(it, 0, depth);
+  for (int j = 0; j < nhist; ++j) {
+    const int sj = ring_slot(it, j, depth);
+    const long long p = (long long)j * ns + i;
+    double sr = 0.0, si = 0.0;
+    for (int k = 0; k < DOT_BLOCKS; ++k) {
+      sr += part[p * DOT_BLOCKS + k].x;
+      si += part[p * DOT_BLOCKS + k].y;
+    }
+    Bi[slot * depth + sj] = make_double2(sr, si);
+    Bi[sj * depth + slot] = make_double2(sr, -si);
+  }
+  double2 x[DIIS_MAX + 1];
+  bool good = false;
+  if (extrapolate && nhist >= 2) {
+    const int m = nhist + 1;
+    double2 A[(DIIS_MAX + 1) * (DIIS_MAX + 1)], b[DIIS_MAX + 1];
+    double sc = 0.0;
+    for (int a = 0; a < nhist; ++a) {
+      const int sa = ring_slot(it, a, depth);
+      sc = fmax(sc, cabs2(Bi[sa * depth + sa]));
+    }
+    sc = sc > 0.0 ? 1.0 / sc : 1.0;
+    for (int a = 0; a < m; ++a) {
+      b[a] = make_double2(a == nhist ? -1.0 : 0.0, 0.0);
+      for (int c = 0; c < m; ++c) A[a * m + c] = make_double2(0.0, 0.0);
+    }
+    for (int a = 0; a < nhist; ++a) {
+      const int sa = ring_slot(it, a, depth);
+      for (int c = 0; c < nhist; ++c) {
+        const double2 v = Bi[sa * depth + ring_slot(it, c, depth)];
+        A[a * m + c] = make_double2(sc * v.x, sc * v.y);
+      }
+      A[a * m + nhist] = make_double2(-1.0, 0.0);
+      A[nhist * m + a] = make_double2(-1.0, 0.0);
+    }
+    good = true;
+    for (int c = 0; c < m && good; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < m; ++r)
+        if (cabs2(A[r * m + c]) > cabs2(A[piv * m + c])) piv = r;
+      if (cabs2(A[piv * m + c]) < 1e-300) {
+        good = false;
+        break;
+      }
+      if (piv != c) {
+        for (int k = 0; k < m; ++k) {
+          const double2 t = A[c * m + k];
+          A[c * m + k] = A[piv * m + k];
+          A[piv * m + k] = t;
+        }
+        const double2 t = b[c];
+        b[c] = b[piv];
+        b[piv] = t;
+      }
+      for (int r = c + 1; r < m; ++r) {
+        const double2 f = cdiv(A[r * m + c], A[c * m + c]);
+        for (int k = c; k < m; ++k) {
+          const double2 u = cmul(f, A[c * m + k]);
+          A[r * m + k] = make_double2(A[r * m + k].x - u.x, A[r * m + k].y - u.y);
+        }
+        const double2 u = cmul(f, b[c]);
+        b[r] = make_double2(b[r].x - u.x, b[r].y - u.y);
+      }
+    }
+    if (good) {
+      for (int r = m - 1; r >= 0; --r) {
+        double2 s = b[r];
+        for (int k = r + 1; k < m; ++k) {
+          const double2 u = cmul(A[r * m + k], x[k]);
+          s = make_double2(s.x - u.x, s.y - u.y);
+        }
+        x[r] = cdiv(s, A[r * m + r]);
+        if (!isfinite(x[r].x) || !isfinite(x[r].y)) good = false;
+      }
+    }
+  }
+  for (int j = 0; j < nhist; ++j)
+    coef[(long long)j * ns + i] = good ? x[j] : make_double2(j == 0 ? 1.0 : 0.0, 0.0);
+}
+
+// out[r] = sum_j c[j*nrhs + r] * HX[slot (it - j)][r]
+__global__ void diis_lincomb_kernel(const double2* HX, int it, int depth, const double2* c, int m, double2* out,
+                                    long long n, long long stride, int nrhs) {
+  const long long r = blockIdx.y;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int j = 0; j < m; ++j) {
+      const double2 cc = c[(long long)j * nrhs + r];
+      const double2 x = HX[((long long)ring_slot(it, j, depth) * nrhs + r) * stride + i];
+      sr += cc.x * x.x - cc.y * x.y;
+      si += cc.x * x.y + cc.y * x.x;
+    }
+    out[r * stride + i] = make_double2(sr, si);
+  }
+}
+
+cudaError_t launch_diis_device(const double2* HE, const double2* HX, double2* B, int it, int depth, int ns, int nhist,
+                               int extrapolate, long long n, double2* part, double2* coef, double2* out,
+                               cudaStream_t st) {
+  if (depth > DIIS_MAX || nhist < 1 || nhist > depth || (long long)nhist * ns > 65535) return cudaErrorInvalidValue;
+  dim3 g1(DOT_BLOCKS, nhist * ns);
+  diis_dot_pass1<<<g1, 256, 0, st>>>(HE, it, depth, ns, n, part);
+  diis_solve_kernel<<<(ns + 31) / 32, 32, 0, st>>>(part, B, it, depth, ns, nhist, extrapolate, coef);
+  dim3 g3(grid_for(n, 256 * 4), ns);
+  diis_lincomb_kernel<<<g3, 256, 0, st>>>(HX, it, depth, coef, nhist, out, n, n, ns);
+  return cudaGetLastError();
+}
+
 // out[r] = sum_j c[j*nrhs + r] * v_j[r]   (v_j given as base pointers with RHS stride)
 __global__ void lincomb_kernel(const double2* const* v, const double2* c, int m, double2* out, long long n,
                                long long stride, int nrhs) {
