@@ -460,6 +460,43 @@ def alpha_run(lr, name, prec, refine_tol=1e-7):
     return out
 
 
+def alpha_batch_run(lr, prec):
+    """The mixed-size batch at its real shapes, (Nk, nocc, nvir) = (3,4,24), (5,6,32), (7,8,48)
+    with naux = 4 nvir: ground states, then alpha_zz at w = 0 and 0.1 Ha for the three chains in
+    one lrcc_batch_polarizability call, then each chain alone; the batch must equal the solo runs
+    bitwise (its kernels are deterministic whatever runs beside them)."""
+    import numpy as np
+    from synth import make_problem
+    shapes = [(3, 4, 24), (5, 6, 32), (7, 8, 48)]
+    comps, omegas = [2], [0.0, 0.1]
+    probs, out = [], {"alpha_run": "mixed-size batch", "shapes": shapes, "comps": comps, "omegas": omegas,
+                      "precision": {0: "fp64", 1: "tf32", 2: "bf16x3"}[prec], "ground_state_seconds": []}
+    opts = lr.default_options(precision=prec, conv_tol=1e-9, refine_tol=1e-9, max_iter=300)
+    for nk, o, v in shapes:
+        p = make_problem(nk, o, v, 4 * v, seed=1266)
+        pr = lr.Problem(nk, o, v, 4 * v)
+        pr.set_integrals(p.L, p.eps, p.dip)
+        t0 = time.perf_counter()
+        pr.solve_ground_state(opts)
+        out["ground_state_seconds"].append(time.perf_counter() - t0)
+        probs.append(pr)
+    aopts = lr.default_options(precision=prec, conv_tol=1e-10, refine_tol=1e-7, max_iter=300)
+    t0 = time.perf_counter()
+    batch = lr.batch_polarizability(probs, comps, omegas, aopts)
+    out["batch_seconds"] = time.perf_counter() - t0
+    solo, t_solo = [], 0.0
+    for pr in probs:
+        t0 = time.perf_counter()
+        solo.append(pr.polarizability(comps, omegas, aopts))
+        t_solo += time.perf_counter() - t0
+        pr.close()
+    out["solo_seconds_total"] = t_solo
+    out["alpha_zz"] = [[float(x) for x in a[:, 0, 0].real] for a, _ in batch]
+    out["bitwise_equal_to_solo"] = [bool(np.array_equal(a, b)) for (a, _), (b, _) in zip(batch, solo)]
+    out["status"] = [int(i[1]) for _, i in batch]
+    return out
+
+
 def dry_run(args):
     """Rank setup only (no GPU, no library): every rank reports its rank and replica seed; rank 0
     prints one line.  Used by the CPU tests of the replica launch."""
@@ -533,13 +570,15 @@ def main():
     from synth import make_problem, random_amplitudes, random_probe
 
     if args.alpha:
-        if args.alpha_comps or args.alpha_omegas:
+        if args.alpha != "batch" and (args.alpha_comps or args.alpha_omegas):
             comps0, omegas0, forms0 = ALPHA_RUNS[args.alpha]
             ALPHA_RUNS[args.alpha] = ([int(x) for x in args.alpha_comps.split(",")] if args.alpha_comps else comps0,
                                       [float(x) for x in args.alpha_omegas.split(",")] if args.alpha_omegas
                                       else omegas0, forms0)
         if rank == 0:
-            print(json.dumps(alpha_run(lr, args.alpha, args.alpha_precision)), flush=True)
+            res = alpha_batch_run(lr, args.alpha_precision) if args.alpha == "batch" else \
+                alpha_run(lr, args.alpha, args.alpha_precision)
+            print(json.dumps(res), flush=True)
         return
 
     cfg, comps, omegas, nsys = workload(args.config)
@@ -662,24 +701,28 @@ def main():
            "h2d_bytes_per_step": int(h1.numel() * 16 + h2.numel() * 16),
            "d2h_bytes_per_step": int(o1.numel() * 16 + o2.numel() * 16)}
 
-    # roofline of the dominant kernel: the FP64 tiled GEMM (every contraction of the FP64 product;
-    # the ladder is its largest op).  Algorithmic flops count 8 real flops per complex
-    # multiply-add; the kernel executes 6 (Gauss's three-product form), so the pipe's own
-    # utilisation is `executed_frac`.
-    achieved = gemm_fl / (gemm_ms * 1e-3) / 1e9 if gemm_ms else None
+    # roofline of the dominant kernel's dominant op: the ladder contraction launches of the FP64
+    # tiled GEMM (SURVEY's unit: 8 flops per complex multiply-add of the ladder, here the
+    # pair-swap-halved count the kernel launches).  The kernel executes 6 flops per complex
+    # multiply-add (Gauss's three-product form): `executed_frac` is the FP64 pipe's utilisation.
     lad_rate = lad_fl / (lad_ms * 1e-3) / 1e9 if lad_ms else None
+    gemm_rate = gemm_fl / (gemm_ms * 1e-3) / 1e9 if gemm_ms else None
     default_workload = args.config == "c2" and not args.shape and nrhs == len(comps)
     traffic = None
     if TRAFFIC_RECORD and default_workload and _source_sha(TRAFFIC_RECORD[0]) == TRAFFIC_RECORD[1]:
         traffic = TRAFFIC_RECORD[2]
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-            "frac": (achieved / FP64_NOMINAL_GFLOPS) if achieved else None,
-            "executed_frac": (0.75 * achieved / FP64_NOMINAL_GFLOPS) if achieved else None,
+    roof = {"bound": "alu", "achieved": lad_rate, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+            "frac": (lad_rate / FP64_NOMINAL_GFLOPS) if lad_rate else None,
+            "executed_frac": (0.75 * lad_rate / FP64_NOMINAL_GFLOPS) if lad_rate else None,
             "traffic": traffic,
-            "kernel": "zgemm_seg_kernel<double> (all FP64 contractions of the product)",
-            "launches_per_step": gemm_n,
+            "kernel": "zgemm_seg_kernel<double,64,64,8,4,4>, ladder contraction launches",
+            "launches_per_step": lad_n,
+            "flops_per_launch": lad_fl / max(lad_n, 1),
             "peak_source": "FP64 nominal 1.25 TFLOP/s of the profiling recipe (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-            "ladder_gflops": lad_rate, "ladder_share_of_step": lad_ms / max(all_ms, 1e-9),
+            "all_fp64_gemm_gflops": gemm_rate, "all_fp64_gemm_executed_frac":
+                (0.75 * gemm_rate / FP64_NOMINAL_GFLOPS) if gemm_rate else None,
+            "gemm_launches_per_step": gemm_n,
+            "ladder_share_of_step": lad_ms / max(all_ms, 1e-9),
             "gemm_share_of_step": gemm_ms / max(all_ms, 1e-9),
             "step_gflops_algorithmic": all_fl / (all_ms * 1e-3) / 1e9 if all_ms else None,
             "profile": "per-op CUDA events on one untimed product after the timed region"}

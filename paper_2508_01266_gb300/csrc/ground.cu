@@ -197,6 +197,7 @@ lrcc_status lrcc_solve_ground_state(lrcc_problem* p, const lrcc_options* optp, v
   // CCSD amplitudes ------------------------------------------------------------------
   const int depth = bs.depth;
   if ((s = bs.diis_reset()) != LRCC_OK) return s;
+  CK(launch_inv_den(bs.DEN, W0, bs.INV, G.vec, 1, G.st), "1 / D");
   int nhist = 0, it = 0;
   bool conv = false;
   double err = 0.0;
@@ -223,7 +224,7 @@ lrcc_status lrcc_solve_ground_state(lrcc_problem* p, const lrcc_options* optp, v
     const int slot = it % depth;
     CK(cudaMemsetAsync(bs.RMAX, 0, sizeof(unsigned long long), G.st), "memset");
     // e = -Omega / D, t_new = t + e  (update kernel with y = 0, w = 0, rhs = Omega)
-    CK(launch_update(T, Z, bs.RES, bs.DEN, W0, bs.HE + (size_t)slot * G.vec, bs.HX + (size_t)slot * G.vec, bs.RMAX,
+    CK(launch_update(T, Z, bs.RES, bs.INV, W0, bs.HE + (size_t)slot * G.vec, bs.HX + (size_t)slot * G.vec, bs.RMAX,
                      G.vec, G.vec, 1, G.st),
        "update");
     rt.launches++;

@@ -375,8 +375,138 @@ __global__ void perm_kernel(PermArgs p) {
   }
 }
 
+// Orbital-index strides of a layout at fixed momenta (every layout is affine in its four
+// orbital indices once k1, k2, k3 are fixed; see lay_off).
+__host__ __device__ inline void lay_strides(int kind, int nk, const int* n, long long* s) {
+  const long long n0 = n[0], n1 = n[1], n2 = n[2], n3 = n[3];
+  if (kind == 0) {  // K3
+    s[0] = n1 * n2 * n3; s[1] = n2 * n3; s[2] = n3; s[3] = 1;
+  } else if (kind == 1) {  // PP: cols = nk n2 n3
+    const long long cols = (long long)nk * n2 * n3;
+    s[0] = n1 * cols; s[1] = cols; s[2] = n3; s[3] = 1;
+  } else if (kind == 2) {  // PH: cols = nk n3 n1
+    const long long cols = (long long)nk * n3 * n1;
+    s[0] = n2 * cols; s[1] = 1; s[2] = cols; s[3] = n1;
+  } else {  // CH
+    s[0] = n2 * n1 * n3; s[1] = n3; s[2] = n1 * n3; s[3] = 1;
+  }
+}
+
+constexpr int SLAB_MAX = 64;  // largest orbital extent of a slab dimension
+
+struct SlabArgs {
+  PermArgs p;
+  int dx, dy;               // destination orbital slots of the slab: dx has stride 1 in the destination
+  int o0, o1;               // the other two destination orbital slots (outer)
+  long long dsx, dsy;       // destination strides of the slab slots
+  long long ssx, ssy;       // source strides of the slab slots
+  long long nouter;         // nk^3 * n[o0] * n[o1]
+};
+
+// One CTA handles whole slabs: the (dy, dx) plane of the destination at fixed momenta and fixed
+// outer orbital indices.  Source elements are read along the source's unit-stride direction
+// into shared memory, destination elements written along dx; both global sides coalesce.
+__global__ void __launch_bounds__(256) perm_slab_kernel(SlabArgs a) {
+  extern __shared__ double2 slab[];  // [ny][nx + 1]
+  const PermArgs& p = a.p;
+  const long long rhs = blockIdx.y;
+  const double2* S = p.S + rhs * p.sS;
+  double2* D = p.D + rhs * p.sD;
+  const int nk = p.dnk;
+  const int nx = p.dn[a.dx], ny = p.dn[a.dy];
+  const int pitch = nx + 1;
+  const int nel = nx * ny;
+  // source slot of each destination slot
+  int inv[4];
+  for (int s = 0; s < 4; ++s) inv[p.pi[s]] = s;
+  const bool src_x_fast = a.ssx <= a.ssy;  // read the source along its faster slab direction
+  for (long long ob = blockIdx.x; ob < a.nouter; ob += gridDim.x) {
+    long long r = ob;
+    int di[4] = {0, 0, 0, 0}, dk[4];
+    di[a.o1] = (int)(r % p.dn[a.o1]); r /= p.dn[a.o1];
+    di[a.o0] = (int)(r % p.dn[a.o0]); r /= p.dn[a.o0];
+    dk[2] = (int)(r % nk); r /= nk;
+    dk[1] = (int)(r % nk); r /= nk;
+    dk[0] = (int)r;
+    dk[3] = kmod(dk[0] + dk[1] - dk[2], nk);
+    const long long dbase = lay_off(p.dkind, nk, p.dn, dk[0], dk[1], dk[2], di[0], di[1], di[2], di[3]);
+    const long long sbase = lay_off(p.skind, p.snk, p.sn, dk[p.pi[0]], dk[p.pi[1]], dk[p.pi[2]], di[p.pi[0]],
+                                    di[p.pi[1]], di[p.pi[2]], di[p.pi[3]]);
+    (void)inv;
+    __syncthreads();  // the previous slab's writes have read the shared tile
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+      int x, y;
+      if (src_x_fast) {
+        x = e % nx;
+        y = e / nx;
+      } else {
+        y = e % ny;
+        x = e / ny;
+      }
+      slab[y * pitch + x] = S[sbase + x * a.ssx + y * a.ssy];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+      const int x = e % nx, y = e / nx;
+      const double2 s = slab[y * pitch + x];
+      double2* dp = D + dbase + x * a.dsx + y * a.dsy;
+      double2 d = *dp;
+      d.x += p.ar * s.x - p.ai * s.y;
+      d.y += p.ar * s.y + p.ai * s.x;
+      *dp = d;
+    }
+  }
+}
+
 cudaError_t launch_perm_f64(const PermArgs& p, int nrhs, cudaStream_t st) {
   if (p.total <= 0) return cudaSuccess;
+  // slab path: destination slot dx with unit stride, dy = the destination slot whose source
+  // slot has unit stride (or the next-fastest destination slot when that is dx itself)
+  long long ds[4], ss[4];
+  lay_strides(p.dkind, p.dnk, p.dn, ds);
+  lay_strides(p.skind, p.snk, p.sn, ss);
+  int dx = 0;
+  for (int s = 0; s < 4; ++s)
+    if (ds[s] == 1) dx = s;
+  int sfast = 0;
+  for (int s = 0; s < 4; ++s)
+    if (ss[s] == 1) sfast = s;
+  int dy = p.pi[sfast];
+  if (dy == dx) {
+    dy = -1;
+    for (int s = 0; s < 4; ++s)
+      if (s != dx && (dy < 0 || ds[s] < ds[dy])) dy = s;
+  }
+  const bool slab_ok = p.dnk == p.snk && p.dn[dx] <= SLAB_MAX && p.dn[dy] <= SLAB_MAX && p.dn[dx] >= 1 &&
+                       p.dn[dy] >= 1;
+  if (slab_ok) {
+    SlabArgs a;
+    a.p = p;
+    a.dx = dx;
+    a.dy = dy;
+    int oth[2], c = 0;
+    for (int s = 0; s < 4; ++s)
+      if (s != dx && s != dy) oth[c++] = s;
+    a.o0 = oth[0];
+    a.o1 = oth[1];
+    a.dsx = ds[dx];
+    a.dsy = ds[dy];
+    int inv[4];
+    for (int s = 0; s < 4; ++s) inv[p.pi[s]] = s;
+    a.ssx = ss[inv[dx]];
+    a.ssy = ss[inv[dy]];
+    a.nouter = (long long)p.dnk * p.dnk * p.dnk * p.dn[a.o0] * p.dn[a.o1];
+    const size_t smem = (size_t)p.dn[dy] * (p.dn[dx] + 1) * sizeof(double2);
+    static const cudaError_t attr =  // thread-safe one-time setup: up to 64 x 65 complex
+        cudaFuncSetAttribute(perm_slab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(SLAB_MAX * (SLAB_MAX + 1) * sizeof(double2)));
+    if (attr != cudaSuccess) return attr;
+    long long blocks = a.nouter;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    dim3 grid((unsigned)blocks, (unsigned)nrhs);
+    perm_slab_kernel<<<grid, 256, smem, st>>>(a);
+    return cudaGetLastError();
+  }
   long long blocks = (p.total + 255) / 256;
   if (blocks > 152LL * 64) blocks = 152LL * 64;
   dim3 grid((unsigned)blocks, (unsigned)nrhs);

@@ -76,6 +76,7 @@ lrcc_status BatchSolver::init() {
   host_history = host;
   RES = dev.get<double2>(rt, (size_t)ns * vec, ok);
   DEN = dev.get<double>(rt, (size_t)vec, ok);
+  INV = dev.get<double>(rt, (size_t)ns * vec, ok);
   RMAX = dev.get<unsigned long long>(rt, (size_t)ns, ok);
   PA = dev.get<const double2*>(rt, (size_t)maxpairs, ok);
   PB = dev.get<const double2*>(rt, (size_t)maxpairs, ok);
@@ -162,7 +163,10 @@ lrcc_status BatchSolver::jacobi_diis(int tr, const double2* rhs, const std::vect
   lrcc_status s2;
   double2* X = tr ? rt.out : rt.in;
   double2* Y = tr ? rt.in : rt.out;
-  if (!rt.ck(launch_guess(rhs, DEN, om, X, vec, vec, ns, st), "guess")) return LRCC_ECUDA;
+  if (!rt.ck(launch_inv_den(DEN, om, INV, vec, ns, st), "1 / (D - w)") ||
+      !rt.ck(launch_guess(rhs, INV, X, vec, vec, ns, st), "guess"))
+    return LRCC_ECUDA;
+  rt.launches++;
   rt.launches++;
   if ((s2 = diis_reset()) != LRCC_OK) return s2;
   int nhist = 0;
@@ -172,7 +176,7 @@ lrcc_status BatchSolver::jacobi_diis(int tr, const double2* rhs, const std::vect
     if ((s2 = rt.apply(tr, ns, st, prec, opt.use_graphs != 0, opt.autotune != 0)) != LRCC_OK) return s2;
     const int slot = it % depth;
     if (!rt.ck(cudaMemsetAsync(RMAX, 0, ns * sizeof(unsigned long long), st), "memset") ||
-        !rt.ck(launch_update(X, Y, rhs, DEN, om, HE + (size_t)slot * ns * vec, HX + (size_t)slot * ns * vec, RMAX,
+        !rt.ck(launch_update(X, Y, rhs, INV, om, HE + (size_t)slot * ns * vec, HX + (size_t)slot * ns * vec, RMAX,
                              vec, vec, ns, st),
                "update"))
       return LRCC_ECUDA;

@@ -59,6 +59,7 @@ struct BatchSolver {
   double2 *HX = nullptr, *HE = nullptr, *RES = nullptr, *PART = nullptr, *DOT = nullptr, *COEF = nullptr;
   double2* BDEV = nullptr;  // per-system DIIS B matrices [ns][depth][depth]
   double* DEN = nullptr;
+  double* INV = nullptr;  // 1 / (DEN - w) per system of the current solve
   unsigned long long* RMAX = nullptr;
   const double2 **PA = nullptr, **PB = nullptr, **PV = nullptr;
   int total_it = 0;

@@ -15,27 +15,72 @@ static unsigned grid_for(long long n, int per_block) {
   return (unsigned)b;
 }
 
-// res = -xi - y + w x ; e = res / (den - w) ; xnew = x + e ; rmax[r] = max |res|
-__global__ void update_kernel(const double2* x, const double2* y, const double2* xi, const double* den,
-                              const double* omega, double2* e, double2* xnew, unsigned long long* rmax, long long n,
-                              long long stride) {
+// Every elementwise pass below takes EU elements per thread per grid-stride step and issues
+// all their loads before any result is stored: these passes are bound by HBM latency x
+// bandwidth, and one 16-byte load in flight per thread leaves the memory system idle.
+constexpr int EU = 4;
+
+// GB300 retires about two FP64 operations per clock per SM, so a division and a square root
+// per element would make these passes FP64-pipe bound instead of HBM bound: the solvers keep
+// 1 / (den - w) per system (inv_den_kernel, once per solve) and the maxima are taken over
+// |res|^2 with one square root per block.
+
+// inv[r][i] = 1 / (den[i] - w_r)
+__global__ void inv_den_kernel(const double* __restrict__ den, const double* __restrict__ omega,
+                               double* __restrict__ inv, long long n) {
+  const long long r = blockIdx.y;
+  const double w = omega[r];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    inv[r * n + i] = 1.0 / (den[i] - w);
+}
+
+cudaError_t launch_inv_den(const double* den, const double* omega, double* inv, long long n, int nrhs,
+                           cudaStream_t st) {
+  dim3 grid(grid_for(n, 256 * 4), nrhs);
+  inv_den_kernel<<<grid, 256, 0, st>>>(den, omega, inv, n);
+  return cudaGetLastError();
+}
+
+// res = -xi - y + w x ; e = res * inv ; xnew = x + e ; rmax[r] = max |res|
+__global__ void update_kernel(const double2* __restrict__ x, const double2* __restrict__ y,
+                              const double2* __restrict__ xi, const double* __restrict__ inv,
+                              const double* __restrict__ omega, double2* __restrict__ e, double2* __restrict__ xnew,
+                              unsigned long long* rmax, long long n, long long stride) {
   const long long r = blockIdx.y;
   const double w = omega[r];
   const double2* X = x + r * stride;
   const double2* Y = y + r * stride;
   const double2* XI = xi + r * stride;
+  const double* IV = inv + r * n;
   double2* E = e + r * stride;
   double2* XN = xnew + r * stride;
   double m = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double2 xv = X[i], yv = Y[i], s = XI[i];
-    const double rr = -s.x - yv.x + w * xv.x;
-    const double ri = -s.y - yv.y + w * xv.y;
-    const double d = den[i] - w;
-    const double2 ev = make_double2(rr / d, ri / d);
-    E[i] = ev;
-    XN[i] = make_double2(xv.x + ev.x, xv.y + ev.y);
-    m = fmax(m, sqrt(rr * rr + ri * ri));
+  const long long step = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += EU * step) {
+    double2 xv[EU], yv[EU], sv[EU];
+    double dv[EU];
+#pragma unroll
+    for (int u = 0; u < EU; ++u) {
+      const long long i = i0 + u * step;
+      if (i < n) {
+        xv[u] = X[i];
+        yv[u] = Y[i];
+        sv[u] = XI[i];
+        dv[u] = IV[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < EU; ++u) {
+      const long long i = i0 + u * step;
+      if (i < n) {
+        const double rr = -sv[u].x - yv[u].x + w * xv[u].x;
+        const double ri = -sv[u].y - yv[u].y + w * xv[u].y;
+        const double2 ev = make_double2(rr * dv[u], ri * dv[u]);
+        E[i] = ev;
+        XN[i] = make_double2(xv[u].x + ev.x, xv[u].y + ev.y);
+        m = fmax(m, rr * rr + ri * ri);
+      }
+    }
   }
   __shared__ double sm[256];
   sm[threadIdx.x] = m;
@@ -44,14 +89,14 @@ __global__ void update_kernel(const double2* x, const double2* y, const double2*
     if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicMax(rmax + r, (unsigned long long)__double_as_longlong(sm[0]));
+  if (threadIdx.x == 0) atomicMax(rmax + r, (unsigned long long)__double_as_longlong(sqrt(sm[0])));
 }
 
-cudaError_t launch_update(const double2* x, const double2* y, const double2* xi, const double* den,
+cudaError_t launch_update(const double2* x, const double2* y, const double2* xi, const double* inv,
                           const double* omega, double2* e, double2* xnew, unsigned long long* rmax, long long n,
                           long long stride, int nrhs, cudaStream_t st) {
-  dim3 grid(grid_for(n, 256 * 4), nrhs);
-  update_kernel<<<grid, 256, 0, st>>>(x, y, xi, den, omega, e, xnew, rmax, n, stride);
+  dim3 grid(grid_for(n, 256 * EU), nrhs);
+  update_kernel<<<grid, 256, 0, st>>>(x, y, xi, inv, omega, e, xnew, rmax, n, stride);
   return cudaGetLastError();
 }
 
@@ -61,12 +106,28 @@ __global__ void residual_kernel(const double2* x, const double2* y, const double
   const long long r = blockIdx.y;
   const double w = omega[r];
   double m = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const long long q = r * stride + i;
-    const double2 xv = x[q], yv = y[q], s = xi[q];
-    const double rr = s.x + yv.x - w * xv.x, ri = s.y + yv.y - w * xv.y;
-    R[q] = make_double2(rr, ri);
-    m = fmax(m, sqrt(rr * rr + ri * ri));
+  const long long step = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += EU * step) {
+    double2 xv[EU], yv[EU], sv[EU];
+#pragma unroll
+    for (int u = 0; u < EU; ++u) {
+      const long long i = i0 + u * step;
+      if (i < n) {
+        const long long q = r * stride + i;
+        xv[u] = x[q];
+        yv[u] = y[q];
+        sv[u] = xi[q];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < EU; ++u) {
+      const long long i = i0 + u * step;
+      if (i < n) {
+        const double rr = sv[u].x + yv[u].x - w * xv[u].x, ri = sv[u].y + yv[u].y - w * xv[u].y;
+        R[r * stride + i] = make_double2(rr, ri);
+        m = fmax(m, rr * rr + ri * ri);
+      }
+    }
   }
   __shared__ double sm[256];
   sm[threadIdx.x] = m;
@@ -75,32 +136,45 @@ __global__ void residual_kernel(const double2* x, const double2* y, const double
     if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicMax(rmax + r, (unsigned long long)__double_as_longlong(sm[0]));
+  if (threadIdx.x == 0) atomicMax(rmax + r, (unsigned long long)__double_as_longlong(sqrt(sm[0])));
 }
 
 cudaError_t launch_residual(const double2* x, const double2* y, const double2* xi, const double* omega, double2* R,
                             unsigned long long* rmax, long long n, long long stride, int nrhs, cudaStream_t st) {
-  dim3 grid(grid_for(n, 256 * 4), nrhs);
+  dim3 grid(grid_for(n, 256 * EU), nrhs);
   residual_kernel<<<grid, 256, 0, st>>>(x, y, xi, omega, R, rmax, n, stride);
   return cudaGetLastError();
 }
 
-// x0 = -xi / (den - w)
-__global__ void guess_kernel(const double2* xi, const double* den, const double* omega, double2* x, long long n,
-                             long long stride) {
+// x0 = -xi * inv   (inv = 1 / (den - w) per system)
+__global__ void guess_kernel(const double2* xi, const double* inv, double2* x, long long n, long long stride) {
   const long long r = blockIdx.y;
-  const double w = omega[r];
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double2 s = xi[r * stride + i];
-    const double d = den[i] - w;
-    x[r * stride + i] = make_double2(-s.x / d, -s.y / d);
+  const long long step = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += EU * step) {
+    double2 sv[EU];
+    double dv[EU];
+#pragma unroll
+    for (int u = 0; u < EU; ++u) {
+      const long long i = i0 + u * step;
+      if (i < n) {
+        sv[u] = xi[r * stride + i];
+        dv[u] = inv[r * n + i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < EU; ++u) {
+      const long long i = i0 + u * step;
+      if (i < n) {
+        x[r * stride + i] = make_double2(-sv[u].x * dv[u], -sv[u].y * dv[u]);
+      }
+    }
   }
 }
 
-cudaError_t launch_guess(const double2* xi, const double* den, const double* omega, double2* x, long long n,
-                         long long stride, int nrhs, cudaStream_t st) {
-  dim3 grid(grid_for(n, 256 * 4), nrhs);
-  guess_kernel<<<grid, 256, 0, st>>>(xi, den, omega, x, n, stride);
+cudaError_t launch_guess(const double2* xi, const double* inv, double2* x, long long n, long long stride, int nrhs,
+                         cudaStream_t st) {
+  dim3 grid(grid_for(n, 256 * EU), nrhs);
+  guess_kernel<<<grid, 256, 0, st>>>(xi, inv, x, n, stride);
   return cudaGetLastError();
 }
 
@@ -110,7 +184,7 @@ __global__ void maxabs_kernel(const double2* x, unsigned long long* out, long lo
   double m = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double2 v = x[r * stride + i];
-    m = fmax(m, sqrt(v.x * v.x + v.y * v.y));
+    m = fmax(m, v.x * v.x + v.y * v.y);
   }
   __shared__ double sm[256];
   sm[threadIdx.x] = m;
@@ -119,7 +193,7 @@ __global__ void maxabs_kernel(const double2* x, unsigned long long* out, long lo
     if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicMax(out + r, (unsigned long long)__double_as_longlong(sm[0]));
+  if (threadIdx.x == 0) atomicMax(out + r, (unsigned long long)__double_as_longlong(sqrt(sm[0])));
 }
 
 cudaError_t launch_maxabs(const double2* x, unsigned long long* out, long long n, long long stride, int nrhs,
@@ -131,7 +205,7 @@ cudaError_t launch_maxabs(const double2* x, unsigned long long* out, long long n
 
 // batched dot products: out[p] = sum_i op(a_p[i]) b_p[i], op = conj or identity.
 // pass 1: fixed partition into DOT_BLOCKS chunks per pair.
-constexpr int DOT_BLOCKS = 256;
+constexpr int DOT_BLOCKS = 1024;
 __global__ void dot_pass1(const double2* const* a, const double2* const* b, int conj, long long n, double2* part) {
   const int p = blockIdx.y;
   const double2* A = a[p];
@@ -242,21 +316,30 @@ constexpr int DIIS_MAX = 16;  // history depth limit (the bordered system is at 
 // newest iterate (coefficient 1 on it).
 __global__ void diis_solve_kernel(const double2* part, double2* B, int it, int depth, int ns, int nhist,
                                   int extrapolate, double2* coef) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ns) return;
+  // one warp per system: lanes sum the partials k = lane, lane + 32, ... in order, then a fixed
+  // shuffle tree; lane 0 goes on alone
+  const int i = blockIdx.x;
+  const int lane = threadIdx.x;
   double2* Bi = B + (long long)i * depth * depth;
   const int slot = ring_slot(it, 0, depth);
   for (int j = 0; j < nhist; ++j) {
-    const int sj = ring_slot(it, j, depth);
     const long long p = (long long)j * ns + i;
     double sr = 0.0, si = 0.0;
-    for (int k = 0; k < DOT_BLOCKS; ++k) {
+    for (int k = lane; k < DOT_BLOCKS; k += 32) {
       sr += part[p * DOT_BLOCKS + k].x;
       si += part[p * DOT_BLOCKS + k].y;
     }
-    Bi[slot * depth + sj] = make_double2(sr, si);
-    Bi[sj * depth + slot] = make_double2(sr, -si);
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_down_sync(0xffffffffu, sr, o);
+      si += __shfl_down_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) {
+      const int sj = ring_slot(it, j, depth);
+      Bi[slot * depth + sj] = make_double2(sr, si);
+      Bi[sj * depth + slot] = make_double2(sr, -si);
+    }
   }
+  if (lane != 0) return;
   double2 x[DIIS_MAX + 1];
   bool good = false;
   if (extrapolate && nhist >= 2) {
@@ -330,15 +413,28 @@ __global__ void diis_solve_kernel(const double2* part, double2* B, int it, int d
 __global__ void diis_lincomb_kernel(const double2* HX, int it, int depth, const double2* c, int m, double2* out,
                                     long long n, long long stride, int nrhs) {
   const long long r = blockIdx.y;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double sr = 0.0, si = 0.0;
+  const long long step = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += EU * step) {
+    double sr[EU], si[EU];
+#pragma unroll
+    for (int u = 0; u < EU; ++u) sr[u] = si[u] = 0.0;
     for (int j = 0; j < m; ++j) {
       const double2 cc = c[(long long)j * nrhs + r];
-      const double2 x = HX[((long long)ring_slot(it, j, depth) * nrhs + r) * stride + i];
-      sr += cc.x * x.x - cc.y * x.y;
-      si += cc.x * x.y + cc.y * x.x;
+      const double2* hx = HX + ((long long)ring_slot(it, j, depth) * nrhs + r) * stride;
+      double2 x[EU];
+#pragma unroll
+      for (int u = 0; u < EU; ++u)
+        if (i0 + u * step < n) x[u] = hx[i0 + u * step];
+#pragma unroll
+      for (int u = 0; u < EU; ++u)
+        if (i0 + u * step < n) {
+          sr[u] += cc.x * x[u].x - cc.y * x[u].y;
+          si[u] += cc.x * x[u].y + cc.y * x[u].x;
+        }
     }
-    out[r * stride + i] = make_double2(sr, si);
+#pragma unroll
+    for (int u = 0; u < EU; ++u)
+      if (i0 + u * step < n) out[r * stride + i0 + u * step] = make_double2(sr[u], si[u]);
   }
 }
 
@@ -348,8 +444,8 @@ cudaError_t launch_diis_device(const double2* HE, const double2* HX, double2* B,
   if (depth > DIIS_MAX || nhist < 1 || nhist > depth || (long long)nhist * ns > 65535) return cudaErrorInvalidValue;
   dim3 g1(DOT_BLOCKS, nhist * ns);
   diis_dot_pass1<<<g1, 256, 0, st>>>(HE, it, depth, ns, n, part);
-  diis_solve_kernel<<<(ns + 31) / 32, 32, 0, st>>>(part, B, it, depth, ns, nhist, extrapolate, coef);
-  dim3 g3(grid_for(n, 256 * 4), ns);
+  diis_solve_kernel<<<ns, 32, 0, st>>>(part, B, it, depth, ns, nhist, extrapolate, coef);
+  dim3 g3(grid_for(n, 256 * EU), ns);
   diis_lincomb_kernel<<<g3, 256, 0, st>>>(HX, it, depth, coef, nhist, out, n, n, ns);
   return cudaGetLastError();
 }
@@ -379,15 +475,25 @@ cudaError_t launch_lincomb(const double2* const* v, const double2* c, int m, dou
 
 // y = a * x + b * y  (complex a, b), one vector
 __global__ void axpby_kernel(double2 a, const double2* x, double2 b, double2* y, long long n) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double2 xv = x[i], yv = y[i];
-    y[i] = make_double2(a.x * xv.x - a.y * xv.y + b.x * yv.x - b.y * yv.y,
-                        a.x * xv.y + a.y * xv.x + b.x * yv.y + b.y * yv.x);
+  const long long step = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += EU * step) {
+    double2 xv[EU], yv[EU];
+#pragma unroll
+    for (int u = 0; u < EU; ++u)
+      if (i0 + u * step < n) {
+        xv[u] = x[i0 + u * step];
+        yv[u] = y[i0 + u * step];
+      }
+#pragma unroll
+    for (int u = 0; u < EU; ++u)
+      if (i0 + u * step < n)
+        y[i0 + u * step] = make_double2(a.x * xv[u].x - a.y * xv[u].y + b.x * yv[u].x - b.y * yv[u].y,
+                                        a.x * xv[u].y + a.y * xv[u].x + b.x * yv[u].y + b.y * yv[u].x);
   }
 }
 
 cudaError_t launch_axpby(double2 a, const double2* x, double2 b, double2* y, long long n, cudaStream_t st) {
-  axpby_kernel<<<grid_for(n, 256 * 4), 256, 0, st>>>(a, x, b, y, n);
+  axpby_kernel<<<grid_for(n, 256 * EU), 256, 0, st>>>(a, x, b, y, n);
   return cudaGetLastError();
 }
 

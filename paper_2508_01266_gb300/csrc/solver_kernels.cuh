@@ -6,13 +6,17 @@
 
 namespace lrcc {
 
-cudaError_t launch_update(const double2* x, const double2* y, const double2* xi, const double* den,
+// inv[r][i] = 1 / (den[i] - omega[r]) for nrhs systems (inv: nrhs x n doubles)
+cudaError_t launch_inv_den(const double* den, const double* omega, double* inv, long long n, int nrhs,
+                           cudaStream_t st);
+// inv as from launch_inv_den (per-system stride n)
+cudaError_t launch_update(const double2* x, const double2* y, const double2* xi, const double* inv,
                           const double* omega, double2* e, double2* xnew, unsigned long long* rmax, long long n,
                           long long stride, int nrhs, cudaStream_t st);
 cudaError_t launch_residual(const double2* x, const double2* y, const double2* xi, const double* omega, double2* r,
                             unsigned long long* rmax, long long n, long long stride, int nrhs, cudaStream_t st);
-cudaError_t launch_guess(const double2* xi, const double* den, const double* omega, double2* x, long long n,
-                         long long stride, int nrhs, cudaStream_t st);
+cudaError_t launch_guess(const double2* xi, const double* inv, double2* x, long long n, long long stride, int nrhs,
+                         cudaStream_t st);
 cudaError_t launch_maxabs(const double2* x, unsigned long long* out, long long n, long long stride, int nrhs,
                           cudaStream_t st);
 size_t dot_partial_elems(int npairs);
