@@ -409,6 +409,15 @@ __device__ __forceinline__ bool wait_or_fail(uint32_t bar, uint32_t parity, vola
   return false;
 }
 
+// 16 consecutive 32-bit TMEM columns of this warp's 32 lanes (one row per lane)
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta));
+}
+
 __device__ __forceinline__ void decode_tile(const PGemmArgs& g, long long tile, int& rhs, int& batch, int& mt,
                                             int& nt) {
   rhs = (int)(tile % g.nrhs);
@@ -616,54 +625,43 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
       if (ch == nch - 1) prefetch_c(tile + gridDim.x);
       const int m = mt * P_BM + q * 32 + lane;
       double2* Cp = g.C + rhs * g.sC + g.coff[batch];
+      // 32 complex columns per step: the 32 FP64 loads of the row segment are issued first (in
+      // flight together), then the accumulator columns are read from TMEM in two halves
 #pragma unroll 1
-      for (int c0 = 0; c0 < P_BNR; c0 += 32) {
-        uint32_t r[32];
-        if (total > 0) {
-          const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * P_BNR + c0);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-              "[%16];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                "=r"(r[15])
-              : "r"(ta));
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-              "[%16];"
-              : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-                "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-                "=r"(r[30]), "=r"(r[31])
-              : "r"(ta + 16u));
-          asm volatile("tcgen05.wait::ld.sync.aligned;");
-        } else {
+      for (int c0 = 0; c0 < P_BNR; c0 += 64) {
+        const bool row = m < g.M && (total > 0 || g.epi == 1);
+        const int nb = nt * (P_BNR / 2) + c0 / 2;
+        const int cnt = row ? min(32, g.N - nb) : 0;
+        double2* cp = Cp + (long long)m * g.ldc + nb;
+        double2 cv[32];
+        if (g.epi == 0) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) r[j] = 0u;
+          for (int j = 0; j < 32; ++j)
+            if (j < cnt) cv[j] = cp[j];
         }
-        if (m < g.M && (total > 0 || g.epi == 1)) {
-          const int nb = nt * (P_BNR / 2) + c0 / 2;
-          const int cnt = min(16, g.N - nb);
-          if (g.epi == 0) {
-            // all loads of the row segment first, then the stores (no load waits on a store)
-            double2* cp = Cp + (long long)m * g.ldc + nb;
-            double2 cv[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (j < cnt) cv[j] = cp[j];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              if (j >= cnt) break;
-              const double ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
-              cv[j].x += g.ar * ar - g.ai * ai;
-              cv[j].y += g.ar * ai + g.ai * ar;
-              cp[j] = cv[j];
-            }
+        for (int h = 0; h < 2; ++h) {
+          uint32_t r[32];
+          if (total > 0) {
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * P_BNR + c0 + 32 * h);
+            tmem_ld16(ta, r);
+            tmem_ld16(ta + 16u, r + 16);
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
           } else {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              if (j >= cnt) break;
-              const int n = nb + j;
-              const double ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
+            for (int j = 0; j < 32; ++j) r[j] = 0u;
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int jj = 16 * h + j;
+            if (jj >= cnt) break;
+            const double ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
+            if (g.epi == 0) {
+              cv[jj].x += g.ar * ar - g.ai * ai;
+              cv[jj].y += g.ar * ai + g.ai * ar;
+              cp[jj] = cv[jj];
+            } else {
+              const int n = nb + jj;
               const double vr = g.ar * ar - g.ai * ai, vi = g.ar * ai + g.ai * ar;
               const int a = m / g.ep2, c = m - a * g.ep2;
               const int bb = n / g.ep3, d = n - bb * g.ep3;
