@@ -106,12 +106,12 @@ class RCC:
         return Lt, ft
 
     # -- residual ----------------------------------------------------------------
-    def residual(self, t1, t2, h=None, blocks=None):
+    def residual(self, t1, t2, h=None, blocks=None, singles=None):
         """Closed-shell CCSD residual (supercell units).
 
         Returns (omega1[k,i,a], omega2[ki,kj,ka,i,j,a,b]).  With `blocks` (a list of
         (ki, kj, ka)), only those doubles blocks are computed (the others stay zero)
-        and the singles are skipped; used to sample large problems.
+        and the singles are skipped unless `singles` is True; used to sample large problems.
         """
         nk, o = self.nk, self.o
         O, Vs = slice(0, o), slice(o, self.n)
@@ -229,7 +229,7 @@ class RCC:
         r2 = torch.stack([torch.stack([torch.stack(r2b[ki][kj]) for kj in K]) for ki in K])
 
         r1b = [torch.zeros((o, self.v), dtype=DT) for _ in K]
-        if blocks is None:
+        if (blocks is None) if singles is None else singles:
             for k in K:
                 r = ft[k][Vs, O].T.clone()
                 for km in K:
@@ -278,7 +278,7 @@ class RCC:
                     out[ki, kj, ka] = 0.5 * (x2[ki, kj, ka] + x2[kj, ki, self.kb(ki, kj, ka)].permute(1, 0, 3, 2))
         return out
 
-    def jacobian(self, t1, t2, x1, x2, h=None, blocks=None):
+    def jacobian(self, t1, t2, x1, x2, h=None, blocks=None, singles=None):
         """A.X by the exact 5-point stencil of the residual (supercell units).
 
         The stencil f'(0) = [f(-2s) - 8 f(-s) + 8 f(s) - f(2s)] / (12 s) is exact for
@@ -286,7 +286,7 @@ class RCC:
         """
         s = max(float(torch.max(torch.abs(x1))) if x1.numel() else 0.0, float(torch.max(torch.abs(x2))), 1e-300)
         hh = 1e-2 / s
-        r = [self.residual(t1 + c * hh * x1, t2 + c * hh * x2, h, blocks) for c in (-2.0, -1.0, 1.0, 2.0)]
+        r = [self.residual(t1 + c * hh * x1, t2 + c * hh * x2, h, blocks, singles) for c in (-2.0, -1.0, 1.0, 2.0)]
         y1 = (r[0][0] - 8.0 * r[1][0] + 8.0 * r[2][0] - r[3][0]) / (12.0 * hh)
         y2 = (r[0][1] - 8.0 * r[1][1] + 8.0 * r[2][1] - r[3][1]) / (12.0 * hh)
         return y1, y2

@@ -88,21 +88,59 @@ def test_zero_and_pair_symmetry(lr):
                 assert np.allclose(y[ki, kj, ka], y[kj, ki, kb(ki, kj, ka)].transpose(1, 0, 3, 2), rtol=0, atol=1e-13)
 
 
+def _host_mem_available_gb():
+    with open("/proc/meminfo") as f:
+        for line in f:
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) / 2**20
+    return 0.0
+
+
+# ten doubles blocks (ki, kj, ka) of the Nk=5 workload: diagonal, self-paired and generic ones
+C2_BLOCKS = [(0, 0, 0), (1, 3, 4), (4, 2, 1), (2, 2, 4), (3, 1, 0), (0, 4, 2), (1, 1, 1), (2, 3, 0),
+             (4, 4, 3), (3, 0, 3)]
+
+
 def test_c2_sampled_blocks(lr):
-    """Full C2 size (Nk=5, o=8, v=40, naux=160): doubles blocks sampled one by one."""
+    """Full C2 size (Nk=5, o=8, v=40, naux=160): singles and ten doubles blocks of A.X against
+    the oracle's exact stencil (doubles blocks computed one by one)."""
     c = CONFIGS["c2"]
     nk, o, v, Q = c["nk"], c["nocc"], c["nvir"], c["naux"]
     p, prob, t1, t2 = _setup(lr, nk, o, v, Q, seed=1266, sigma=0.02, tscale=0.01)
     x1, x2 = random_amplitudes(nk, o, v, seed=5, scale1=1.0, scale2=1.0)
     dev = torch.device("cuda")
     y1, y2 = prob.jacobian_apply(torch.as_tensor(x1, device=dev)[None], torch.as_tensor(x2 * nk, device=dev)[None])
+    prob.close()
     R = rcc.RCC(p)
     T = torch.as_tensor
-    blocks = [(0, 0, 0), (1, 3, 4), (4, 2, 1)]
-    a1, a2 = R.jacobian(T(t1), T(t2), T(x1), T(x2), blocks=blocks)
+    a1, a2 = R.jacobian(T(t1), T(t2), T(x1), T(x2), blocks=C2_BLOCKS, singles=True)
+    assert _rel(y1[0].cpu().numpy(), a1.numpy()) < TOL
     y2 = y2[0].cpu().numpy()
-    for bk in blocks:
+    for bk in C2_BLOCKS:
         assert _rel(y2[bk], nk * a2[bk].numpy()) < TOL, bk
+
+
+def test_c2_transpose_vs_oracle(lr):
+    """Full C2 size, transposed product: singles and the same ten doubles blocks against the
+    oracle's reverse-mode gradient of <y, Omega(t)> over the full residual.  The oracle's
+    gradient of the full Nk=5 residual holds about 55 GB of host memory."""
+    if _host_mem_available_gb() < 96:
+        pytest.skip("the oracle's full-residual gradient needs about 55 GB of free host memory")
+    c = CONFIGS["c2"]
+    nk, o, v, Q = c["nk"], c["nocc"], c["nvir"], c["naux"]
+    p, prob, t1, t2 = _setup(lr, nk, o, v, Q, seed=1266, sigma=0.02, tscale=0.01)
+    x1, x2 = random_amplitudes(nk, o, v, seed=6, scale1=1.0, scale2=1.0)
+    dev = torch.device("cuda")
+    z1, z2 = prob.jacobian_apply(torch.as_tensor(x1, device=dev)[None], torch.as_tensor(x2 * nk, device=dev)[None],
+                                 transpose=True)
+    prob.close()
+    R = rcc.RCC(p)
+    T = torch.as_tensor
+    b1, b2 = R.transpose(T(t1), T(t2), T(x1), T(x2 * nk * nk))  # paper units: A_paper^T = D_in A^T D_out
+    assert _rel(z1[0].cpu().numpy(), b1.numpy()) < TOL
+    z2 = z2[0].cpu().numpy()
+    for bk in C2_BLOCKS:
+        assert _rel(z2[bk], b2[bk].numpy() / nk) < TOL, bk
 
 
 def test_graph_replay_bitwise_and_invalidation(lr):

@@ -330,12 +330,12 @@ def _p3_deviation():
     return abs(lhs - rhs) / abs(lhs)
 
 
-def _jacobian_three_point(self, t1, t2, x1, x2, h=None, blocks=None):
+def _jacobian_three_point(self, t1, t2, x1, x2, h=None, blocks=None, singles=None):
     # central difference [f(s) - f(-s)] / 2s: not exact for the quartic CCSD residual
     s = max(float(torch.max(torch.abs(x1))), float(torch.max(torch.abs(x2))), 1e-300)
     hh = 1e-2 / s
-    rp = self.residual(t1 + hh * x1, t2 + hh * x2, h, blocks)
-    rm = self.residual(t1 - hh * x1, t2 - hh * x2, h, blocks)
+    rp = self.residual(t1 + hh * x1, t2 + hh * x2, h, blocks, singles)
+    rm = self.residual(t1 - hh * x1, t2 - hh * x2, h, blocks, singles)
     return (rp[0] - rm[0]) / (2 * hh), (rp[1] - rm[1]) / (2 * hh)
 
 

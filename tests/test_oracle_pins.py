@@ -90,6 +90,8 @@ def test_closed_shell_vs_spinorb(nk, o, v, seed, tr):
     _, s2 = R.residual(T(t1k), T(t2k), blocks=blocks)
     for bk in blocks:
         assert torch.allclose(s2[bk], b2[bk], atol=1e-15)
+    s1, _ = R.residual(T(t1k), T(t2k), blocks=blocks, singles=True)
+    assert torch.allclose(s1, b1, atol=1e-15)
 
 
 # P2 ---------------------------------------------------------------------------
