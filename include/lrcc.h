@@ -286,7 +286,10 @@ lrcc_status lrcc_plan_gemm(const lrcc_plan* h, int32_t idx, int32_t* ints, int64
  * within 8192 complex terms, the partials of K splits being summed in FP64.  EINVAL for a
  * bad handle, index or precision. */
 lrcc_status lrcc_plan_choice(const lrcc_plan* h, int32_t idx, int32_t precision, int32_t* out);
-/* ints int32[18]: src(kind nk n0..n3) dst(kind nk n0..n3) pi0..pi3 arS arD; offs int64[2]. */
+/* ints int32[19]: src(kind nk n0..n3) dst(kind nk n0..n3) pi0..pi3 arS arD store; offs int64[2].
+ * store = 1: the permutation overwrites its destination (dst = alpha * src) instead of adding
+ * to it; the plan sets it where the permutation is the first writer of a scratch buffer and
+ * covers all of it, in place of zeroing the buffer first. */
 lrcc_status lrcc_plan_perm(const lrcc_plan* h, int32_t idx, int32_t* ints, int64_t* offs, double* alpha);
 /* ints int32[5]: nb R C arS arD; offs int64[2]. */
 lrcc_status lrcc_plan_btrans(const lrcc_plan* h, int32_t idx, int32_t* ints, int64_t* offs, double* alpha);

@@ -39,6 +39,7 @@ struct PermArgs {
   double2* D;
   long long sS, sD;
   double ar, ai;
+  int store = 0;  // 1: D = alpha S (D is not read), 0: D += alpha S
 };
 
 struct BTransArgs {

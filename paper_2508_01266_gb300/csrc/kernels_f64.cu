@@ -368,7 +368,7 @@ __global__ void perm_kernel(PermArgs p) {
     const long long os = lay_off(p.skind, p.snk, p.sn, dk[p.pi[0]], dk[p.pi[1]], dk[p.pi[2]], di[p.pi[0]],
                                  di[p.pi[1]], di[p.pi[2]], di[p.pi[3]]);
     const double2 s = S[os];
-    double2 d = D[od];
+    double2 d = p.store ? make_double2(0.0, 0.0) : D[od];
     d.x += p.ar * s.x - p.ai * s.y;
     d.y += p.ar * s.y + p.ai * s.x;
     D[od] = d;
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(256) perm_slab_kernel(SlabArgs a) {
       const int x = e % nx, y = e / nx;
       const double2 s = slab[y * pitch + x];
       double2* dp = D + dbase + x * a.dsx + y * a.dsy;
-      double2 d = *dp;
+      double2 d = p.store ? make_double2(0.0, 0.0) : *dp;
       d.x += p.ar * s.x - p.ai * s.y;
       d.y += p.ar * s.y + p.ai * s.x;
       *dp = d;

@@ -1179,6 +1179,7 @@ Plan build_plan(const Dims& d, int64_t ws_budget) {
   }
 
   pack_scratch(P, {&P.jac, &P.xi, &P.egrad, &P.omega0, &P.tgrad});
+  for (Program* pr : {&P.jac, &P.xi, &P.egrad, &P.omega0, &P.tgrad}) fold_first_writes(P, *pr);
 
   double tot = 0;
   for (const Op& op : J.ops)
@@ -1223,6 +1224,8 @@ std::string validate_plan(const Plan& P, const Program& pr) {
       if (p.src.size() != p.dst.size()) return "perm " + p.tag + ": sizes";
       if (!(e = chk(p.arS, p.offS, p.src.size(), "perm src " + p.tag)).empty()) return e;
       if (!(e = chk(p.arD, p.offD, p.dst.size(), "perm dst " + p.tag)).empty()) return e;
+      if (p.arS == p.arD && p.offS < p.offD + p.dst.size() && p.offD < p.offS + p.src.size())
+        return "perm " + p.tag + ": source and destination overlap";
     } else if (op.kind == OP_BTRANS) {
       const BTrans& t = P.btrans[op.idx];
       int64_t n = (int64_t)t.nb * t.R * t.C;
@@ -1237,6 +1240,36 @@ std::string validate_plan(const Plan& P, const Program& pr) {
     }
   }
   return "";
+}
+
+void fold_first_writes(Plan& P, Program& pr) {
+  std::vector<Op> out;
+  out.reserve(pr.ops.size());
+  for (const Op& op : pr.ops) {
+    bool folded = false;
+    if (op.kind == OP_PERM && !P.perms[op.idx].store) {
+      const Perm p = P.perms[op.idx];
+      // the zero ops directly ahead of this one (a buffer is zeroed just before its first use)
+      for (int j = (int)out.size() - 1; j >= 0 && out[j].kind == OP_ZERO; --j) {
+        const ZeroSpec& z = P.zeros[out[j].idx];
+        const bool covers = p.arD == z.arena && p.offD == z.off && p.dst.size() == z.n;
+        const bool reads = p.arS == z.arena && p.offS < z.off + z.n && z.off < p.offS + p.src.size();
+        if (covers && !reads) {
+          Perm s = p;
+          s.store = 1;
+          P.perms.push_back(s);
+          Op o2 = op;
+          o2.idx = (int)P.perms.size() - 1;
+          out.erase(out.begin() + j);
+          out.push_back(o2);
+          folded = true;
+          break;
+        }
+      }
+    }
+    if (!folded) out.push_back(op);
+  }
+  pr.ops = out;
 }
 
 // ---------------------------------------------------------------------------
@@ -1395,6 +1428,7 @@ Program transpose_program(Plan& P, const Program& fwd) {
     }
   }
   (void)pending;
+  fold_first_writes(P, out);
   return out;
 }
 

@@ -61,13 +61,15 @@ struct Gemm {
 };
 
 // dst[L_dst(e)] += alpha * src[L_src(e o pi)], e over the destination elements;
-// source slot s takes destination slot pi[s].
+// source slot s takes destination slot pi[s].  store == 1: dst[L_dst(e)] = alpha * src[...]
+// (the destination is not read; set by fold_first_writes).
 struct Perm {
   Layout src, dst;
   int pi[4] = {0, 1, 2, 3};
   double ar = 1.0, ai = 0.0;
   int arS = AR_FIX, arD = AR_FIX;
   int64_t offS = 0, offD = 0;
+  int store = 0;
   std::string tag;
 };
 
@@ -137,5 +139,10 @@ std::string validate_plan(const Plan& P, const Program& pr);
 // Transposed op list of the Jacobian program (reverse order, transposed ops).
 // New GEMM/PERM/BTRANS entries are appended to the plan's tables.
 Program transpose_program(Plan& P, const Program& fwd);
+
+// A scratch buffer is zeroed just before its first use.  Where that use is a permutation that
+// writes every element of exactly that buffer and does not read it, the permutation stores
+// instead of accumulating (a copy of it with store = 1) and the zero op is dropped.
+void fold_first_writes(Plan& P, Program& pr);
 
 }  // namespace lrcc

@@ -124,9 +124,10 @@ lrcc_status lrcc_plan_perm(const lrcc_plan* h, int32_t idx, int32_t* ints, int64
   if (!h || idx < 0 || idx >= (int32_t)h->P.perms.size()) return LRCC_EINVAL;
   const Perm& p = h->P.perms[idx];
   if (ints) {
-    int32_t v[18] = {p.src.kind, p.src.nk, p.src.n[0], p.src.n[1], p.src.n[2], p.src.n[3],
+    int32_t v[19] = {p.src.kind, p.src.nk, p.src.n[0], p.src.n[1], p.src.n[2], p.src.n[3],
                      p.dst.kind, p.dst.nk, p.dst.n[0], p.dst.n[1], p.dst.n[2], p.dst.n[3],
-                     p.pi[0],    p.pi[1],  p.pi[2],    p.pi[3],    p.arS,      p.arD};
+                     p.pi[0],    p.pi[1],  p.pi[2],    p.pi[3],    p.arS,      p.arD,
+                     p.store};
     std::memcpy(ints, v, sizeof(v));
   }
   if (offs) {

@@ -843,6 +843,7 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
       a.sS = op.fixed_only ? 0 : stride[p.arS];
       a.sD = op.fixed_only ? 0 : stride[p.arD];
       a.ar = p.ar; a.ai = p.ai;
+      a.store = p.store;
       e = launch_perm_f64(a, nr, st);
       ++launches;
     } else if (op.kind == OP_BTRANS) {

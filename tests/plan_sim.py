@@ -71,7 +71,7 @@ class PlanView:
                 ops.append(("gemm", fixed, dict(ints=ints.copy(), lds=lds.copy(), alpha=complex(al[0], al[1]),
                                                 coff=coff, sbeg=sbeg, aoff=aoff, boff=boff)))
             elif kind == 1:
-                ints = np.zeros(18, np.int32)
+                ints = np.zeros(19, np.int32)
                 offs = np.zeros(2, np.int64)
                 al = np.zeros(2)
                 lib.lrcc_plan_perm(h, idx, _p(ints, I32P), _p(offs, I64P), _p(al, F64P))
@@ -171,7 +171,12 @@ def run(ops, arenas):
             os_ = layout_offsets(skind, snk, sn, sk[0], sk[1], sk[2], si[0], si[1], si[2], si[3])
             Dst, Src = arenas[arD], arenas[arS]
             vals = d["alpha"] * Src[offS + os_.ravel()]
-            np.add.at(Dst, offD + od.ravel(), vals)
+            if v[18]:  # store: every destination element written once, old values not read
+                idx = offD + od.ravel()
+                assert np.unique(idx).size == idx.size
+                Dst[idx] = vals
+            else:
+                np.add.at(Dst, offD + od.ravel(), vals)
         elif kind == "zero":
             arenas[d["arena"]][d["off"]:d["off"] + d["n"]] = 0
         elif kind == "btrans":

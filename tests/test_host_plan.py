@@ -42,6 +42,24 @@ def test_plan_validates_for_workloads(lib, cfg):
     assert pv.flops[0] > 0 and pv.flops[1] > 0
 
 
+def test_first_writes_fold_zeroing_at_c2(lib):
+    """At the Nk=5 workload the permutations that are first writers of a whole scratch buffer
+    store into it (no zero op ahead of them): five in the Jacobian program, nine in its
+    transpose.  A store permutation never reads the buffer it writes."""
+    c = CONFIGS["c2"]
+    pv = plan_sim.PlanView(lib, c["nk"], c["nocc"], c["nvir"], c["naux"], 1 << 30)
+    for which, want in ((1, 5), (2, 9)):
+        ops = pv.programs[which]
+        stores = [d for k, _, d in ops if k == "perm" and d["ints"][18]]
+        assert len(stores) == want
+        for d in stores:
+            v = d["ints"]
+            n = int(np.prod(v[8:12])) * int(v[7]) ** 3
+            offS, offD = map(int, d["offs"])
+            assert v[17] == 3  # scratch
+            assert v[16] != v[17] or offS + n <= offD or offD + n <= offS
+
+
 def _sim_setup(lib, prob, t1, t2sc, ws):
     nk, o, v, Q = prob.nk, prob.nocc, prob.nvir, prob.naux
     pv = plan_sim.PlanView(lib, nk, o, v, Q, ws)
