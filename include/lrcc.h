@@ -272,8 +272,10 @@ lrcc_status lrcc_plan_validate(const lrcc_plan* h, char* msg, int32_t len);
 /* kind_idx_fixed int32[3]: kind (0 GEMM, 1 permute, 2 2-D transpose, 3 zero a
  * scratch range), table index, fixed-only flag. */
 lrcc_status lrcc_plan_op(const lrcc_plan* h, int32_t which, int32_t i, int32_t* kind_idx_fixed);
-/* ints int32[15]: M N K ta tb arA arB arC epi ep0..ep3 nbatch nseg; lds int64[3];
- * alpha double[2]; coff int64[nbatch], sbeg int32[nbatch+1], aoff/boff int64[nseg]. */
+/* ints int32[16]: M N K ta tb arA arB arC epi ep0..ep3 nbatch nseg store; lds int64[3];
+ * alpha double[2]; coff int64[nbatch], sbeg int32[nbatch+1], aoff/boff int64[nseg].
+ * store = 1: C = alpha * sum instead of C += alpha * sum (the GEMM is the first writer of a
+ * scratch buffer and covers all of it, in place of zeroing the buffer first). */
 lrcc_status lrcc_plan_gemm(const lrcc_plan* h, int32_t idx, int32_t* ints, int64_t* lds, double* alpha,
                            int64_t* coff, int32_t* sbeg, int64_t* aoff, int64_t* boff);
 /* Kernel the executor launches by default for GEMM op idx at a precision (0 FP64,

@@ -28,6 +28,8 @@ struct GemmArgs {
   // tensor-core kernel only: the launch computes C^T = B^T A^T (operands and M, N swapped
   // by the caller) and the epilogue writes element (m, n) of the launch to C[n][m]
   int swap = 0;
+  // epi == 0: 1 = C is overwritten (C = alpha AB; its old contents are not read), 0 = C += alpha AB
+  int store = 0;
 };
 
 struct PermArgs {
@@ -110,6 +112,8 @@ struct PGemmArgs {
   // tile with more is done in chunks, each added into the FP64 destination by the epilogue
   // (accumulating epilogue only)
   int kchunk = 1 << 30;
+  // epi == 0: 1 = the first (or only) chunk overwrites C, later chunks add; 0 = every chunk adds
+  int store = 0;
 };
 long long packed_bytes(int mode, int R, int K);
 cudaError_t launch_pack(const PackArgs& p, int prec, int nrhs, cudaStream_t st);

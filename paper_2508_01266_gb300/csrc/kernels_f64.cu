@@ -205,7 +205,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       const double vr = g.ar * ur - g.ai * ui;
       const double vi = g.ar * ui + g.ai * ur;
       if (g.epi == 0) {
-        double2 cv = Cp[addr];
+        double2 cv = g.store ? make_double2(0.0, 0.0) : Cp[addr];
         cv.x += vr;
         cv.y += vi;
         Cp[addr] = cv;
@@ -238,7 +238,7 @@ __global__ void split_reduce_kernel(GemmArgs g) {
     double2* Cp = Cb + g.coff[batch];
     if (g.epi == 0) {
       double2* cp = Cp + (long long)m * g.ldc + n;
-      double2 cv = *cp;
+      double2 cv = g.store ? make_double2(0.0, 0.0) : *cp;
       cv.x += vr;
       cv.y += vi;
       *cp = cv;

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(SK_THREADS) skinny_k_kernel(GemmArgs g, int nc
   double2 cv[MM];  // all loads first, then the stores (no load waits on a store)
 #pragma unroll
   for (int m = 0; m < MM; ++m)
-    if (m < M) cv[m] = Cp[(long long)m * g.ldc + n];
+    if (m < M) cv[m] = g.store ? make_double2(0.0, 0.0) : Cp[(long long)m * g.ldc + n];
 #pragma unroll
   for (int m = 0; m < MM; ++m) {
     if (m >= M) break;

@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(GemmArgs g, int* er
           if (j >= cnt) break;
           const int n = n0 + c0 / 2 + j;
           const int mo = g.swap ? n : m, no = g.swap ? m : n;  // element of the original C
-          cv[j] = Cp[(long long)mo * g.ldc + no];
+          cv[j] = g.store ? make_double2(0.0, 0.0) : Cp[(long long)mo * g.ldc + no];
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {

@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_kernel(PGemmArgs g, int
           double2 cv[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j)
-            if (j < cnt) cv[j] = cp[j];
+            if (j < cnt) cv[j] = g.store ? make_double2(0.0, 0.0) : cp[j];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             if (j >= cnt) break;
@@ -587,11 +587,12 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
   } else if (warp >= 2) {
     // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31.  The read-modify-write of the
     // FP64 destination dominates short contractions, so the C rows of this CTA's next
-    // tile are prefetched into L2 while the current tile drains, and each step keeps 16
-    // complex loads of a row in flight.
+    // tile are prefetched into L2 while the current tile drains, and each step keeps 32
+    // complex loads of a row in flight.  A storing GEMM does not read C (its first chunk
+    // overwrites, later chunks add to what the first wrote).
     const int q = warp & 3;
     auto prefetch_c = [&](long long tl) {
-      if (g.epi != 0 || tl >= ntiles) return;
+      if (g.epi != 0 || g.store || tl >= ntiles) return;
       int prhs, pbatch, pmt, pnt;
       decode_tile(g, tl, prhs, pbatch, pmt, pnt);
       const int pm = pmt * P_BM + q * 32 + lane;
@@ -628,8 +629,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
       // 32 complex columns per step: the 32 FP64 loads of the row segment are issued first (in
       // flight together), then the accumulator columns are read from TMEM in two halves
 #pragma unroll 1
+      const bool st = g.store && ch == 0;
       for (int c0 = 0; c0 < P_BNR; c0 += 64) {
-        const bool row = m < g.M && (total > 0 || g.epi == 1);
+        const bool row = m < g.M && (total > 0 || g.epi == 1 || st);
         const int nb = nt * (P_BNR / 2) + c0 / 2;
         const int cnt = row ? min(32, g.N - nb) : 0;
         double2* cp = Cp + (long long)m * g.ldc + nb;
@@ -637,7 +639,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) tcp_gemm_persistent(PGemmArgs g,
         if (g.epi == 0) {
 #pragma unroll
           for (int j = 0; j < 32; ++j)
-            if (j < cnt) cv[j] = cp[j];
+            if (j < cnt) cv[j] = st ? make_double2(0.0, 0.0) : cp[j];
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {

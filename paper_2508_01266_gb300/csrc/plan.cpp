@@ -82,9 +82,10 @@ struct B {
 
   int64_t alloc(int ar, int64_t n) {
     int64_t off = P.arena_size[ar];
+    const int64_t used = n;
     n = (n + 31) / 32 * 32;  // 512-byte alignment of every buffer
     P.arena_size[ar] += n;
-    if (ar == AR_SCR) P.scr_bufs.push_back({off, n});
+    if (ar == AR_SCR) P.scr_bufs.push_back({off, n, used});
     return off;
   }
   T4 t4(int ar, int kind, int a, int b, int c, int d) {
@@ -313,7 +314,7 @@ void pack_scratch(Plan& P, const std::vector<Program*>& progs) {
   std::vector<std::vector<int>> zlast(progs[0]->ops.size());
   for (int b = 0; b < nb; ++b) {
     if (prog_of[b] < 0) continue;
-    P.zeros.push_back({AR_SCR, place[b], bufs[b].n});
+    P.zeros.push_back({AR_SCR, place[b], bufs[b].n, bufs[b].used});
     const int zi = (int)P.zeros.size() - 1;
     zfirst[prog_of[b]][first[b]].push_back(zi);
     if (prog_of[b] == 0) zlast[last[b]].push_back(zi);
@@ -1242,17 +1243,64 @@ std::string validate_plan(const Plan& P, const Program& pr) {
   return "";
 }
 
+// True when the C tiles of g (all batch entries) cover [off, off + n) exactly, each element once.
+static bool gemm_covers(const Gemm& g, int64_t off, int64_t n) {
+  if (g.epi != 0 || (int64_t)g.M * g.N * g.nbatch() != n) return false;
+  std::vector<std::pair<int64_t, int64_t>> iv;  // row segments [start, end)
+  iv.reserve((size_t)g.M * g.nbatch());
+  for (int b = 0; b < g.nbatch(); ++b) {
+    if (g.sbeg[b + 1] <= g.sbeg[b]) return false;  // an empty entry: its kernels may skip the tile
+    for (int m = 0; m < g.M; ++m) iv.push_back({g.coff[b] + (int64_t)m * g.ldc, g.coff[b] + (int64_t)m * g.ldc + g.N});
+  }
+  std::sort(iv.begin(), iv.end());
+  int64_t at = off;
+  for (const auto& x : iv) {
+    if (x.first != at) return false;  // a gap or an overlap
+    at = x.second;
+  }
+  return at == off + n;
+}
+
+// True when any operand segment of g lies (partly) in arena ar, [off, off + n).
+static bool gemm_reads(const Gemm& g, int ar, int64_t off, int64_t n) {
+  const int64_t rA = g.ta ? g.K : g.M, cA = g.ta ? g.M : g.K;
+  const int64_t rB = g.tb ? g.N : g.K, cB = g.tb ? g.K : g.N;
+  const int64_t extA = (rA - 1) * g.lda + cA, extB = (rB - 1) * g.ldb + cB;
+  for (size_t s = 0; s < g.aoff.size(); ++s) {
+    if (g.arA == ar && g.aoff[s] < off + n && off < g.aoff[s] + extA) return true;
+    if (g.arB == ar && g.boff[s] < off + n && off < g.boff[s] + extB) return true;
+  }
+  return false;
+}
+
 void fold_first_writes(Plan& P, Program& pr) {
   std::vector<Op> out;
   out.reserve(pr.ops.size());
   for (const Op& op : pr.ops) {
     bool folded = false;
+    if (op.kind == OP_GEMM && !op.fixed_only && !P.gemms[op.idx].store) {
+      for (int j = (int)out.size() - 1; j >= 0 && out[j].kind == OP_ZERO; --j) {
+        const ZeroSpec& z = P.zeros[out[j].idx];
+        const Gemm& g = P.gemms[op.idx];
+        if (g.arC == z.arena && gemm_covers(g, z.off, z.used) && !gemm_reads(g, z.arena, z.off, z.n)) {
+          Gemm s = g;
+          s.store = 1;
+          P.gemms.push_back(s);
+          Op o2 = op;
+          o2.idx = (int)P.gemms.size() - 1;
+          out.erase(out.begin() + j);
+          out.push_back(o2);
+          folded = true;
+          break;
+        }
+      }
+    }
     if (op.kind == OP_PERM && !P.perms[op.idx].store) {
       const Perm p = P.perms[op.idx];
       // the zero ops directly ahead of this one (a buffer is zeroed just before its first use)
       for (int j = (int)out.size() - 1; j >= 0 && out[j].kind == OP_ZERO; --j) {
         const ZeroSpec& z = P.zeros[out[j].idx];
-        const bool covers = p.arD == z.arena && p.offD == z.off && p.dst.size() == z.n;
+        const bool covers = p.arD == z.arena && p.offD == z.off && p.dst.size() == z.used;
         const bool reads = p.arS == z.arena && p.offS < z.off + z.n && z.off < p.offS + p.src.size();
         if (covers && !reads) {
           Perm s = p;

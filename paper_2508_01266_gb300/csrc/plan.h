@@ -44,6 +44,7 @@ int64_t layout_offset(const Layout& L, int k1, int k2, int k3, int i1, int i2, i
 //   epi == 0:  C[m*ldc + n]
 //   epi == 1:  m = a*nc + c, n = b*nd + d  ->  C[((a*nb + b)*nc + c)*nd + d] = (stored,
 //              not accumulated: W-block workspace slots are reused across chunks)
+//   store == 1 (epi == 0 only): C = alpha * sum (C is not read; set by fold_first_writes)
 struct Gemm {
   int M = 0, N = 0, K = 0;
   int ta = 0, tb = 0;
@@ -52,6 +53,7 @@ struct Gemm {
   int arA = AR_FIX, arB = AR_FIX, arC = AR_FIX;
   int epi = 0;
   int ep[4] = {0, 0, 0, 0};  // na, nb, nc, nd for epi == 1
+  int store = 0;
   std::vector<int64_t> coff;       // per batch
   std::vector<int32_t> sbeg;       // per batch + 1
   std::vector<int64_t> aoff, boff; // per segment
@@ -92,9 +94,11 @@ struct Op {
                       // (the transposed program zeroes them before this op's transpose)
 };
 
-struct ZeroSpec { int arena; int64_t off, n; };  // zero n elements before the next op
+// zero n elements before the next op; the buffer's tensor holds the first `used` of them (the
+// rest is alignment padding that no op reads)
+struct ZeroSpec { int arena; int64_t off, n, used; };
 
-struct ScrBuf { int64_t off, n; };
+struct ScrBuf { int64_t off, n, used; };  // used: elements before rounding to the alignment
 
 struct Program {
   std::vector<Op> ops;
@@ -140,9 +144,10 @@ std::string validate_plan(const Plan& P, const Program& pr);
 // New GEMM/PERM/BTRANS entries are appended to the plan's tables.
 Program transpose_program(Plan& P, const Program& fwd);
 
-// A scratch buffer is zeroed just before its first use.  Where that use is a permutation that
-// writes every element of exactly that buffer and does not read it, the permutation stores
-// instead of accumulating (a copy of it with store = 1) and the zero op is dropped.
+// A scratch buffer is zeroed just before its first use.  Where that use is a permutation or a
+// GEMM (epi == 0, every batch entry with at least one segment) that writes every element of
+// exactly that buffer once and does not read it, the op stores instead of accumulating (a copy
+// of it with store = 1) and the zero op is dropped.
 void fold_first_writes(Plan& P, Program& pr);
 
 }  // namespace lrcc

@@ -99,9 +99,9 @@ lrcc_status lrcc_plan_gemm(const lrcc_plan* h, int32_t idx, int32_t* ints, int64
   if (!h || idx < 0 || idx >= (int32_t)h->P.gemms.size()) return LRCC_EINVAL;
   const Gemm& g = h->P.gemms[idx];
   if (ints) {
-    int32_t v[15] = {g.M,     g.N,     g.K,     g.ta,    g.tb,    g.arA,       g.arB,
+    int32_t v[16] = {g.M,     g.N,     g.K,     g.ta,    g.tb,    g.arA,       g.arB,
                      g.arC,   g.epi,   g.ep[0], g.ep[1], g.ep[2], g.ep[3], g.nbatch(),
-                     (int32_t)g.aoff.size()};
+                     (int32_t)g.aoff.size(), g.store};
     std::memcpy(ints, v, sizeof(v));
   }
   if (lds) {

@@ -381,6 +381,7 @@ lrcc_status Runtime::run_packed(int gi, const Gemm& g, double2* const ar[AR_COUN
   a.M = g.M; a.N = g.N; a.nkt = (int)((2LL * g.K + 31) / 32);
   a.epi = g.epi; a.ep1 = g.ep[1]; a.ep2 = g.ep[2]; a.ep3 = g.ep[3];
   a.ldc = g.ldc; a.ar = g.ar; a.ai = g.ai;
+  a.store = g.store;
   a.coff = d.coff; a.sbeg = d.sbeg; a.ia = pp.d_ia; a.ib = pp.d_ib;
   a.nbatch = g.nbatch();
   a.tiles_m = a.tiles_n = 1;
@@ -650,6 +651,7 @@ lrcc_status Runtime::autotune(const Program& pr, double2* const ar[AR_COUNT], in
     a.epi = g.epi; a.ep1 = g.ep[1]; a.ep2 = g.ep[2]; a.ep3 = g.ep[3];
     a.lda = g.lda; a.ldb = g.ldb; a.ldc = g.ldc;
     a.ar = g.ar; a.ai = g.ai;
+    a.store = g.store;
     a.coff = d.coff; a.sbeg = d.sbeg; a.aoff = d.aoff; a.boff = d.boff;
     a.nbatch = g.nbatch();
     a.tiles_m = a.tiles_n = 1;
@@ -808,6 +810,7 @@ lrcc_status Runtime::run(const Program& pr, double2* const ar[AR_COUNT], int nrh
       a.epi = g.epi; a.ep1 = g.ep[1]; a.ep2 = g.ep[2]; a.ep3 = g.ep[3];
       a.lda = g.lda; a.ldb = g.ldb; a.ldc = g.ldc;
       a.ar = g.ar; a.ai = g.ai;
+      a.store = g.store;
       a.coff = d.coff; a.sbeg = d.sbeg; a.aoff = d.aoff; a.boff = d.boff;
       a.nbatch = g.nbatch();
       a.tiles_m = a.tiles_n = 1;

@@ -57,7 +57,7 @@ class PlanView:
             lib.lrcc_plan_op(h, which, i, _p(kif, I32P))
             kind, idx, fixed = map(int, kif)
             if kind == 0:
-                ints = np.zeros(15, np.int32)
+                ints = np.zeros(16, np.int32)
                 lds = np.zeros(3, np.int64)
                 al = np.zeros(2)
                 lib.lrcc_plan_gemm(h, idx, _p(ints, I32P), _p(lds, I64P), _p(al, F64P), None, None, None, None)
@@ -126,7 +126,7 @@ def _mat(buf, off, rows, cols, ld):
 def run(ops, arenas):
     for kind, _fixed, d in ops:
         if kind == "gemm":
-            M, N, K, ta, tb, arA, arB, arC, epi, e0, e1, e2, e3, nb, ns = map(int, d["ints"])
+            M, N, K, ta, tb, arA, arB, arC, epi, e0, e1, e2, e3, nb, ns, store = map(int, d["ints"])
             lda, ldb, ldc = map(int, d["lds"])
             al = d["alpha"]
             A, Bm, Cm = arenas[arA], arenas[arB], arenas[arC]
@@ -139,7 +139,10 @@ def run(ops, arenas):
                 c0 = int(d["coff"][b])
                 if epi == 0:
                     cm = _mat(Cm, c0, M, N, ldc)
-                    cm += al * acc
+                    if store:  # first writer: the old contents are not read
+                        cm[...] = al * acc
+                    else:
+                        cm += al * acc
                 else:
                     na, nbb, nc, nd = e0, e1, e2, e3
                     m = np.arange(M)[:, None]

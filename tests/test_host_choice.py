@@ -53,7 +53,7 @@ def _gemm_ops(lib, h, epi=None):
             if kif[0] != 0 or kif[1] in seen:
                 continue
             idx = kif[1]
-            ints = (C.c_int32 * 15)()
+            ints = (C.c_int32 * 16)()
             assert lib.lrcc_plan_gemm(h, idx, ints, None, None, None, None, None, None) == 0
             nb = ints[13]
             sbeg = np.zeros(nb + 1, np.int32)

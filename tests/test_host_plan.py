@@ -43,15 +43,19 @@ def test_plan_validates_for_workloads(lib, cfg):
 
 
 def test_first_writes_fold_zeroing_at_c2(lib):
-    """At the Nk=5 workload the permutations that are first writers of a whole scratch buffer
-    store into it (no zero op ahead of them): five in the Jacobian program, nine in its
-    transpose.  A store permutation never reads the buffer it writes."""
+    """At the Nk=5 workload the permutations and GEMMs that are first writers of a whole
+    scratch buffer store into it (no zero op ahead of them): 5 permutations and 21 GEMMs of
+    the Jacobian program, 9 and 17 of its transpose; two zero ops remain in each (the ladder's
+    half-filled pair-pair buffer and a singles transpose).  A store permutation never reads the
+    buffer it writes."""
     c = CONFIGS["c2"]
     pv = plan_sim.PlanView(lib, c["nk"], c["nocc"], c["nvir"], c["naux"], 1 << 30)
-    for which, want in ((1, 5), (2, 9)):
+    for which, want, want_g in ((1, 5, 21), (2, 9, 17)):
         ops = pv.programs[which]
         stores = [d for k, _, d in ops if k == "perm" and d["ints"][18]]
         assert len(stores) == want
+        assert sum(1 for k, _, d in ops if k == "gemm" and d["ints"][15]) == want_g
+        assert sum(1 for k, _, d in ops if k == "zero") == 2
         for d in stores:
             v = d["ints"]
             n = int(np.prod(v[8:12])) * int(v[7]) ** 3
