@@ -35,7 +35,7 @@ FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 pipe, nominal (profiling recipe table
 # case scaled to the workload (profiles/): (kernel source file, its sha256 prefix when the
 # counters were taken, bytes per launch at the default workload).  The bench reports null
 # once the source has changed since.
-TRAFFIC_RECORD = ("paper_2508_01266_gb300/csrc/kernels_f64.cu", "cc609e373f39761f", 3.2417e9)
+TRAFFIC_RECORD = ("paper_2508_01266_gb300/csrc/kernels_f64.cu", "03d9683c8eec91ec", 3.2225e9)
 
 
 def _dist():
