@@ -19,7 +19,11 @@ fixture keeps the CCSD energy per cell and a seeded sample of T and Lambda eleme
 paper's normalization (t2 and lambda2 carry the factor Nk; lambda as the paper's
 multipliers), so that a GPU ground state can be compared element by element.
 
-    python tests/golden/make_c2_alpha.py [workers] [threads per worker]   # from the repo root
+    python tests/golden/make_c2_alpha.py [workers] [threads per worker] [components] [omegas]
+
+from the repo root; components as letters (default xyz), frequencies in Ha separated by commas
+(default 0,0.05,0.1).  A subset (say z and 0,0.05) writes alpha for those components and
+frequencies only; the fixture records which.
 """
 import json
 import multiprocessing as mp
@@ -89,15 +93,15 @@ def _init_worker(threads):
 
 def _resp_task_iters(args):
     """One perturbed-amplitude system, (A - w) t = -xi^X, with its iteration count."""
-    ic, w = args
+    c, w = args
     import torch
     from oracle import rcc
-    name = tname(COMPS[ic], w)
+    name = tname(c, w)
     if os.path.exists(_path(name)):
         return name
     p, R = _system()
     t1, t2, _ = torch.load(_path("ccsd"))
-    xi = torch.load(_path(f"xi{COMPS[ic]}"))
+    xi = torch.load(_path(f"xi{c}"))
 
     def run():
         x1, x2, it = rcc.solve_response(R, t1, t2, *xi, w, RESP_TOL)
@@ -112,14 +116,14 @@ def _F_task(args):
     x, y, w = args
     import torch
     from oracle import rcc
-    name = f"F{COMPS[x]}{COMPS[y]}_w{w:.3f}"
+    name = f"F{x}{y}_w{w:.3f}"
     if os.path.exists(_path(name)):
         return name
     p, R = _system()
     t1, t2, _ = torch.load(_path("ccsd"))
     l1, l2, _ = torch.load(_path("lambda"))
-    um = torch.load(_path(tname(COMPS[x], -w)))
-    wp = torch.load(_path(tname(COMPS[y], w)))
+    um = torch.load(_path(tname(x, -w)))
+    wp = torch.load(_path(tname(y, w)))
     staged(name, lambda: torch.tensor(complex(rcc.F_dot(R, t1, t2, l1, l2, um[0], um[1], wp[0], wp[1]))))
     return name
 
@@ -146,6 +150,11 @@ def main():
     from oracle import rcc
     workers = int(sys.argv[1]) if len(sys.argv) > 1 else 3
     wthreads = int(sys.argv[2]) if len(sys.argv) > 2 else 2
+    global COMPS, OMEGAS
+    if len(sys.argv) > 3:
+        COMPS = tuple("xyz".index(ch) for ch in sys.argv[3])
+    if len(sys.argv) > 4:
+        OMEGAS = tuple(float(w) for w in sys.argv[4].split(","))
     torch.set_num_threads(os.cpu_count() or 8)
     os.makedirs(CACHE, exist_ok=True)
     p, R = _system()
@@ -162,9 +171,9 @@ def main():
         staged(f"xi{c}", lambda m=m: rcc.perturbation_rhs(R, t1, t2, m))
     ctx = mp.get_context("spawn")
     # response systems (need T only)
-    jobs = [(ic, w) for w in OMEGAS for ic in range(len(COMPS))]
-    jobs += [(ic, -w) for w in OMEGAS if w != 0 for ic in range(len(COMPS))]
-    todo = [j for j in jobs if not os.path.exists(_path(tname(COMPS[j[0]], j[1])))]
+    jobs = [(c, w) for w in OMEGAS for c in COMPS]
+    jobs += [(c, -w) for w in OMEGAS if w != 0 for c in COMPS]
+    todo = [j for j in jobs if not os.path.exists(_path(tname(j[0], j[1])))]
     if todo:
         _log(f"response systems: {len(todo)} on {workers} workers x {wthreads} threads")
         with ctx.Pool(workers, initializer=_init_worker, initargs=(wthreads,)) as pool:
@@ -184,8 +193,8 @@ def main():
             for y in range(nc):
                 if w == 0 and y < x:
                     continue  # F is symmetric: F(t^x, t^y) = F(t^y, t^x) at w = 0
-                fjobs.append((x, y, w))
-    todo = [j for j in fjobs if not os.path.exists(_path(f"F{COMPS[j[0]]}{COMPS[j[1]]}_w{j[2]:.3f}"))]
+                fjobs.append((COMPS[x], COMPS[y], w))
+    todo = [j for j in fjobs if not os.path.exists(_path(f"F{j[0]}{j[1]}_w{j[2]:.3f}"))]
     if todo:
         _log(f"F scalars: {len(todo)} on {workers} workers x {wthreads} threads")
         with ctx.Pool(workers, initializer=_init_worker, initargs=(wthreads,)) as pool:
