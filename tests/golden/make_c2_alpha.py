@@ -19,11 +19,12 @@ fixture keeps the CCSD energy per cell and a seeded sample of T and Lambda eleme
 paper's normalization (t2 and lambda2 carry the factor Nk; lambda as the paper's
 multipliers), so that a GPU ground state can be compared element by element.
 
-    python tests/golden/make_c2_alpha.py [workers] [threads per worker] [components] [omegas]
+    python tests/golden/make_c2_alpha.py [workers] [threads per worker] [components] [omegas] [output]
 
 from the repo root; components as letters (default xyz), frequencies in Ha separated by commas
-(default 0,0.05,0.1).  A subset (say z and 0,0.05) writes alpha for those components and
-frequencies only; the fixture records which.
+(default 0,0.05,0.1), output file name under tests/golden (default oracle_c2_alpha.json).  A
+subset (say z and 0,0.1) writes alpha for those components and frequencies only; the fixture
+records which.  Runs with different subsets share the cache.
 """
 import json
 import multiprocessing as mp
@@ -111,6 +112,35 @@ def _resp_task_iters(args):
     return name
 
 
+def _grad_task(args):
+    """The gradient stages (Lambda, Eqs. 10-11; eta^X) in a child process of their own: they
+    peak near 55 GB, and memory the parent kept after them would be missing for the F pool."""
+    kind, c = args
+    import torch
+    from oracle import rcc
+    p, R = _system()
+    t1, t2, _ = torch.load(_path("ccsd"))
+    if kind == "lambda":
+        def lam():
+            l1, l2, it = rcc.solve_lambda(R, t1, t2, tol=GS_TOL)
+            return l1, l2, torch.tensor(it)
+        staged("lambda", lam)
+    else:
+        l1, l2, _ = torch.load(_path("lambda"))
+        m = rcc.dipole_ops(p, (c,))[0]
+        staged(f"eta{c}", lambda: rcc.eta_vector(R, t1, t2, l1, l2, m))
+    return kind
+
+
+def _in_child(ctx, threads, args):
+    """Run _grad_task(args) in one spawned worker unless its result is cached."""
+    name = "lambda" if args[0] == "lambda" else f"eta{args[1]}"
+    if os.path.exists(_path(name)):
+        return
+    with ctx.Pool(1, initializer=_init_worker, initargs=(threads,)) as pool:
+        pool.map(_grad_task, [args])
+
+
 def _F_task(args):
     """F(t^x(-w), t^y(+w)), the quadratic term of Eq. 15 (rcc.F_dot)."""
     x, y, w = args
@@ -155,6 +185,7 @@ def main():
         COMPS = tuple("xyz".index(ch) for ch in sys.argv[3])
     if len(sys.argv) > 4:
         OMEGAS = tuple(float(w) for w in sys.argv[4].split(","))
+    outname = sys.argv[5] if len(sys.argv) > 5 else "oracle_c2_alpha.json"
     torch.set_num_threads(os.cpu_count() or 8)
     os.makedirs(CACHE, exist_ok=True)
     p, R = _system()
@@ -180,12 +211,12 @@ def main():
             for name in pool.imap_unordered(_resp_task_iters, todo):
                 _log(f"done {name}")
 
-    def lam():
-        l1, l2, it = rcc.solve_lambda(R, t1, t2, tol=GS_TOL)
-        return l1, l2, torch.tensor(it)
-
-    l1, l2, it_l = staged("lambda", lam)
-    etas = [staged(f"eta{c}", lambda m=m: rcc.eta_vector(R, t1, t2, l1, l2, m)) for c, m in zip(COMPS, mus)]
+    nthreads = os.cpu_count() or 8
+    _in_child(ctx, nthreads, ("lambda", None))
+    for c in COMPS:
+        _in_child(ctx, nthreads, ("eta", c))
+    l1, l2, it_l = torch.load(_path("lambda"))
+    etas = [torch.load(_path(f"eta{c}")) for c in COMPS]
     nc = len(COMPS)
     fjobs = []
     for w in OMEGAS:
@@ -246,7 +277,7 @@ def main():
         "alpha": [[[_cplx(x) for x in row] for row in blk] for blk in alpha],
         "ground_state_sample": sample,
     }
-    with open(os.path.join(HERE, "oracle_c2_alpha.json"), "w") as f:
+    with open(os.path.join(HERE, outname), "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")
     _log(f"alpha written ({time.time() - t0:.0f} s this run)")

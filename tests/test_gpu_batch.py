@@ -71,6 +71,43 @@ def test_batch_vs_oracle_converged(lr):
         pr.close()
 
 
+def test_batch_at_real_shapes_smallest_vs_oracle(lr):
+    """Two chains of the mixed-size batch at their real shapes, (Nk, nocc, nvir, naux) =
+    (3, 4, 24, 96) and (5, 6, 32, 128), in one FP64 batch call: the smaller, given the oracle's
+    converged T and Lambda, matches the oracle's alpha_zz(0, 0.1) to 1e-8 relative (Eq. 15),
+    and each problem's alpha equals its solo solve bit for bit.  The larger one takes a seeded
+    weakly correlated ground state (amplitudes of size 0.01): the oracle would need hours for
+    it on the host."""
+    from test_gpu_alpha import paper_lambda
+    comps, omegas = [2], [0.0, 0.1]
+    p = make_problem(3, 4, 24, 96, seed=1266)
+    R = rcc.RCC(p)
+    t1, t2, _ = rcc.solve_ccsd(R, tol=1e-10)
+    l1, l2, _ = rcc.solve_lambda(R, t1, t2, tol=1e-10)
+    ref = rcc.polarizability(R, t1, t2, l1, l2, rcc.dipole_ops(p, comps), omegas, tol=1e-11)
+    pl1, pl2 = paper_lambda(3, l1, l2)
+    small = lr.Problem(3, 4, 24, 96)
+    small.set_integrals(p.L, p.eps, p.dip)
+    small.set_ground_state(t1, t2 * 3, pl1, pl2)
+    q = make_problem(5, 6, 32, 128, seed=1267)
+    u1, u2 = random_amplitudes(5, 6, 32, seed=1268, scale1=0.01, scale2=0.01)
+    m1, m2 = random_amplitudes(5, 6, 32, seed=1269, scale1=0.01, scale2=0.01)
+    big = lr.Problem(5, 6, 32, 128)
+    big.set_integrals(q.L, q.eps, q.dip)
+    big.set_ground_state(u1, u2 * 5, m1, m2 * 5)
+    opts = lr.default_options(conv_tol=1e-11, max_iter=300)
+    res = lr.batch_polarizability([small, big], comps, omegas, opts)
+    alone = [pr.polarizability(comps, omegas, opts)[0] for pr in (small, big)]
+    for (a, info), b in zip(res, alone):
+        assert info[1] == 0
+        assert np.array_equal(a, b)
+    rel = np.abs(res[0][0] - ref).max() / np.abs(ref).max()
+    print("(3,4,24,96) alpha_zz batch", res[0][0].ravel(), "oracle", ref.ravel(), "rel", rel)
+    assert rel < 1e-8
+    small.close()
+    big.close()
+
+
 def test_batch_rejects_duplicate_handles(lr):
     pr = _prob(lr, 1, 1, 2, 3, seed=300)
     with pytest.raises(lr.LrccError):

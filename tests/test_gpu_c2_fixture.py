@@ -1,0 +1,110 @@
+"""The Nk=5 chain workload (nocc=8, nvir=40, naux=160, seed 1266) end to end on the GPU against
+the oracle's stored results (tests/golden/oracle_c2_alpha*.json: alpha_zz at 0 and 0.1 Ha, and
+the 3 x 3 tensor at 0 Ha; written by tests/golden/make_c2_alpha.py from oracle/ and synth/
+alone; hours of CPU time, so they are stored rather than recomputed here).
+
+The GPU starts from the integrals: it solves the CCSD amplitudes (Eqs. 7-8) and the Lambda
+multipliers (Eqs. 10-11) itself, then the perturbed amplitudes (Eqs. 13-14) and alpha in the
+symmetric form of Eq. 15 for the components and frequencies the fixture holds.
+
+Tolerances: alpha 1e-8 relative per element on the FP64 path and 1e-5 a.u. absolute on the
+BF16x3 path with FP64 refinement; CCSD energy per cell 1e-8 relative; the fixture's seeded
+sample of T and Lambda elements (paper normalization) within 1e-7 of the sample's largest
+element.  Both sides are converged to a residual of 1e-10 or below, so amplitudes agree to
+about residual / smallest denominator (1e-10 absolute), and the energy, a sum of millions of
+amplitude-integral products, to well below the 1e-8 relative of alpha's own tolerance.
+"""
+import glob
+import json
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+FIXTURES = sorted(glob.glob(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_c2_alpha*.json")))
+
+
+@pytest.fixture(scope="module")
+def lr():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2508_01266_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def refs():
+    assert FIXTURES, "oracle fixture missing"
+    out = []
+    for path in FIXTURES:
+        with open(path) as f:
+            d = json.load(f)
+        cplx = lambda z: complex(z[0], z[1])  # noqa: E731
+        d["alpha_c"] = np.array([[[cplx(x) for x in row] for row in blk] for blk in d["alpha"]])
+        out.append(d)
+    return out
+
+
+@pytest.fixture(scope="module")
+def problem(refs):
+    from synth import make_problem
+    r = refs[0]
+    assert all((d["nk"], d["nocc"], d["nvir"], d["naux"], d["seed"]) ==
+               (r["nk"], r["nocc"], r["nvir"], r["naux"], r["seed"]) for d in refs)
+    return make_problem(r["nk"], r["nocc"], r["nvir"], r["naux"], seed=r["seed"])
+
+
+def _sample_err(got, sample):
+    """max |got[i] - ref_i| over the stored elements, and max |ref_i|."""
+    g = got.cpu().numpy()
+    err = max(abs(g[tuple(i)] - complex(*z)) for i, z in sample)
+    big = max(abs(complex(*z)) for _, z in sample)
+    return err, big
+
+
+def test_c2_fp64_ground_state_and_alpha_vs_oracle(lr, refs, problem):
+    p = problem
+    prob = lr.Problem(p.nk, p.nocc, p.nvir, p.naux)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    opts = lr.default_options(conv_tol=1e-11, max_iter=300)
+    g1, g2, h1, h2, e, info = prob.solve_ground_state(opts)
+    assert info[1] == 0 and info[3] == 0
+    ref = refs[0]
+    e_ref = complex(*ref["energy_per_cell"]).real
+    print(f"C2 energy per cell gpu {e!r} oracle {e_ref!r}")
+    assert abs(e - e_ref) <= 1e-8 * abs(e_ref)
+    s = ref["ground_state_sample"]
+    for name, got in (("t1", g1), ("t2", g2), ("l1", h1), ("l2", h2)):
+        err, big = _sample_err(got, s[name])
+        print(f"C2 {name} sample: max |err| {err:.2e}, max |ref| {big:.2e}")
+        assert err <= 1e-7 * big
+    for ref in refs:
+        got, info = prob.polarizability(ref["comps"], ref["omegas"], opts)
+        assert info[1] == 0
+        want = ref["alpha_c"]
+        rel = np.abs(got - want) / np.abs(want).max()
+        print(f"C2 alpha comps {ref['comps']} omegas {ref['omegas']}: gpu {got.real.ravel()} "
+              f"oracle {want.real.ravel()} max rel {rel.max():.2e}")
+        assert rel.max() < 1e-8
+    prob.close()
+
+
+def test_c2_bf16x3_end_to_end_vs_oracle(lr, refs, problem):
+    """Ground state and alpha in BF16x3 contractions with FP64 refinement (residual 1e-7 or
+    below in the response solves): every alpha element within 1e-5 a.u. of the oracle."""
+    p = problem
+    prob = lr.Problem(p.nk, p.nocc, p.nvir, p.naux)
+    prob.set_integrals(p.L, p.eps, p.dip)
+    opts = lr.default_options(precision=2, conv_tol=1e-9, refine_tol=1e-7, max_iter=300)
+    *_, e, info = prob.solve_ground_state(opts)
+    assert info[1] == 0 and info[3] == 0
+    for ref in refs:
+        got, info = prob.polarizability(ref["comps"], ref["omegas"], opts)
+        assert info[1] == 0
+        err = np.abs(got - ref["alpha_c"])
+        print(f"C2 alpha BF16x3 comps {ref['comps']} omegas {ref['omegas']}: {got.real.ravel()} "
+              f"per-element |err| {err.ravel()}")
+        assert err.max() <= 1e-5
+    prob.close()
