@@ -392,8 +392,7 @@ __host__ __device__ inline void lay_strides(int kind, int nk, const int* n, long
   }
 }
 
-constexpr int SLAB_MAX = 64;   // largest orbital extent of a slab dimension
-constexpr int SLAB_BATCH = 4;  // global loads in flight per thread in the slab kernel
+constexpr int SLAB_MAX = 64;  // largest orbital extent of a slab dimension
 
 struct SlabArgs {
   PermArgs p;
@@ -407,7 +406,7 @@ struct SlabArgs {
 // One CTA handles whole slabs: the (dy, dx) plane of the destination at fixed momenta and fixed
 // outer orbital indices.  Source elements are read along the source's unit-stride direction
 // into shared memory, destination elements written along dx; both global sides coalesce.
-__global__ void __launch_bounds__(256, 4) perm_slab_kernel(SlabArgs a) {
+__global__ void __launch_bounds__(256) perm_slab_kernel(SlabArgs a) {
   extern __shared__ double2 slab[];  // [ny][nx + 1]
   const PermArgs& p = a.p;
   const long long rhs = blockIdx.y;
@@ -435,52 +434,26 @@ __global__ void __launch_bounds__(256, 4) perm_slab_kernel(SlabArgs a) {
                                     di[p.pi[1]], di[p.pi[2]], di[p.pi[3]]);
     (void)inv;
     __syncthreads();  // the previous slab's writes have read the shared tile
-    // Each thread issues all its global loads of a batch before it uses any of them, so that
-    // SLAB_BATCH 16-byte loads per thread are in flight instead of one.
-    for (int e0 = threadIdx.x; e0 < nel; e0 += SLAB_BATCH * blockDim.x) {
-      double2 v[SLAB_BATCH];
-      int so[SLAB_BATCH];
-#pragma unroll
-      for (int u = 0; u < SLAB_BATCH; ++u) {
-        const int e = e0 + u * blockDim.x;
-        so[u] = -1;
-        if (e < nel) {
-          int x, y;
-          if (src_x_fast) {
-            x = e % nx;
-            y = e / nx;
-          } else {
-            y = e % ny;
-            x = e / ny;
-          }
-          so[u] = y * pitch + x;
-          v[u] = S[sbase + x * a.ssx + y * a.ssy];
-        }
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+      int x, y;
+      if (src_x_fast) {
+        x = e % nx;
+        y = e / nx;
+      } else {
+        y = e % ny;
+        x = e / ny;
       }
-#pragma unroll
-      for (int u = 0; u < SLAB_BATCH; ++u)
-        if (so[u] >= 0) slab[so[u]] = v[u];
+      slab[y * pitch + x] = S[sbase + x * a.ssx + y * a.ssy];
     }
     __syncthreads();
-    for (int e0 = threadIdx.x; e0 < nel; e0 += SLAB_BATCH * blockDim.x) {
-      double2 d[SLAB_BATCH];
-#pragma unroll
-      for (int u = 0; u < SLAB_BATCH; ++u) {
-        const int e = e0 + u * blockDim.x;
-        d[u] = make_double2(0.0, 0.0);
-        if (e < nel && !p.store) d[u] = D[dbase + (e % nx) * a.dsx + (e / nx) * a.dsy];
-      }
-#pragma unroll
-      for (int u = 0; u < SLAB_BATCH; ++u) {
-        const int e = e0 + u * blockDim.x;
-        if (e < nel) {
-          const int x = e % nx, y = e / nx;
-          const double2 s = slab[y * pitch + x];
-          d[u].x += p.ar * s.x - p.ai * s.y;
-          d[u].y += p.ar * s.y + p.ai * s.x;
-          D[dbase + x * a.dsx + y * a.dsy] = d[u];
-        }
-      }
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+      const int x = e % nx, y = e / nx;
+      const double2 s = slab[y * pitch + x];
+      double2* dp = D + dbase + x * a.dsx + y * a.dsy;
+      double2 d = p.store ? make_double2(0.0, 0.0) : *dp;
+      d.x += p.ar * s.x - p.ai * s.y;
+      d.y += p.ar * s.y + p.ai * s.x;
+      *dp = d;
     }
   }
 }
