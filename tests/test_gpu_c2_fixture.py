@@ -1,6 +1,6 @@
 """The Nk=5 chain workload (nocc=8, nvir=40, naux=160, seed 1266) end to end on the GPU against
-the oracle's stored results (tests/golden/oracle_c2_alpha*.json: alpha_zz at 0 and 0.1 Ha, and
-the 3 x 3 tensor at 0 Ha; written by tests/golden/make_c2_alpha.py from oracle/ and synth/
+the oracle's stored results (tests/golden/oracle_c2_alpha*.json: alpha_zz at 0, 0.05 and 0.1 Ha,
+and the 3 x 3 tensor at 0 Ha; written by tests/golden/make_c2_alpha.py from oracle/ and synth/
 alone; hours of CPU time, so they are stored rather than recomputed here).
 
 The GPU starts from the integrals: it solves the CCSD amplitudes (Eqs. 7-8) and the Lambda
